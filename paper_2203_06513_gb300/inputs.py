@@ -1,0 +1,137 @@
+"""Seeded synthetic inputs shared by the CUDA path, its tests and the oracle.
+
+This module holds no arithmetic of the method: it only draws marker positions
+and momenta and writes the initial field coefficients of the workloads the
+library is measured on.  Both sides (CUDA library and CPU oracle) take these
+arrays as given.
+
+Recipe (one electron species on a neutralising unit ion background):
+* positions x in [0, L): inverse CDF of the density (1 + eps cos(kappa x)) / L,
+  i.e. x + (eps/kappa) sin(kappa x) = u L with u ~ U[0,1), solved by Newton;
+* momenta p ~ N(0, vth^2) (a Maxwellian in p with c = 1);
+* equal weights w = L / Np, so that sum w = L balances the background;
+* pump A_y = amp cos(k0 x), A_z = 0, E_y = E_z = 0 (released from rest).  The
+  A_y coefficients are the values of the pump at the Greville abscissae
+  x_j + (k+1) dx / 2 of the degree-k basis (the Schoenberg quasi-interpolant,
+  one reading of the projector Pi_0 of Sec. 3.1);
+* E_x is not an input: each side solves the discrete Poisson equation.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    L: float = 4.0 * math.pi
+    nx: int = 128
+    degree: int = 3
+    np: int = 20000
+    dt: float = 0.05
+    steps: int = 50
+    tol: float = 1e-13
+    eps: float = 0.01          # density perturbation amplitude
+    kappa: float = 0.5         # density perturbation wavenumber
+    vth: float = 0.1
+    pump: float = 0.1          # A_y amplitude
+    k0_mode: int = 4           # k0 = 2 pi k0_mode / L
+    seed: int = 0
+    max_iter: int = 100
+
+    @property
+    def dx(self) -> float:
+        return self.L / self.nx
+
+    @property
+    def k0(self) -> float:
+        return 2.0 * math.pi * self.k0_mode / self.L
+
+    @property
+    def weight(self) -> float:
+        return self.L / self.np
+
+
+# The five measured workloads (1D periodic, L = 4 pi, k0 = 2 pi 4 / L = 2).
+WORKLOADS = {
+    # plain method, FP64: the parity workload
+    "C1": Workload("C1", nx=128, degree=3, np=20000, dt=0.05, steps=50, tol=1e-13,
+                   vth=0.1, pump=0.1),
+    # plain method at scale (FP32 particle state, FP64 grid)
+    "C2": Workload("C2", nx=2048, degree=3, np=100_000_000, dt=0.05, steps=1000,
+                   vth=0.1, pump=0.2),
+    # precision sweep: quintic splines
+    "C3": Workload("C3", nx=4096, degree=5, np=400_000_000, dt=0.05, steps=1000,
+                   vth=0.05, pump=0.3),
+    # learned warm start: C2 shape
+    "C5": Workload("C5", nx=2048, degree=3, np=100_000_000, dt=0.05, steps=1000,
+                   vth=0.1, pump=0.2),
+}
+
+
+def workload(name: str, **overrides) -> Workload:
+    return replace(WORKLOADS[name], **overrides)
+
+
+def ensemble_members(n_runs: int = 256, seed: int = 0, np_scale: float = 1.0):
+    """The batched-ensemble workload: per run r, nx ~ U{256,512,1024,2048},
+    Np = floor(exp(U[ln 1e5, ln 4e6])) (times np_scale), pump ~ U[0.01, 0.3],
+    vth ~ U[0.02, 0.15], seed r.  Cubic splines, dt = 0.05."""
+    rng = np.random.default_rng(seed + 7919)
+    out = []
+    for r in range(n_runs):
+        nx = int(rng.choice([256, 512, 1024, 2048]))
+        npart = int(math.floor(math.exp(rng.uniform(math.log(1e5), math.log(4e6)))))
+        npart = max(64, int(npart * np_scale))
+        pump = float(rng.uniform(0.01, 0.3))
+        vth = float(rng.uniform(0.02, 0.15))
+        out.append(Workload(f"E{r}", nx=nx, degree=3, np=npart, dt=0.05, steps=1,
+                            vth=vth, pump=pump, seed=1000 + r))
+    return out
+
+
+def _inverse_cdf(u: np.ndarray, L: float, eps: float, kappa: float) -> np.ndarray:
+    """Solve x + (eps/kappa) sin(kappa x) = u L for x in [0, L) (Newton)."""
+    target = u * L
+    x = target.copy()
+    if eps != 0.0:
+        a = eps / kappa
+        for _ in range(60):
+            f = x + a * np.sin(kappa * x) - target
+            fp = 1.0 + eps * np.cos(kappa * x)
+            step = f / fp
+            x -= step
+            if np.max(np.abs(step)) < 1e-15 * L:
+                break
+    x = np.where(x < 0.0, x + L, x)
+    x = np.where(x >= L, x - L, x)
+    return x
+
+
+def particles(w: Workload, np_override: int | None = None, chunk: int = 1 << 24):
+    """(x, p) as float64 arrays, seeded by w.seed.  Generated in chunks so that
+    1e8-marker workloads stay within a few GB of host memory."""
+    n = w.np if np_override is None else int(np_override)
+    rng = np.random.default_rng(w.seed)
+    x = np.empty(n, dtype=np.float64)
+    p = np.empty(n, dtype=np.float64)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        u = rng.random(e - s)
+        x[s:e] = _inverse_cdf(u, w.L, w.eps, w.kappa)
+        p[s:e] = rng.normal(0.0, w.vth, e - s)
+    return x, p
+
+
+def fields(w: Workload):
+    """(ay, az, ey, ez) initial coefficients, float64 arrays of length nx."""
+    j = np.arange(w.nx, dtype=np.float64)
+    greville = (j + 0.5 * (w.degree + 1)) * w.dx
+    ay = w.pump * np.cos(w.k0 * greville)
+    az = np.zeros(w.nx)
+    ey = np.zeros(w.nx)
+    ez = np.zeros(w.nx)
+    return ay, az, ey, ez
