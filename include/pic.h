@@ -1,0 +1,178 @@
+/*
+ * pic.h -- C ABI of libpic, the GB300 (sm_103a) implementation of the
+ * particle side of the energy-conserving PIC scheme of Y. Li,
+ * "Energy conserving particle-in-cell methods for relativistic
+ * Vlasov--Maxwell equations of laser-plasma interaction" (arXiv:2203.06513),
+ * one dimension, hbar = 0 (no spin).
+ *
+ * The discrete system (Sec. 3.1): M uniform periodic cells of width
+ * dx = L/M; E_x in the degree-(k-1) spline space V1, E_y, E_z, A_y, A_z in
+ * the degree-k space V0; N_p markers with positions x_a, momenta p_a and
+ * equal weights w.  One time step is the Lie--Trotter composition of
+ * subsystem I (x, p, e_x) and subsystem II (e_y, e_z, a_y, a_z) of Sec. 4.2,
+ * each solved by fixed-point iteration of its discrete-gradient scheme.
+ *
+ * Conventions for every entry point:
+ *  - Return value: PIC_OK (0) or an error code below; on error
+ *    pic_last_error(h) returns a message owned by the handle (valid until the
+ *    next call on that handle).  A NULL handle yields PIC_ERR_INVALID.
+ *  - All floating-point arrays crossing the ABI are IEEE double, contiguous.
+ *    Particle arrays have N_p entries and are in the caller's original marker
+ *    order (the library may reorder markers internally and undoes it).  Grid
+ *    arrays have M entries, index j = coefficient of the j-th basis function.
+ *  - Arrays passed with mem = PIC_MEM_DEVICE are device pointers on the
+ *    handle's device; with PIC_MEM_HOST they are host pointers (pageable or
+ *    pinned).  The caller owns every array it passes; the handle never keeps
+ *    a caller pointer after a call returns.
+ *  - The handle owns its device state and scratch (allocated in pic_init,
+ *    freed in pic_destroy).  All work is ordered on the stream given to
+ *    pic_init (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *    Calls return after their results are complete on that stream unless
+ *    stated otherwise.  A handle must not be used from two threads at once.
+ */
+#ifndef PIC_H_
+#define PIC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PIC_OK              0
+#define PIC_ERR_INVALID     1   /* bad argument or configuration            */
+#define PIC_ERR_NOCONVERGE  2   /* fixed point hit max_iter; state is the last iterate */
+#define PIC_ERR_CUDA        3   /* CUDA runtime error                        */
+#define PIC_ERR_NOMEM       4   /* device or host allocation failed          */
+#define PIC_ERR_NUMERIC     5   /* NaN/Inf or a displacement beyond c*dt     */
+
+/* particle arithmetic */
+#define PIC_FP64            0   /* particle state and arithmetic in double   */
+#define PIC_FP32            1   /* particle state (cell, offset, p) and arithmetic in float;
+                                   deposits accumulated, solves, convergence and energy in double */
+/* memory spaces */
+#define PIC_MEM_HOST        0
+#define PIC_MEM_DEVICE      1
+
+/* initial guess of the subsystem-I fixed point */
+#define PIC_WARM_NONE       0   /* x^(0) = x^n                               */
+#define PIC_WARM_EXPLICIT   1   /* x^(0) = x^n + dt p^n / gamma(p^n, A^n(x^n)) */
+#define PIC_WARM_MLP        2   /* learned predictor loaded by pic_mlp_load  */
+
+/* pic_deposit kinds */
+#define PIC_DEP_CHARGE      0   /* rho_j = sum_a w Lambda^0_j(x_a)                                  */
+#define PIC_DEP_CURRENT     1   /* j_i = sum_a w int_{x_a}^{x_a+d_a} Lambda^1_i  (d_a from aux)     */
+#define PIC_DEP_SUSCEPT     2   /* s_i = sum_a w (A^n+A^*)(x_a) Lambda^0_i(x_a) / (g(p_a,A^n)+g(p_a,A^*)) */
+
+/* pic_gather fields */
+#define PIC_FIELD_EX        0   /* E_x,h(x_a) = sum_i e_x,i Lambda^1_i(x_a) */
+#define PIC_FIELD_EY        1   /* E_y,h(x_a), V0                           */
+#define PIC_FIELD_EZ        2
+#define PIC_FIELD_AY        3   /* A_y,h(x_a), V0                           */
+#define PIC_FIELD_AZ        4
+
+/* pic_substep selectors */
+#define PIC_SUBSYSTEM_I     1
+#define PIC_SUBSYSTEM_II    2
+
+typedef struct pic_handle pic_handle;
+
+typedef struct {
+    double  L;           /* domain length (periodic [0, L))                        */
+    int32_t nx;          /* M: number of cells = dim V0 = dim V1, 8 <= M <= 8192    */
+    int32_t degree;      /* k: degree of V0 (V1 has k-1), 2 <= k <= 5               */
+    int64_t np;          /* N_p >= 1                                                */
+    double  weight;      /* w: equal marker weight (L/N_p neutralises the background) */
+    double  dt;          /* time step, 0 < dt, and dt/dx <= 64                      */
+    double  tol;         /* fixed-point tolerance: max-norm of the position increment
+                            (length units) and of the field increment               */
+    int32_t max_iter;    /* cap on fixed-point sweeps per substep (1..1000)         */
+    int32_t precision;   /* PIC_FP64 or PIC_FP32                                    */
+    int32_t warm_start;  /* PIC_WARM_*                                              */
+    int32_t sort_every;  /* re-sort markers by cell every this many steps (0: only at init) */
+} pic_config;
+
+/* FP64 arrays of the discrete state u = (X, P, e_x, e_y, e_z, a_y, a_z), Sec. 3.1.
+ * Any member may be NULL where a call says it is ignored. */
+typedef struct {
+    double *x;           /* N_p positions in [0, L)        */
+    double *p;           /* N_p longitudinal momenta       */
+    double *ex;          /* M coefficients in V1           */
+    double *ey, *ez;     /* M coefficients in V0           */
+    double *ay, *az;     /* M coefficients in V0           */
+} pic_arrays;
+
+/* Create a handle and load the initial state (Sec. 3.1).  Reads x, p, ey, ez,
+ * ay, az from `in` (mem space `mem`); in->ex is ignored: e_x is computed from
+ * the discrete Poisson equation G^T M1 e_x = -Lambda_0(X)^T W 1 + dx 1 with
+ * sum_j e_x,j = 0 (Remark 2 of Sec. 4.2, with the neutralising background).
+ * Markers are sorted by cell.  On success *out owns the handle. */
+int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem,
+             void *stream, pic_handle **out);
+
+/* Copy the current state to `out` (members that are NULL are skipped), in
+ * the caller's marker order.  Positions are returned wrapped into [0, L). */
+int pic_get_state(pic_handle *h, const pic_arrays *out, int32_t mem);
+
+/* Deposit on the grid at the current positions (device output, `out`):
+ *  PIC_DEP_CHARGE : out[M]   = rho (Lambda^0 deposit), aux ignored.
+ *  PIC_DEP_CURRENT: out[M]   = w * path integral of Lambda^1 along x_a -> x_a + d_a
+ *                   (Sec. 4.2, subsystem I), aux = device d[N_p] in caller order.
+ *  PIC_DEP_SUSCEPT: out[2M]  = (s_y, s_z) of subsystem II (Sec. 4.2) with A^n the
+ *                   handle's a and A^* from aux = device (a*_y[M], a*_z[M]).
+ * Accumulation is in double. */
+int pic_deposit(pic_handle *h, int32_t kind, const double *aux, double *out);
+
+/* Gather a field at the current positions: out[N_p] (device), caller order. */
+int pic_gather(pic_handle *h, int32_t field, double *out);
+
+/* Advance one subsystem by dt (Sec. 4.2).  which = PIC_SUBSYSTEM_I: Picard
+ * iteration of the implicit discrete-gradient scheme for (X, P, e_x), one
+ * global e_x update per sweep; PIC_SUBSYSTEM_II: fixed point for
+ * (e_y, e_z, a_y, a_z) with the exact solve of (M0 + dt^2/4 G^T M1 G).
+ * *iters (may be NULL) receives the number of particle sweeps.
+ * PIC_ERR_NOCONVERGE when max_iter sweeps did not reach the tolerance (the
+ * state is then the last iterate). */
+int pic_substep(pic_handle *h, int32_t which, int32_t *iters);
+
+/* nsteps Lie--Trotter steps Phi_II(dt) o Phi_I(dt) (Sec. 5).  Sweep counts
+ * summed over the steps go to *iters_I / *iters_II (may be NULL). */
+int pic_step(pic_handle *h, int32_t nsteps, int64_t *iters_I, int64_t *iters_II);
+
+/* Discrete Hamiltonian (Eq. discrete_H, hbar = 0) and Gauss-law residual,
+ * evaluated in double from the stored state:
+ *  out[0] = sum_a w (gamma(p_a, A_h(x_a)) - 1)     kinetic
+ *  out[1] = 1/2 e_x^T M1 e_x
+ *  out[2] = 1/2 (e_y^T M0 e_y + e_z^T M0 e_z)
+ *  out[3] = 1/2 (a_y^T K a_y + a_z^T K a_z),  K = G^T M1 G
+ *  out[4] = total = out[0]+out[1]+out[2]+out[3]
+ *  out[5] = max_j |(G^T M1 e_x)_j + rho_j - dx|   (discrete Poisson residual) */
+int pic_energy(pic_handle *h, double out[6]);
+
+/* Kernel timing of the hot loop (CUDA events on the handle's stream).
+ * pic_timing_enable(h, 1) starts recording; pic_timing_read fills
+ * out[0] = total ms in subsystem-I sweep kernels, out[1] = their launches,
+ * out[2] = ms in subsystem-II sweep kernels, out[3] = launches,
+ * out[4] = ms in grid solve kernels, out[5] = launches,
+ * out[6] = total kernel launches issued by the library since enable,
+ * out[7] = marker-sweeps done by subsystem-I sweep kernels (sum of N_p per launch). */
+int pic_timing_enable(pic_handle *h, int32_t on);
+int pic_timing_read(pic_handle *h, double out[8]);
+
+/* Release the handle and all memory it owns.  NULL is allowed. */
+int pic_destroy(pic_handle *h);
+
+/* Message of the last error on h; with h == NULL, the message of the last
+ * failed pic_init on the calling thread. */
+/* Message of the last error on h; with h == NULL, the message of the last
+ * failed pic_init on the calling thread. */
+const char *pic_last_error(const pic_handle *h);
+
+/* Library version string, e.g. "libpic 1.0 sm_103a". */
+const char *pic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H_ */

@@ -1,0 +1,691 @@
+// pic_api.cu -- the C ABI of libpic (declared in include/pic.h): handle,
+// device memory, and the fixed-point drivers of subsystems I and II.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pic.h"
+#include "pic_internal.h"
+
+using namespace pic;
+
+int pic_set_smem_attrs(size_t s1, size_t s2, size_t s3);
+static thread_local std::string g_init_error;
+
+struct pic_handle {
+    pic_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    int M = 0, K = 0, H = 0, Dlim = 0, fp32 = 0;
+    long long np = 0;
+    double dx = 0.0;
+    size_t rsize = 8;               // bytes of one particle real
+    long long steps_done = 0;
+
+    // marker state: two copies of (cell, t, p, id) for the counting sort
+    PartPtrs P[2]{};
+    int cur = 0;
+    void *delta = nullptr, *pnew = nullptr;
+
+    // grid state (double)
+    double *ex = nullptr, *ey = nullptr, *ez = nullptr, *ay = nullptr, *az = nullptr;
+    double *ek = nullptr, *ebar = nullptr, *ga_y = nullptr, *ga_z = nullptr, *jb[2] = {nullptr, nullptr};
+    double *eky = nullptr, *ekz = nullptr, *aky = nullptr, *akz = nullptr;
+    double *by = nullptr, *bz = nullptr, *r0y = nullptr, *r0z = nullptr;
+    double *sy[2] = {nullptr, nullptr}, *sz[2] = {nullptr, nullptr};
+    double *rho = nullptr, *work = nullptr, *diag = nullptr;
+    int32_t *counts = nullptr;
+
+    // circulant bands and inverse taps
+    double *d_rowM0 = nullptr, *d_rowM1 = nullptr, *d_rowK = nullptr, *d_rowPm = nullptr;
+    double *d_tapM1 = nullptr, *d_tapP = nullptr;
+    int tapM1_start = 0, tapM1_n = 0, tapP_start = 0, tapP_n = 0;
+
+    DevCtrl *ctrl = nullptr;
+    int *h_flag = nullptr;          // pinned: converged flag readback
+    DevCtrl *h_ctrl = nullptr;      // pinned: full control block readback
+
+    int sweep_grid = 0, sweep_block = 256;
+    size_t smem1 = 0, smem2 = 0;
+
+    // timing
+    int timing = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double t_sw1 = 0, t_sw2 = 0, t_solve = 0;
+    long long n_sw1 = 0, n_sw2 = 0, n_solve = 0, launches = 0, marker_sweeps = 0;
+
+    std::string err;
+};
+
+static const char *kVersion = "libpic 1.0 sm_103a";
+
+static int fail(pic_handle *h, int code, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(h, PIC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL()                                                                               \
+    do {                                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                                \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(h, PIC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+        ++h->launches;                                                                      \
+    } while (0)
+
+template <typename T>
+static int dalloc(pic_handle *h, T **p, size_t n)
+{
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(h, PIC_ERR_NOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    }
+    return PIC_OK;
+}
+
+static void release(pic_handle *h)
+{
+    auto f = [](void *p) { if (p) cudaFree(p); };
+    for (int b = 0; b < 2; ++b) {
+        f(h->P[b].cell); f(h->P[b].t); f(h->P[b].p); f(h->P[b].id);
+        f(h->jb[b]); f(h->sy[b]); f(h->sz[b]);
+    }
+    f(h->delta); f(h->pnew);
+    double *arr[] = {h->ex, h->ey, h->ez, h->ay, h->az, h->ek, h->ebar, h->ga_y, h->ga_z,
+                     h->eky, h->ekz, h->aky, h->akz, h->by, h->bz, h->r0y, h->r0z, h->rho,
+                     h->work, h->diag, h->d_rowM0, h->d_rowM1, h->d_rowK, h->d_rowPm,
+                     h->d_tapM1, h->d_tapP};
+    for (double *a : arr) f(a);
+    f(h->counts);
+    f(h->ctrl);
+    if (h->h_flag) cudaFreeHost(h->h_flag);
+    if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+}
+
+static PartPtrs cur_parts(pic_handle *h)
+{
+    PartPtrs p = h->P[h->cur];
+    p.delta = h->delta;
+    p.pnew = h->pnew;
+    return p;
+}
+
+static int sync(pic_handle *h)
+{
+    CK(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
+static int read_ctrl(pic_handle *h)
+{
+    CK(cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
+static int particle_grid(pic_handle *h) { return h->num_sms * 4; }
+
+// ------------------------------------------------------------------ sort
+static int sort_markers(pic_handle *h)
+{
+    PartPtrs src = cur_parts(h);
+    PartPtrs dst = h->P[1 - h->cur];
+    dst.delta = h->delta;
+    dst.pnew = h->pnew;
+    if (launch_sort(h->fp32, h->np, h->M, src, dst, h->counts, particle_grid(h), 256, h->stream))
+        return fail(h, PIC_ERR_CUDA, "sort launch failed");
+    CKL();
+    h->cur = 1 - h->cur;
+    return PIC_OK;
+}
+
+// ------------------------------------------------------------------ charge + Poisson
+static int deposit_charge(pic_handle *h, double *out)
+{
+    CK(cudaMemsetAsync(out, 0, sizeof(double) * h->M, h->stream));
+    DiagArgs a{};
+    a.M = h->M; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.dx = h->dx; a.w = h->cfg.weight;
+    a.P = cur_parts(h);
+    a.out = out;
+    if (launch_charge(a, particle_grid(h), 256, charge_smem(h->M, h->K + 1), h->stream))
+        return fail(h, PIC_ERR_INVALID, "charge: bad degree");
+    CKL();
+    return PIC_OK;
+}
+
+static int conv_plain(pic_handle *h, const double *taps, int d_start, int ntap,
+                      const double *in0, double *out0, const double *in1, double *out1)
+{
+    ConvArgs c{};
+    c.M = h->M; c.d_start = d_start; c.ntap = ntap; c.mode = CONV_PLAIN; c.ncomp = in1 ? 2 : 1;
+    c.taps = taps;
+    c.in[0] = in0; c.in[1] = in1;
+    c.out[0] = out0; c.out[1] = out1;
+    c.ctrl = h->ctrl;
+    launch_conv(c, h->stream);
+    CKL();
+    return PIC_OK;
+}
+
+static int solve_poisson(pic_handle *h)
+{
+    int rc;
+    if ((rc = deposit_charge(h, h->rho))) return rc;
+    launch_poisson_rhs(h->M, h->dx, h->rho, h->work, h->stream);
+    CKL();
+    return conv_plain(h, h->d_tapM1, h->tapM1_start, h->tapM1_n, h->work, h->ex, nullptr, nullptr);
+}
+
+// ------------------------------------------------------------------ init
+extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem, void *stream,
+                        pic_handle **out)
+{
+    if (!cfg || !in || !out) return PIC_ERR_INVALID;
+    *out = nullptr;
+    const pic_config &c = *cfg;
+    if (!(c.L > 0) || c.nx < 8 || c.nx > 8192 || c.degree < 2 || c.degree > 5 || c.np < 1 ||
+        c.np > 2147483647LL || !(c.dt > 0) || !(c.tol > 0) || c.max_iter < 1 || c.max_iter > 1000 ||
+        (c.precision != PIC_FP64 && c.precision != PIC_FP32) ||
+        (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE) || !in->x || !in->p || !in->ay || !in->az ||
+        !std::isfinite(c.weight) || c.warm_start < 0 || c.warm_start > 2 || c.sort_every < 0) {
+        g_init_error = "invalid configuration or missing input array";
+        return PIC_ERR_INVALID;
+    }
+    const double dx = c.L / c.nx;
+    if (c.dt / dx > 64.0) {
+        g_init_error = "dt/dx > 64";
+        return PIC_ERR_INVALID;
+    }
+
+    pic_handle *h = new (std::nothrow) pic_handle();
+    if (!h) return PIC_ERR_NOMEM;
+    h->cfg = c;
+    h->stream = (cudaStream_t)stream;
+    h->M = c.nx;
+    h->K = c.degree;
+    h->np = c.np;
+    h->dx = dx;
+    h->fp32 = c.precision == PIC_FP32;
+    h->rsize = h->fp32 ? sizeof(float) : sizeof(double);
+    // |x^{n+1} - x^n| < dt because |p|/gamma < 1: at most ceil(dt/dx) cells
+    h->Dlim = (int)std::ceil(c.dt / dx) + 1;
+    h->H = h->K + h->Dlim + 2;
+    int rc = PIC_OK;
+    auto bail = [&](int code) {
+        g_init_error = h->err.empty() ? "pic_init failed" : h->err;
+        release(h);
+        delete h;
+        return code;
+    };
+
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(PIC_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+        return bail(PIC_ERR_CUDA);
+
+    const size_t np = (size_t)h->np, M = (size_t)h->M;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dalloc(h, &h->P[b].cell, np))) return bail(rc);
+        if ((rc = dalloc(h, (char **)&h->P[b].t, np * h->rsize))) return bail(rc);
+        if ((rc = dalloc(h, (char **)&h->P[b].p, np * h->rsize))) return bail(rc);
+        if ((rc = dalloc(h, &h->P[b].id, np))) return bail(rc);
+        if ((rc = dalloc(h, &h->jb[b], M))) return bail(rc);
+        if ((rc = dalloc(h, &h->sy[b], M))) return bail(rc);
+        if ((rc = dalloc(h, &h->sz[b], M))) return bail(rc);
+    }
+    if ((rc = dalloc(h, (char **)&h->delta, np * h->rsize))) return bail(rc);
+    if ((rc = dalloc(h, (char **)&h->pnew, np * h->rsize))) return bail(rc);
+    double **grid_arrays[] = {&h->ex, &h->ey, &h->ez, &h->ay, &h->az, &h->ek, &h->ebar, &h->ga_y,
+                              &h->ga_z, &h->eky, &h->ekz, &h->aky, &h->akz, &h->by, &h->bz,
+                              &h->r0y, &h->r0z, &h->rho, &h->work};
+    for (double **a : grid_arrays)
+        if ((rc = dalloc(h, a, M))) return bail(rc);
+    if ((rc = dalloc(h, &h->diag, 8))) return bail(rc);
+    if ((rc = dalloc(h, &h->counts, 2 * M))) return bail(rc);
+    if ((rc = dalloc(h, &h->ctrl, 1))) return bail(rc);
+    if (cudaMallocHost((void **)&h->h_flag, sizeof(int)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
+    if (cudaMallocHost((void **)&h->h_ctrl, sizeof(DevCtrl)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
+        return bail(PIC_ERR_CUDA);
+
+    // circulant bands: M0 (degree k), M1 (degree k-1), K = G^T M1 G, P = M0 +/- dt^2/4 K
+    const int K = h->K;
+    std::vector<double> m0(K + 1, 0.0), m1(K + 1, 0.0), kr(K + 1, 0.0), pp(K + 1), pm(K + 1);
+    mass_band(K, dx, m0.data());
+    mass_band(K - 1, dx, m1.data());
+    // K_d = (2 m1_d - m1_{d-1} - m1_{d+1}) / dx^2 with m1_{-d} = m1_d
+    auto m1at = [&](int d) { d = std::abs(d); return d <= K - 1 ? m1[d] : 0.0; };
+    for (int d = 0; d <= K; ++d) kr[d] = (2.0 * m1at(d) - m1at(d - 1) - m1at(d + 1)) / (dx * dx);
+    const double q = c.dt * c.dt / 4.0;
+    for (int d = 0; d <= K; ++d) { pp[d] = m0[d] + q * kr[d]; pm[d] = m0[d] - q * kr[d]; }
+    std::vector<double> gfull(M), taps(M);
+    if ((rc = dalloc(h, &h->d_rowM0, K + 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_rowM1, K + 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_rowK, K + 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_rowPm, K + 1))) return bail(rc);
+    cudaMemcpyAsync(h->d_rowM0, m0.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->d_rowM1, m1.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->d_rowK, kr.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->d_rowPm, pm.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream);
+    const double cut = 1e-19;
+    inverse_taps(m1.data(), K - 1, h->M, cut, gfull.data(), &h->tapM1_start, &h->tapM1_n, taps.data());
+    if ((rc = dalloc(h, &h->d_tapM1, h->tapM1_n))) return bail(rc);
+    if (cudaMemcpy(h->d_tapM1, taps.data(), sizeof(double) * h->tapM1_n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(PIC_ERR_CUDA);
+    inverse_taps(pp.data(), K, h->M, cut, gfull.data(), &h->tapP_start, &h->tapP_n, taps.data());
+    if ((rc = dalloc(h, &h->d_tapP, h->tapP_n))) return bail(rc);
+    if (cudaMemcpy(h->d_tapP, taps.data(), sizeof(double) * h->tapP_n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(PIC_ERR_CUDA);
+
+    // shared-memory budgets and persistent grid size
+    h->smem1 = sweep1_smem(h->M, h->H, h->fp32);
+    h->smem2 = sweep2_smem(h->M, h->H, h->fp32);
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (h->smem1 > (size_t)maxsm || h->smem2 > (size_t)maxsm) {
+        fail(h, PIC_ERR_INVALID, "grid too large for shared memory (%zu > %d)", h->smem1, maxsm);
+        return bail(PIC_ERR_INVALID);
+    }
+    // opt in to large dynamic shared memory (per kernel instantiation), then size the
+    // persistent sweep grids as SMs x resident blocks per SM
+    if (pic_set_smem_attrs(std::max(h->smem1, h->smem2), std::max(h->smem1, h->smem2),
+                           charge_smem(h->M, h->H)))
+        return bail(fail(h, PIC_ERR_CUDA, "cudaFuncSetAttribute failed"));
+    {
+        const int b1 = sweep_blocks_per_sm(h->K, h->fp32, 1, h->sweep_block, h->smem1);
+        const int b2 = sweep_blocks_per_sm(h->K, h->fp32, 2, h->sweep_block, h->smem2);
+        if (b1 < 1 || b2 < 1) return bail(fail(h, PIC_ERR_INVALID, "sweep kernels do not fit on an SM"));
+        h->sweep_grid = h->num_sms * std::min(b1, b2);
+    }
+
+    // inputs
+    {
+        double *dx_in = nullptr, *dp_in = nullptr;
+        const bool host = mem == PIC_MEM_HOST;
+        if (host) {
+            if ((rc = dalloc(h, &dx_in, np))) return bail(rc);
+            if ((rc = dalloc(h, &dp_in, np))) { cudaFree(dx_in); return bail(rc); }
+            cudaMemcpyAsync(dx_in, in->x, np * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            cudaMemcpyAsync(dp_in, in->p, np * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        }
+        const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        cudaMemcpyAsync(h->ay, in->ay, M * sizeof(double), kind, h->stream);
+        cudaMemcpyAsync(h->az, in->az, M * sizeof(double), kind, h->stream);
+        if (in->ey) cudaMemcpyAsync(h->ey, in->ey, M * sizeof(double), kind, h->stream);
+        else cudaMemsetAsync(h->ey, 0, M * sizeof(double), h->stream);
+        if (in->ez) cudaMemcpyAsync(h->ez, in->ez, M * sizeof(double), kind, h->stream);
+        else cudaMemsetAsync(h->ez, 0, M * sizeof(double), h->stream);
+        PartPtrs P0 = h->P[0];
+        P0.delta = h->delta;
+        P0.pnew = h->pnew;
+        launch_load(h->fp32, h->np, h->M, dx, host ? dx_in : in->x, host ? dp_in : in->p, P0,
+                    particle_grid(h), 256, h->stream);
+        cudaError_t e = cudaGetLastError();
+        if (host) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(dx_in);
+            cudaFree(dp_in);
+        }
+        if (e != cudaSuccess) return bail(fail(h, PIC_ERR_CUDA, "load: %s", cudaGetErrorString(e)));
+    }
+    if (launch_ctrl_reset(h->ctrl, h->stream) || cudaGetLastError() != cudaSuccess) return bail(PIC_ERR_CUDA);
+    h->cur = 0;
+    if ((rc = sort_markers(h))) return bail(rc);
+    if ((rc = solve_poisson(h))) return bail(rc);
+    if ((rc = sync(h))) return bail(rc);
+    *out = h;
+    return PIC_OK;
+}
+
+// ------------------------------------------------------------------ substeps
+static int check_status(pic_handle *h, int which)
+{
+    if (h->h_ctrl->status & STATUS_NUMERIC)
+        return fail(h, PIC_ERR_NUMERIC, "subsystem %d: non-finite value or displacement beyond c dt", which);
+    if (h->h_ctrl->status & STATUS_NOCONV)
+        return fail(h, PIC_ERR_NOCONVERGE, "subsystem %d: no convergence in %d sweeps", which,
+                    h->cfg.max_iter);
+    return PIC_OK;
+}
+
+static int timed_begin(pic_handle *h)
+{
+    if (h->timing) CK(cudaEventRecord(h->ev0, h->stream));
+    return PIC_OK;
+}
+
+static int timed_end(pic_handle *h, double *acc, long long *cnt)
+{
+    if (!h->timing) return PIC_OK;
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    *acc += ms;
+    ++*cnt;
+    return PIC_OK;
+}
+
+static int substep1(pic_handle *h, int *iters)
+{
+    int rc;
+    launch_prep1(h->M, h->dx, h->ex, h->ek, h->ebar, h->ay, h->az, h->ga_y, h->ga_z, h->jb[0],
+                 h->jb[1], h->ctrl, h->stream);
+    CKL();
+    Sweep1Args a{};
+    a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.np = h->np;
+    a.dx = h->dx; a.dt = h->cfg.dt; a.w = h->cfg.weight;
+    a.P = cur_parts(h);
+    a.ebar = h->ebar; a.ga_y = h->ga_y; a.ga_z = h->ga_z; a.ay = h->ay; a.az = h->az;
+    a.ctrl = h->ctrl;
+    ConvArgs c{};
+    c.M = h->M; c.d_start = h->tapM1_start; c.ntap = h->tapM1_n; c.mode = CONV_SOLVE1; c.ncomp = 1;
+    c.taps = h->d_tapM1;
+    c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
+    c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1.0 / (1 << 20);
+    c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 1; c.ctrl = h->ctrl;
+    int it = 0;
+    for (;;) {
+        a.j = h->jb[it & 1];
+        a.warm = (it == 0 && h->cfg.warm_start == PIC_WARM_EXPLICIT) ? 1 : 0;
+        if ((rc = timed_begin(h))) return rc;
+        if (launch_sweep1(a, h->sweep_grid, h->sweep_block, h->smem1, h->stream))
+            return fail(h, PIC_ERR_INVALID, "sweep1: bad degree");
+        CKL();
+        if ((rc = timed_end(h, &h->t_sw1, &h->n_sw1))) return rc;
+        h->marker_sweeps += h->np;
+        c.in[0] = h->jb[it & 1];
+        c.zero[0] = h->jb[(it + 1) & 1];
+        if ((rc = timed_begin(h))) return rc;
+        launch_conv(c, h->stream);
+        CKL();
+        if ((rc = timed_end(h, &h->t_solve, &h->n_solve))) return rc;
+        ++it;
+        if ((rc = read_ctrl(h))) return rc;
+        if (h->h_ctrl->converged) break;
+    }
+    if (iters) *iters = it;
+    if ((rc = check_status(h, 1))) return rc;
+    launch_finalize1(h->fp32, h->np, h->M, cur_parts(h), particle_grid(h), 256, h->stream);
+    CKL();
+    launch_copy(h->M, h->ek, h->ex, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, h->stream);
+    CKL();
+    return PIC_OK;
+}
+
+static int substep2(pic_handle *h, int *iters)
+{
+    int rc;
+    launch_prep2(h->M, h->K, h->cfg.dt, h->d_rowPm, h->d_rowK, h->ey, h->ez, h->ay, h->az, h->by,
+                 h->bz, h->eky, h->ekz, h->aky, h->akz, h->sy[0], h->sz[0], h->sy[1], h->sz[1],
+                 h->ctrl, h->stream);
+    CKL();
+    if ((rc = conv_plain(h, h->d_tapP, h->tapP_start, h->tapP_n, h->by, h->r0y, h->bz, h->r0z))) return rc;
+    Sweep2Args a{};
+    a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.w = h->cfg.weight;
+    a.P = cur_parts(h);
+    a.an_y = h->ay; a.an_z = h->az; a.ak_y = h->aky; a.ak_z = h->akz;
+    ConvArgs c{};
+    c.M = h->M; c.d_start = h->tapP_start; c.ntap = h->tapP_n; c.mode = CONV_SOLVE2; c.ncomp = 2;
+    c.taps = h->d_tapP;
+    c.en[0] = h->ey; c.en[1] = h->ez; c.ek[0] = h->eky; c.ek[1] = h->ekz;
+    c.aux[0] = h->aky; c.aux[1] = h->akz; c.an[0] = h->ay; c.an[1] = h->az;
+    c.r0[0] = h->r0y; c.r0[1] = h->r0z;
+    c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 0.0;
+    c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 2; c.ctrl = h->ctrl;
+    int it = 0;
+    for (;;) {
+        a.s_y = h->sy[it & 1];
+        a.s_z = h->sz[it & 1];
+        if ((rc = timed_begin(h))) return rc;
+        if (launch_sweep2(a, h->sweep_grid, h->sweep_block, h->smem2, h->stream))
+            return fail(h, PIC_ERR_INVALID, "sweep2: bad degree");
+        CKL();
+        if ((rc = timed_end(h, &h->t_sw2, &h->n_sw2))) return rc;
+        c.in[0] = h->sy[it & 1];
+        c.in[1] = h->sz[it & 1];
+        c.zero[0] = h->sy[(it + 1) & 1];
+        c.zero[1] = h->sz[(it + 1) & 1];
+        if ((rc = timed_begin(h))) return rc;
+        launch_conv(c, h->stream);
+        CKL();
+        if ((rc = timed_end(h, &h->t_solve, &h->n_solve))) return rc;
+        ++it;
+        if ((rc = read_ctrl(h))) return rc;
+        if (h->h_ctrl->converged) break;
+    }
+    if (iters) *iters = it;
+    if ((rc = check_status(h, 2))) return rc;
+    // a^{n+1} = a^n - dt/2 (e^n + e^{n+1}) is the last a^(k); e^{n+1} the last e^(k)
+    launch_copy(h->M, h->eky, h->ey, h->ekz, h->ez, h->aky, h->ay, h->akz, h->az, h->stream);
+    CKL();
+    return PIC_OK;
+}
+
+extern "C" int pic_substep(pic_handle *h, int32_t which, int32_t *iters)
+{
+    if (!h) return PIC_ERR_INVALID;
+    int it = 0, rc;
+    if (which == PIC_SUBSYSTEM_I) rc = substep1(h, &it);
+    else if (which == PIC_SUBSYSTEM_II) rc = substep2(h, &it);
+    else return fail(h, PIC_ERR_INVALID, "which must be 1 or 2");
+    if (iters) *iters = it;
+    if (rc) return rc;
+    return sync(h);
+}
+
+extern "C" int pic_step(pic_handle *h, int32_t nsteps, int64_t *iters_I, int64_t *iters_II)
+{
+    if (!h) return PIC_ERR_INVALID;
+    if (nsteps < 0) return fail(h, PIC_ERR_INVALID, "nsteps < 0");
+    long long s1 = 0, s2 = 0;
+    int rc = PIC_OK;
+    for (int n = 0; n < nsteps; ++n) {
+        int i1 = 0, i2 = 0;
+        if ((rc = substep1(h, &i1))) break;
+        if ((rc = substep2(h, &i2))) break;
+        s1 += i1;
+        s2 += i2;
+        ++h->steps_done;
+        if (h->cfg.sort_every > 0 && h->steps_done % h->cfg.sort_every == 0)
+            if ((rc = sort_markers(h))) break;
+    }
+    if (iters_I) *iters_I = s1;
+    if (iters_II) *iters_II = s2;
+    if (rc) return rc;
+    return sync(h);
+}
+
+// ------------------------------------------------------------------ diagnostics
+extern "C" int pic_energy(pic_handle *h, double out[6])
+{
+    if (!h || !out) return h ? fail(h, PIC_ERR_INVALID, "out is NULL") : PIC_ERR_INVALID;
+    int rc;
+    CK(cudaMemsetAsync(h->diag, 0, 8 * sizeof(double), h->stream));
+    if ((rc = deposit_charge(h, h->rho))) return rc;
+    DiagArgs a{};
+    a.M = h->M; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.dx = h->dx; a.w = h->cfg.weight;
+    a.P = cur_parts(h);
+    a.c0 = h->ay; a.c1 = h->az; a.acc = h->diag;
+    launch_kinetic(a, particle_grid(h), 256, h->stream);
+    CKL();
+    launch_energy_grid(h->M, h->K, h->dx, h->d_rowM0, h->d_rowM1, h->d_rowK, h->ex, h->ey, h->ez,
+                       h->ay, h->az, h->rho, h->diag, h->stream);
+    CKL();
+    double d[8];
+    CK(cudaMemcpyAsync(d, h->diag, sizeof(d), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out[0] = d[0];
+    out[1] = d[1];
+    out[2] = d[2];
+    out[3] = d[3];
+    out[4] = d[0] + d[1] + d[2] + d[3];
+    out[5] = d[5];
+    return PIC_OK;
+}
+
+extern "C" int pic_get_state(pic_handle *h, const pic_arrays *o, int32_t mem)
+{
+    if (!h || !o) return h ? fail(h, PIC_ERR_INVALID, "out is NULL") : PIC_ERR_INVALID;
+    if (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE) return fail(h, PIC_ERR_INVALID, "bad mem");
+    const size_t np = (size_t)h->np, M = (size_t)h->M;
+    const bool host = mem == PIC_MEM_HOST;
+    int rc = PIC_OK;
+    if (o->x || o->p) {
+        double *dx_out = o->x, *dp_out = o->p;
+        double *tx = nullptr, *tp = nullptr;
+        if (host) {
+            if (o->x && (rc = dalloc(h, &tx, np))) return rc;
+            if (o->p && (rc = dalloc(h, &tp, np))) { if (tx) cudaFree(tx); return rc; }
+            dx_out = tx;
+            dp_out = tp;
+        }
+        launch_store(h->fp32, h->np, h->dx, cur_parts(h), dx_out, dp_out, particle_grid(h), 256, h->stream);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && host) {
+            if (o->x) e = cudaMemcpyAsync(o->x, tx, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess && o->p)
+                e = cudaMemcpyAsync(o->p, tp, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            cudaError_t e2 = cudaStreamSynchronize(h->stream);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (tx) cudaFree(tx);
+        if (tp) cudaFree(tp);
+        if (e != cudaSuccess) return fail(h, PIC_ERR_CUDA, "get_state: %s", cudaGetErrorString(e));
+        ++h->launches;
+    }
+    const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    struct { double *dst; const double *src; } g[] = {
+        {o->ex, h->ex}, {o->ey, h->ey}, {o->ez, h->ez}, {o->ay, h->ay}, {o->az, h->az}};
+    for (auto &f : g)
+        if (f.dst) CK(cudaMemcpyAsync(f.dst, f.src, M * sizeof(double), kind, h->stream));
+    return sync(h);
+}
+
+extern "C" int pic_deposit(pic_handle *h, int32_t kind, const double *aux, double *out)
+{
+    if (!h) return PIC_ERR_INVALID;
+    if (!out) return fail(h, PIC_ERR_INVALID, "out is NULL");
+    int rc;
+    if (kind == PIC_DEP_CHARGE) {
+        if ((rc = deposit_charge(h, out))) return rc;
+        return sync(h);
+    }
+    if (kind == PIC_DEP_CURRENT) {
+        if (!aux) return fail(h, PIC_ERR_INVALID, "CURRENT needs the displacements");
+        CK(cudaMemsetAsync(out, 0, sizeof(double) * h->M, h->stream));
+        launch_ctrl_reset(h->ctrl, h->stream);
+        CKL();
+        CurrentArgs a{};
+        a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.np = h->np;
+        a.dx = h->dx; a.w = h->cfg.weight; a.P = cur_parts(h); a.disp = aux; a.out = out; a.ctrl = h->ctrl;
+        if (launch_current(a, particle_grid(h), 256, charge_smem(h->M, h->H), h->stream))
+            return fail(h, PIC_ERR_INVALID, "bad degree");
+        CKL();
+        if ((rc = read_ctrl(h))) return rc;
+        if (h->h_ctrl->status & STATUS_NUMERIC)
+            return fail(h, PIC_ERR_NUMERIC, "displacement beyond the halo or not finite");
+        return PIC_OK;
+    }
+    if (kind == PIC_DEP_SUSCEPT) {
+        if (!aux) return fail(h, PIC_ERR_INVALID, "SUSCEPT needs a*");
+        CK(cudaMemsetAsync(out, 0, sizeof(double) * 2 * h->M, h->stream));
+        Sweep2Args a{};
+        a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.w = h->cfg.weight;
+        a.P = cur_parts(h);
+        a.an_y = h->ay; a.an_z = h->az; a.ak_y = aux; a.ak_z = aux + h->M;
+        a.s_y = out; a.s_z = out + h->M;
+        if (launch_sweep2(a, h->sweep_grid, h->sweep_block, h->smem2, h->stream))
+            return fail(h, PIC_ERR_INVALID, "bad degree");
+        CKL();
+        return sync(h);
+    }
+    return fail(h, PIC_ERR_INVALID, "unknown deposit kind %d", kind);
+}
+
+extern "C" int pic_gather(pic_handle *h, int32_t field, double *out)
+{
+    if (!h) return PIC_ERR_INVALID;
+    if (!out) return fail(h, PIC_ERR_INVALID, "out is NULL");
+    const double *coef = nullptr;
+    int d = h->K;
+    switch (field) {
+    case PIC_FIELD_EX: coef = h->ex; d = h->K - 1; break;
+    case PIC_FIELD_EY: coef = h->ey; break;
+    case PIC_FIELD_EZ: coef = h->ez; break;
+    case PIC_FIELD_AY: coef = h->ay; break;
+    case PIC_FIELD_AZ: coef = h->az; break;
+    default: return fail(h, PIC_ERR_INVALID, "unknown field %d", field);
+    }
+    DiagArgs a{};
+    a.M = h->M; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.dx = h->dx; a.w = h->cfg.weight;
+    a.P = cur_parts(h);
+    a.c0 = coef;
+    a.out = out;
+    if (launch_gather(a, d, particle_grid(h), 256, h->stream)) return fail(h, PIC_ERR_INVALID, "bad degree");
+    CKL();
+    return sync(h);
+}
+
+extern "C" int pic_timing_enable(pic_handle *h, int32_t on)
+{
+    if (!h) return PIC_ERR_INVALID;
+    h->timing = on ? 1 : 0;
+    h->t_sw1 = h->t_sw2 = h->t_solve = 0.0;
+    h->n_sw1 = h->n_sw2 = h->n_solve = 0;
+    h->launches = 0;
+    h->marker_sweeps = 0;
+    return PIC_OK;
+}
+
+extern "C" int pic_timing_read(pic_handle *h, double out[8])
+{
+    if (!h || !out) return PIC_ERR_INVALID;
+    out[0] = h->t_sw1;
+    out[1] = (double)h->n_sw1;
+    out[2] = h->t_sw2;
+    out[3] = (double)h->n_sw2;
+    out[4] = h->t_solve;
+    out[5] = (double)h->n_solve;
+    out[6] = (double)h->launches;
+    out[7] = (double)h->marker_sweeps;
+    return PIC_OK;
+}
+
+extern "C" int pic_destroy(pic_handle *h)
+{
+    if (!h) return PIC_OK;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+    return PIC_OK;
+}
+
+extern "C" const char *pic_last_error(const pic_handle *h)
+{
+    if (!h) return g_init_error.c_str();
+    return h->err.c_str();
+}
+
+extern "C" const char *pic_version(void) { return kVersion; }

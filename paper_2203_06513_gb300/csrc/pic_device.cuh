@@ -1,0 +1,252 @@
+// pic_device.cuh -- device-side building blocks of libpic (sm_103a).
+//
+// Positions are stored as (cell c, offset t in [0,1)) in cell units: x = (c + t) dx.
+// In cell c the degree-d periodic basis functions j = c - r (r = 0..d) are nonzero
+// with values N^d(r + t), N^d the cardinal B-spline on the integer knots (Sec. 3.1:
+// Lambda^0_j = N^k_j, Lambda^1_j = N^{k-1}_j, supp N^d_j = [x_j, x_{j+d+1})).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+// ---------------------------------------------------------------------------
+// Device control block of one fixed-point loop.
+// Non-negative doubles are kept as their bit patterns so that integer atomicMax
+// orders them; NaN (0x7ff8...) compares above +Inf, so it reads "not converged".
+// ---------------------------------------------------------------------------
+struct DevCtrl {
+    unsigned long long dmax_bits;      // max particle increment of this sweep
+    unsigned long long emax_bits;      // max field increment of this sweep
+    unsigned long long dprev_bits;     // previous sweep's values (stagnation test)
+    unsigned long long eprev_bits;
+    int iter;                          // sweeps done in the current loop
+    int converged;                     // 1 once the test passed
+    int status;                        // error bits, see STATUS_*
+    unsigned int ticket;               // last-block election in multi-block grid kernels
+    double acc[4];                     // reductions for diagnostics (energy, residual)
+};
+
+enum : int {
+    STATUS_NUMERIC = 1,    // NaN/Inf or displacement beyond the halo
+    STATUS_NOCONV  = 2,
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v)
+{
+    // v >= 0 or NaN: the IEEE bit pattern is monotone in v for non-negative values
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double bits_to_double(unsigned long long b)
+{
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ int wrap_cell(int c, int M)
+{
+    c %= M;
+    return c < 0 ? c + M : c;
+}
+
+template <typename R> __device__ __forceinline__ R rsqrt_(R v);
+template <> __device__ __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ double rsqrt_(double v) { return rsqrt(v); }
+
+template <typename R> __device__ __forceinline__ R sqrt_(R v);
+template <> __device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
+
+template <typename R> __device__ __forceinline__ R floor_(R v);
+template <> __device__ __forceinline__ float floor_(float v) { return floorf(v); }
+template <> __device__ __forceinline__ double floor_(double v) { return ::floor(v); }
+
+// ---------------------------------------------------------------------------
+// Uniform B-spline values by the triangular (de Boor) scheme:
+// level 0: b = [1]; level n: b'_r = ((t + r) b_r + (n + 1 - t - r) b_{r-1}) / n,
+// with b_{-1} = b_n = 0.  After level d, v[r] = N^d(r + t), r = 0..d.
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__device__ __forceinline__ void bspline_vals(R t, R *v)
+{
+    v[0] = R(1);
+#pragma unroll
+    for (int n = 1; n <= D; ++n) {
+        const R inv = R(1) / R(n);
+        v[n] = (R(1) - t) * v[n - 1] * inv;
+#pragma unroll
+        for (int r = n - 1; r >= 1; --r)
+            v[r] = ((t + R(r)) * v[r] + (R(n + 1 - r) - t) * v[r - 1]) * inv;
+        v[0] = t * v[0] * inv;
+    }
+}
+
+// Same triangle, also returning the level D-2 and D-4 values (second and fourth
+// derivatives of the pieces by the derivative relation of Sec. 3.1 applied twice:
+// d^2/ds^2 N^D(s) = N^{D-2}(s) - 2 N^{D-2}(s-1) + N^{D-2}(s-2)).
+template <int D, typename R>
+__device__ __forceinline__ void bspline_vals_levels(R t, R *v, R *lv2, R *lv4)
+{
+    v[0] = R(1);
+    if (D == 2) lv2[0] = R(1);
+    if (D == 4) lv4[0] = R(1);
+#pragma unroll
+    for (int n = 1; n <= D; ++n) {
+        const R inv = R(1) / R(n);
+        v[n] = (R(1) - t) * v[n - 1] * inv;
+#pragma unroll
+        for (int r = n - 1; r >= 1; --r)
+            v[r] = ((t + R(r)) * v[r] + (R(n + 1 - r) - t) * v[r - 1]) * inv;
+        v[0] = t * v[0] * inv;
+        if (n == D - 2) {
+#pragma unroll
+            for (int r = 0; r <= (D - 2 > 0 ? D - 2 : 0); ++r) lv2[r] = v[r];
+        }
+        if (n == D - 4) {
+#pragma unroll
+            for (int r = 0; r <= (D - 4 > 0 ? D - 4 : 0); ++r) lv4[r] = v[r];
+        }
+    }
+}
+
+// Mean of the D+1 pieces N^D(r + t), r = 0..D, over the local interval centred at
+// tm with signed length h (|h| <= 1), exact for polynomials of degree <= 5:
+//   mean f = f(tm) + f''(tm) h^2 / 24 + f''''(tm) h^4 / 1920.
+// (Midpoint Taylor expansion of the interval mean; odd terms cancel.)
+template <int D, typename R>
+__device__ __forceinline__ void piece_means(R tm, R h, R *m)
+{
+    static_assert(D >= 0 && D <= 5, "degree");
+    if (D < 2) {
+        bspline_vals<D, R>(tm, m);
+        return;
+    }
+    R l2[D + 1 > 1 ? D + 1 : 1];
+    R l4[D + 1 > 1 ? D + 1 : 1];
+    bspline_vals_levels<D, R>(tm, m, l2, l4);
+    const R h2 = h * h * R(1.0 / 24.0);
+#pragma unroll
+    for (int r = 0; r <= D; ++r) {
+        // second difference of the level D-2 values (zero outside 0..D-2)
+        R a0 = (r <= D - 2) ? l2[r] : R(0);
+        R a1 = (r - 1 >= 0 && r - 1 <= D - 2) ? l2[r - 1] : R(0);
+        R a2 = (r - 2 >= 0 && r - 2 <= D - 2) ? l2[r - 2] : R(0);
+        m[r] += h2 * (a0 - R(2) * a1 + a2);
+    }
+    if (D >= 4) {
+        const R h4 = h * h * h * h * R(1.0 / 1920.0);
+#pragma unroll
+        for (int r = 0; r <= D; ++r) {
+            // fourth difference of the level D-4 values
+            R s = R(0);
+            const R c4[5] = {R(1), R(-4), R(6), R(-4), R(1)};
+#pragma unroll
+            for (int q = 0; q <= 4; ++q) {
+                int i = r - q;
+                if (i >= 0 && i <= D - 4) s += c4[q] * l4[i];
+            }
+            m[r] += h4 * s;
+        }
+    }
+}
+
+// Walk the straight path from local offset t0 (in cell 0) by the signed
+// displacement d (cell units), split at every knot (Sec. 4.2: the path integral
+// of Lambda_1 along x^n -> x^{n+1}).  For each piece, visit(c, h, m) gets the
+// cell c relative to the start cell, the signed piece length h (cells) and the
+// means m[r] of the degree-(K-1) pieces over it.  The path integral of
+// Lambda^1_{c0+c-r} over the piece is dx * h * m[r]; the path mean is the
+// sum over pieces of (h/d) m[r] (or m[r] itself for a single piece).
+// Returns the number of pieces.
+template <int K, typename R, class Visit>
+__device__ __forceinline__ int walk_path(R t0, R d, Visit &&visit)
+{
+    constexpr int D = K - 1;
+    R m[D + 1];
+    const R s = t0 + d;
+    const int cend = (int)floor_(s);
+    if (cend == 0) {
+        piece_means<D, R>(R(0.5) * (t0 + s), d, m);
+        visit(0, d, m, true);
+        return 1;
+    }
+    int n = 0;
+    if (cend > 0) {
+        piece_means<D, R>(R(0.5) * (t0 + R(1)), R(1) - t0, m);
+        visit(0, R(1) - t0, m, false); ++n;
+        for (int c = 1; c < cend; ++c) {
+            piece_means<D, R>(R(0.5), R(1), m);
+            visit(c, R(1), m, false); ++n;
+        }
+        const R tl = s - R(cend);
+        if (tl > R(0)) {
+            piece_means<D, R>(R(0.5) * tl, tl, m);
+            visit(cend, tl, m, false); ++n;
+        }
+    } else {
+        if (t0 > R(0)) {
+            piece_means<D, R>(R(0.5) * t0, -t0, m);
+            visit(0, -t0, m, false); ++n;
+        }
+        for (int c = -1; c > cend; --c) {
+            piece_means<D, R>(R(0.5), R(-1), m);
+            visit(c, R(-1), m, false); ++n;
+        }
+        const R tl = s - R(cend);          // in [0,1): the piece runs from 1 down to tl
+        piece_means<D, R>(R(0.5) * (R(1) + tl), tl - R(1), m);
+        visit(cend, tl - R(1), m, false); ++n;
+    }
+    return n;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = (w > v || w != w) ? w : v;       // NaN wins
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide max of a non-negative double, then one atomicMax per block.
+__device__ __forceinline__ void block_max_to(unsigned long long *dst, double v, double *s_red)
+{
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double u = lane < nw ? s_red[lane] : 0.0;
+        u = warp_max(u);
+        if (lane == 0) atomic_max_nonneg(dst, u);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void block_sum_to(double *dst, double v, double *s_red)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double u = lane < nw ? s_red[lane] : 0.0;
+        u = warp_sum(u);
+        if (lane == 0) atomicAdd(dst, u);
+    }
+    __syncthreads();
+}
+
+}  // namespace pic

@@ -1,0 +1,419 @@
+// pic_grid.cu -- grid-side kernels of libpic (double precision) and the host
+// algebra of the periodic spline matrices.
+//
+// Every matrix of the method is a symmetric circulant on M nodes (Sec. 3.1):
+//   M0 (degree k), M1 (degree k-1), K = G^T M1 G, P = M0 + dt^2/4 K.
+// Solves apply the exact inverse as a circulant convolution: the inverse of a
+// banded SPD circulant has a first row that decays geometrically, so it is
+// truncated where its entries fall below 1e-19 of the largest (or kept whole).
+#include <cmath>
+#include <vector>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+// ---------------------------------------------------------------------------
+// Host: exact mass-matrix bands.  (M_d)_{0,r} = int N^d(s) N^d(s - r) ds * dx,
+// the autocorrelation of the cardinal B-spline, equals dx N^{2d+1}(d + 1 + r).
+// N^n is evaluated from the truncated-power form
+//   N^n(s) = 1/n! sum_{i=0}^{n+1} (-1)^i C(n+1, i) (s - i)_+^n,
+// exact in rational arithmetic; at the integer arguments used here every term
+// is an integer divided by n!, so double evaluation is exact for n <= 11.
+// ---------------------------------------------------------------------------
+static double cardinal_tp(int n, double s)
+{
+    double acc = 0.0, binom = 1.0, fact = 1.0;
+    for (int i = 1; i <= n; ++i) fact *= i;
+    for (int i = 0; i <= n + 1; ++i) {
+        const double u = s - i;
+        if (u > 0.0) acc += ((i & 1) ? -1.0 : 1.0) * binom * std::pow(u, n);
+        binom = binom * (n + 1 - i) / (i + 1);
+    }
+    return acc / fact;
+}
+
+void mass_band(int d, double dx, double *band)
+{
+    for (int r = 0; r <= d; ++r) band[r] = dx * cardinal_tp(2 * d + 1, (double)(d + 1 + r));
+}
+
+// First row g of the inverse of the symmetric circulant with band c_0..c_bw:
+// eigenvalues lambda_m = c_0 + 2 sum_d c_d cos(2 pi m d / M), g_d = 1/M sum_m
+// cos(2 pi m d / M) / lambda_m, with one step of iterative refinement.
+void inverse_taps(const double *band, int bw, int M, double cut, double *g, int *d_start,
+                  int *ntap, double *taps)
+{
+    const double twopi = 6.283185307179586476925286766559;
+    std::vector<double> cs(M), lam(M), r(M), corr(M);
+    for (int m = 0; m < M; ++m) cs[m] = std::cos(twopi * (double)m / (double)M);
+    for (int m = 0; m < M; ++m) {
+        double l = band[0];
+        for (int d = 1; d <= bw; ++d) l += 2.0 * band[d] * cs[(long long)m * d % M];
+        lam[m] = 1.0 / l;
+    }
+    auto apply_inv = [&](const std::vector<double> &rhs_even, std::vector<double> &out) {
+        // rhs is symmetric (even) so its DFT is real: R_m = sum_q rhs_q cos(2 pi m q / M)
+        std::vector<double> R(M);
+        for (int m = 0; m < M; ++m) {
+            double s = 0.0, comp = 0.0;
+            for (int q = 0; q < M; ++q) {
+                const double y = rhs_even[q] * cs[(long long)m * q % M] - comp;
+                const double tt = s + y;
+                comp = (tt - s) - y;
+                s = tt;
+            }
+            R[m] = s * lam[m];
+        }
+        for (int d = 0; d < M; ++d) {
+            double s = 0.0, comp = 0.0;
+            for (int m = 0; m < M; ++m) {
+                const double y = R[m] * cs[(long long)m * d % M] - comp;
+                const double tt = s + y;
+                comp = (tt - s) - y;
+                s = tt;
+            }
+            out[d] = s / (double)M;
+        }
+    };
+    std::vector<double> e0(M, 0.0), gv(M);
+    e0[0] = 1.0;
+    apply_inv(e0, gv);
+    // refinement: r = e0 - A g, g += A^{-1} r
+    for (int i = 0; i < M; ++i) {
+        double s = band[0] * gv[i];
+        for (int d = 1; d <= bw; ++d) s += band[d] * (gv[(i + d) % M] + gv[(i - d + M) % M]);
+        r[i] = e0[i] - s;
+    }
+    apply_inv(r, corr);
+    for (int i = 0; i < M; ++i) gv[i] += corr[i];
+    for (int i = 0; i < M; ++i) g[i] = gv[i];
+    double gmax = 0.0;
+    for (int i = 0; i < M; ++i) gmax = std::fmax(gmax, std::fabs(gv[i]));
+    int T = 0;
+    for (int d = 1; d <= M / 2; ++d)
+        if (std::fabs(gv[d]) > cut * gmax) T = d;
+    if (2 * T + 1 <= M && !(M % 2 == 0 && T == M / 2)) {
+        *d_start = -T;
+        *ntap = 2 * T + 1;
+        for (int n = 0; n < 2 * T + 1; ++n) taps[n] = gv[(n - T + M) % M];
+    } else {  // whole circulant: offsets -(M/2 - 1) .. M/2 (M entries)
+        const int lo = -(M / 2 - 1 + (M % 2));
+        *d_start = lo;
+        *ntap = M;
+        for (int n = 0; n < M; ++n) taps[n] = gv[((lo + n) % M + M) % M];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Convergence decision, made by the last block of a solve kernel.
+// FP64 form (Sec. 5, tolerance tol): max |x^(k+1) - x^(k)| <= tol (length) and
+// max |e^(k+1) - e^(k)| <= tol.  FP32 form: position increments at the float
+// resolution of the offset (dtol, relative to max(1, |delta|)) and field
+// increments below tol or no longer shrinking (stagnation at float noise).
+// ---------------------------------------------------------------------------
+__device__ void decide(const ConvArgs &A)
+{
+    DevCtrl *c = A.ctrl;
+    __threadfence();
+    const double d = (A.subsystem == 1) ? bits_to_double(c->dmax_bits) : 0.0;
+    const double e = bits_to_double(c->emax_bits);
+    const double ep = bits_to_double(c->eprev_bits);
+    c->iter += 1;
+    bool ok;
+    if (!A.fp32) {
+        ok = (d * A.dx <= A.tol) && (e <= A.tol);
+    } else {
+        const bool dok = (A.subsystem == 1) ? (d <= A.dtol) : true;
+        ok = dok && ((e <= A.tol) || (c->iter >= 3 && e >= 0.25 * ep && e <= 1e-6));
+    }
+    bool stop = ok;
+    if (!ok && c->iter >= A.max_iter) {
+        c->status |= STATUS_NOCONV;
+        stop = true;
+    }
+    if (c->status & STATUS_NUMERIC) stop = true;
+    c->converged = stop ? 1 : 0;
+    c->dprev_bits = c->dmax_bits;
+    c->eprev_bits = c->emax_bits;
+    c->dmax_bits = 0ull;
+    c->emax_bits = 0ull;
+    c->ticket = 0u;
+    __threadfence();
+}
+
+// y_i = sum_n taps[n] in[(i - (d_start + n)) mod M], one output per thread,
+// input and taps staged in shared memory (input twice, so no index wraps).
+__global__ void __launch_bounds__(64) k_conv(ConvArgs A)
+{
+    extern __shared__ __align__(16) double s_conv[];
+    __shared__ double s_red[32];
+    const int M = A.M;
+    const int comp = blockIdx.y;
+    double *s_in = s_conv;              // 2M
+    double *s_tap = s_conv + 2 * M;     // ntap
+    const double *in = A.in[comp];
+    const int off = M / 2;              // s_in[q] = in[(q - off) mod M], q in [0, 2M)
+    for (int q = threadIdx.x; q < 2 * M; q += blockDim.x) {
+        int g = q - off;
+        g = g < 0 ? g + M : (g >= M ? g - M : g);
+        s_in[q] = in[g];
+    }
+    for (int n = threadIdx.x; n < A.ntap; n += blockDim.x) s_tap[n] = A.taps[n];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double diff = 0.0;
+    if (i < M) {
+        // offsets d = d_start + n lie in [-(M-1)/2, M/2], so i - d + off is in [0, 2M)
+        const double *base = s_in + (i - A.d_start + off);
+        double acc0 = 0.0, acc1 = 0.0;
+        int n = 0;
+        for (; n + 1 < A.ntap; n += 2) {
+            acc0 = fma(s_tap[n], base[-n], acc0);
+            acc1 = fma(s_tap[n + 1], base[-n - 1], acc1);
+        }
+        if (n < A.ntap) acc0 = fma(s_tap[n], base[-n], acc0);
+        const double y = acc0 + acc1;
+        if (A.mode == CONV_PLAIN) {
+            A.out[comp][i] = y;
+        } else if (A.mode == CONV_SOLVE1) {
+            const double en = A.en[0][i];
+            const double enew = en - y;                  // e^(k+1) = e^n - M1^{-1} j
+            diff = fabs(enew - A.ek[0][i]);
+            A.ek[0][i] = enew;
+            A.aux[0][i] = 0.5 * (en + enew);             // ebar for the next sweep
+            A.zero[0][i] = 0.0;
+        } else {                                         // CONV_SOLVE2
+            const double en = A.en[comp][i];
+            const double enew = A.r0[comp][i] + A.dt * y;   // P e^(k+1) = b + dt s
+            diff = fabs(enew - A.ek[comp][i]);
+            A.ek[comp][i] = enew;
+            A.aux[comp][i] = A.an[comp][i] - 0.5 * A.dt * (en + enew);   // a^(k+1)
+            A.zero[comp][i] = 0.0;
+        }
+    }
+    if (A.mode == CONV_PLAIN) return;
+    block_max_to(&A.ctrl->emax_bits, diff, s_red);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int nblk = gridDim.x * gridDim.y;
+        const unsigned int t = atomicAdd(&A.ctrl->ticket, 1u);
+        if (t == nblk - 1) decide(A);
+    }
+}
+
+int launch_conv(const ConvArgs &a, cudaStream_t s)
+{
+    const int threads = 64;
+    dim3 grid((a.M + threads - 1) / threads, a.ncomp);
+    const size_t smem = (2 * (size_t)a.M + (size_t)a.ntap) * sizeof(double);
+    k_conv<<<grid, threads, smem, s>>>(a);
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Subsystem I preparation: (G a)_i = (a_i - a_{i-1}) / dx, e^(0) = e^n,
+// ebar = e^n, cleared deposit buffers, reset control block.
+// ---------------------------------------------------------------------------
+__global__ void k_prep1(int M, double dx, const double *ex, double *ek, double *ebar,
+                        const double *ay, const double *az, double *gay, double *gaz,
+                        double *j0, double *j1, DevCtrl *ctrl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) {
+        const int im = (i == 0) ? M - 1 : i - 1;
+        gay[i] = (ay[i] - ay[im]) / dx;
+        gaz[i] = (az[i] - az[im]) / dx;
+        ek[i] = ex[i];
+        ebar[i] = ex[i];
+        j0[i] = 0.0;
+        j1[i] = 0.0;
+    }
+    if (i == 0) {
+        ctrl->dmax_bits = 0ull;
+        ctrl->emax_bits = 0ull;
+        ctrl->dprev_bits = 0x7ff0000000000000ull;
+        ctrl->eprev_bits = 0x7ff0000000000000ull;
+        ctrl->iter = 0;
+        ctrl->converged = 0;
+        ctrl->ticket = 0u;
+    }
+}
+
+int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, const double *ay,
+                 const double *az, double *ga_y, double *ga_z, double *j0, double *j1,
+                 DevCtrl *ctrl, cudaStream_t s)
+{
+    k_prep1<<<(M + 255) / 256, 256, 0, s>>>(M, dx, ex, ek, ebar, ay, az, ga_y, ga_z, j0, j1, ctrl);
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Subsystem II preparation: b = (M0 - dt^2/4 K) e^n + dt K a^n (banded
+// circulant products), e^(0) = e^n, a^(0) = a^n - dt e^n, cleared deposits.
+// ---------------------------------------------------------------------------
+__global__ void k_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
+                        const double *ey, const double *ez, const double *ay, const double *az,
+                        double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
+                        double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) {
+        double vy = rowPm[0] * ey[i] + dt * rowK[0] * ay[i];
+        double vz = rowPm[0] * ez[i] + dt * rowK[0] * az[i];
+        for (int d = 1; d <= K; ++d) {
+            const int ip = (i + d) % M, im = (i - d + M) % M;
+            vy += rowPm[d] * (ey[ip] + ey[im]) + dt * rowK[d] * (ay[ip] + ay[im]);
+            vz += rowPm[d] * (ez[ip] + ez[im]) + dt * rowK[d] * (az[ip] + az[im]);
+        }
+        by[i] = vy;
+        bz[i] = vz;
+        eky[i] = ey[i];
+        ekz[i] = ez[i];
+        aky[i] = ay[i] - dt * ey[i];
+        akz[i] = az[i] - dt * ez[i];
+        s00[i] = 0.0; s01[i] = 0.0; s10[i] = 0.0; s11[i] = 0.0;
+    }
+    if (i == 0) {
+        ctrl->dmax_bits = 0ull;
+        ctrl->emax_bits = 0ull;
+        ctrl->dprev_bits = 0x7ff0000000000000ull;
+        ctrl->eprev_bits = 0x7ff0000000000000ull;
+        ctrl->iter = 0;
+        ctrl->converged = 0;
+        ctrl->ticket = 0u;
+    }
+}
+
+int launch_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
+                 const double *ey, const double *ez, const double *ay, const double *az,
+                 double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
+                 double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl, cudaStream_t s)
+{
+    k_prep2<<<(M + 255) / 256, 256, 0, s>>>(M, K, dt, rowPm, rowK, ey, ez, ay, az, by, bz, eky, ekz,
+                                            aky, akz, s00, s01, s10, s11, ctrl);
+    return 0;
+}
+
+__global__ void k_copy4(int M, const double *s0, double *d0, const double *s1, double *d1,
+                        const double *s2, double *d2, const double *s3, double *d3)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) {
+        if (s0) d0[i] = s0[i];
+        if (s1) d1[i] = s1[i];
+        if (s2) d2[i] = s2[i];
+        if (s3) d3[i] = s3[i];
+    }
+}
+
+int launch_copy(int M, const double *src0, double *dst0, const double *src1, double *dst1,
+                const double *src2, double *dst2, const double *src3, double *dst3, cudaStream_t s)
+{
+    k_copy4<<<(M + 255) / 256, 256, 0, s>>>(M, src0, dst0, src1, dst1, src2, dst2, src3, dst3);
+    return 0;
+}
+
+// Discrete Poisson right side: with r = -rho + dx, d = M1 e_x solves
+// (d_j - d_{j+1}) / dx = r_j (Remark 2, Sec. 4.2): a running sum made mean-free.
+__global__ void k_poisson_rhs(int M, double dx, const double *rho, double *d)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double run = 0.0, sum = 0.0;
+    for (int j = 0; j < M; ++j) {
+        d[j] = run;
+        sum += run;
+        run -= dx * (dx - rho[j]);
+    }
+    const double mean = sum / M;
+    for (int j = 0; j < M; ++j) d[j] -= mean;
+}
+
+int launch_poisson_rhs(int M, double dx, const double *rho, double *d, cudaStream_t s)
+{
+    k_poisson_rhs<<<1, 32, 0, s>>>(M, dx, rho, d);
+    return 0;
+}
+
+// Field energies (Eq. discrete_H) and the Gauss-law residual (Remark 2, Sec. 4.2).
+__global__ void k_energy_grid(int M, int K, double dx, const double *rowM0, const double *rowM1,
+                              const double *rowK, const double *ex, const double *ey,
+                              const double *ez, const double *ay, const double *az,
+                              const double *rho, double *diag)
+{
+    __shared__ double s_red[32];
+    double eex = 0.0, eperp = 0.0, aperp = 0.0, gres = 0.0;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        double m1e = rowM1[0] * ex[i], m1e_next = 0.0;
+        const int inx = (i + 1) % M;
+        m1e_next = rowM1[0] * ex[inx];
+        for (int d = 1; d <= K - 1; ++d) {
+            m1e += rowM1[d] * (ex[(i + d) % M] + ex[(i - d + M) % M]);
+            m1e_next += rowM1[d] * (ex[(inx + d) % M] + ex[(inx - d + M) % M]);
+        }
+        double m0y = rowM0[0] * ey[i], m0z = rowM0[0] * ez[i];
+        double ky = rowK[0] * ay[i], kz = rowK[0] * az[i];
+        for (int d = 1; d <= K; ++d) {
+            const int ip = (i + d) % M, im = (i - d + M) % M;
+            m0y += rowM0[d] * (ey[ip] + ey[im]);
+            m0z += rowM0[d] * (ez[ip] + ez[im]);
+            ky += rowK[d] * (ay[ip] + ay[im]);
+            kz += rowK[d] * (az[ip] + az[im]);
+        }
+        eex += 0.5 * ex[i] * m1e;
+        eperp += 0.5 * (ey[i] * m0y + ez[i] * m0z);
+        aperp += 0.5 * (ay[i] * ky + az[i] * kz);
+        const double r = (m1e - m1e_next) / dx + rho[i] - dx;
+        gres = fmax(gres, fabs(r));
+    }
+    double v;
+    v = warp_sum(eex);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) { double s = 0; for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w]; diag[1] = s; }
+    __syncthreads();
+    v = warp_sum(eperp);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) { double s = 0; for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w]; diag[2] = s; }
+    __syncthreads();
+    v = warp_sum(aperp);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) { double s = 0; for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w]; diag[3] = s; }
+    __syncthreads();
+    v = warp_max(gres);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) { double s = 0; for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, s_red[w]); diag[5] = s; }
+}
+
+int launch_energy_grid(int M, int K, double dx, const double *rowM0, const double *rowM1,
+                       const double *rowK, const double *ex, const double *ey, const double *ez,
+                       const double *ay, const double *az, const double *rho, double *diag,
+                       cudaStream_t s)
+{
+    k_energy_grid<<<1, 256, 0, s>>>(M, K, dx, rowM0, rowM1, rowK, ex, ey, ez, ay, az, rho, diag);
+    return 0;
+}
+
+__global__ void k_ctrl_reset(DevCtrl *c)
+{
+    c->dmax_bits = 0ull;
+    c->emax_bits = 0ull;
+    c->dprev_bits = 0x7ff0000000000000ull;
+    c->eprev_bits = 0x7ff0000000000000ull;
+    c->iter = 0;
+    c->converged = 0;
+    c->status = 0;
+    c->ticket = 0u;
+    c->acc[0] = c->acc[1] = c->acc[2] = c->acc[3] = 0.0;
+}
+
+int launch_ctrl_reset(DevCtrl *ctrl, cudaStream_t s)
+{
+    k_ctrl_reset<<<1, 1, 0, s>>>(ctrl);
+    return 0;
+}
+
+}  // namespace pic

@@ -1,0 +1,121 @@
+// pic_internal.h -- launchers shared by the translation units of libpic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+// ---------------------------------------------------------------- particles
+struct PartPtrs {
+    int32_t *cell;      // cell index in [0, M)
+    void *t;            // offset in [0,1): float or double
+    void *p;            // momentum
+    void *delta;        // subsystem-I iterate: displacement x^(k) - x^n, cell units
+    void *pnew;         // subsystem-I iterate p^(k+1)
+    int64_t *id;        // caller index of each stored marker
+};
+
+struct Sweep1Args {
+    int M, H, Dlim, K, fp32;
+    long long np;
+    double dx, dt, w;
+    PartPtrs P;
+    const double *ebar, *ga_y, *ga_z, *ay, *az;
+    double *j;
+    DevCtrl *ctrl;
+    int warm;           // 1: delta^(0) = explicit predictor, computed in-kernel
+};
+
+struct Sweep2Args {
+    int M, H, K, fp32;
+    long long np;
+    double w;
+    PartPtrs P;
+    const double *an_y, *an_z, *ak_y, *ak_z;
+    double *s_y, *s_z;
+};
+
+struct CurrentArgs {
+    int M, H, Dlim, K, fp32;
+    long long np;
+    double dx, w;
+    PartPtrs P;
+    const double *disp;     // caller order, length units
+    double *out;
+    DevCtrl *ctrl;
+};
+
+struct DiagArgs {
+    int M, K, fp32;
+    long long np;
+    double dx, w;
+    PartPtrs P;
+    const double *c0, *c1;  // field coefficients (gather: c0; kinetic: a_y, a_z)
+    double *out;            // gather output (caller order) or rho
+    double *acc;            // kinetic sum
+};
+
+int launch_sweep1(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s);
+size_t sweep1_smem(int M, int H, int fp32);
+int launch_sweep2(const Sweep2Args &a, int grid, int block, size_t smem, cudaStream_t s);
+size_t sweep2_smem(int M, int H, int fp32);
+int launch_current(const CurrentArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+int launch_charge(const DiagArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+size_t charge_smem(int M, int H);
+int launch_gather(const DiagArgs &a, int field_degree, int grid, int block, cudaStream_t s);
+int launch_kinetic(const DiagArgs &a, int grid, int block, cudaStream_t s);
+int launch_finalize1(int fp32, long long np, int M, PartPtrs P, int grid, int block, cudaStream_t s);
+int launch_load(int fp32, long long np, int M, double dx, const double *x, const double *p,
+                PartPtrs P, int grid, int block, cudaStream_t s);
+int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, double *p,
+                 int grid, int block, cudaStream_t s);
+int sweep_blocks_per_sm(int K, int fp32, int which, int block, size_t smem);
+int launch_sort(int fp32, long long np, int M, PartPtrs src, PartPtrs dst, int32_t *counts,
+                int grid, int block, cudaStream_t s);
+
+// ---------------------------------------------------------------- grid
+enum ConvMode { CONV_PLAIN = 0, CONV_SOLVE1 = 1, CONV_SOLVE2 = 2 };
+
+struct ConvArgs {
+    int M, d_start, ntap, mode, ncomp;
+    const double *taps;
+    const double *in[2];
+    double *out[2];
+    const double *en[2];    // e^n
+    double *ek[2];          // e^(k) (in: previous, out: new)
+    double *aux[2];         // SOLVE1: ebar out; SOLVE2: a^(k) out
+    const double *an[2];    // SOLVE2: a^n
+    const double *r0[2];    // SOLVE2: P^{-1} b
+    double *zero[2];        // deposit buffers of the next sweep, cleared here
+    double dt, dx, tol, dtol;
+    int max_iter, fp32, subsystem;
+    DevCtrl *ctrl;
+    unsigned long long cond_handle;   // graph conditional handle (0: none)
+};
+
+int launch_conv(const ConvArgs &a, cudaStream_t s);
+int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, const double *ay,
+                 const double *az, double *ga_y, double *ga_z, double *j0, double *j1,
+                 DevCtrl *ctrl, cudaStream_t s);
+int launch_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
+                 const double *ey, const double *ez, const double *ay, const double *az,
+                 double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
+                 double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl, cudaStream_t s);
+int launch_copy(int M, const double *src0, double *dst0, const double *src1, double *dst1,
+                const double *src2, double *dst2, const double *src3, double *dst3, cudaStream_t s);
+int launch_poisson_rhs(int M, double dx, const double *rho, double *d, cudaStream_t s);
+int launch_energy_grid(int M, int K, double dx, const double *rowM0, const double *rowM1,
+                       const double *rowK, const double *ex, const double *ey, const double *ez,
+                       const double *ay, const double *az, const double *rho, double *diag,
+                       cudaStream_t s);
+int launch_ctrl_reset(DevCtrl *ctrl, cudaStream_t s);
+
+// host-side spline algebra (exact rows and inverse taps of the circulant matrices)
+void mass_band(int d, double dx, double *band /* d+1 */);
+void inverse_taps(const double *band, int bw, int M, double cut, double *g_full /* M */,
+                  int *d_start, int *ntap, double *taps /* M */);
+
+}  // namespace pic
