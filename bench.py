@@ -1,0 +1,322 @@
+"""Benchmark: particle-steps/s of the energy-conserving PIC step on one GB300.
+
+Workload (default): L = 4 pi, M = 2048 cells, cubic splines, N_p = 1e8 markers,
+density 1 + 0.01 cos(0.5 x), Maxwellian p with v_th = 0.1, pump A_y = 0.2 cos(2x),
+dt = 0.05 -- float particle state with double grid accumulation, solves and
+energy sums ("FP32" form), beside the plain all-double form on the same shape.
+A step is one full Lie--Trotter step (subsystem I then II, every fixed-point
+sweep included).  Inputs are synthetic and seeded; markers (1.2-2 GB) exceed
+the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances an
+independent replica (seed + rank): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import os
+
+# the CPU baseline (oracle) is timed single-threaded, BLAS included
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import math
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_06513_gb300 import inputs as I  # noqa: E402
+
+METRIC = "particle-steps/s at rel. energy err ≤1e-10: FP32+learned vs plain FP64"
+UNIT = "particle-steps/s"
+WORKLOAD = "C2"
+# algorithmic bytes per marker per subsystem-I sweep: read cell, offset, p, delta;
+# write delta, p_new (float form 6 x 4 B; double form 4 + 5 x 8 B)
+BYTES_SWEEP1 = {1: 24, 0: 44}
+BYTES_SWEEP2 = {1: 12, 0: 20}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_form(pic, torch, w, precision, warm, steps, warmup, stream, timing=True):
+    """Advance one replica; returns timings and diagnostics."""
+    x, p = I.particles(w)
+    ay, az, ey, ez = I.fields(w)
+    tol = 1e-13 if precision == pic.PIC_FP64 else 1e-13
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=8, tol=tol)
+    g = pic.Pic(cfg, x, p, ay, az, ey, ez, stream=stream.cuda_stream)
+    del x, p
+    H0 = g.energy()["total"]
+    it_warm = g.step(warmup)
+    g.timing_enable(timing)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    it = g.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    tr = g.timing_read()
+    E = g.energy()
+    g.close()
+    return {"ms": ms, "iters": it, "iters_warm": it_warm, "timing": tr, "H0": H0, "H": E["total"],
+            "gauss": E["gauss"], "rel_energy_err": abs(E["total"] - H0) / abs(H0)}
+
+
+def e2e_run(pic, torch, w, precision, warm, steps, stream):
+    """Whole job through the public API with host buffers: pic_init from pinned
+    host arrays (H2D), `steps` steps, pic_get_state back to pinned host (D2H)."""
+    x, p = I.particles(w)
+    ay, az, ey, ez = I.fields(w)
+    hx = torch.from_numpy(x).pin_memory().numpy()
+    hp = torch.from_numpy(p).pin_memory().numpy()
+    del x, p
+    out = {k: torch.empty(w.np, dtype=torch.float64).pin_memory().numpy() for k in ("x", "p")}
+    out.update({k: np.empty(w.nx) for k in ("ex", "ey", "ez", "ay", "az")})
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = pic.Pic(cfg, hx, hp, ay, az, ey, ez, stream=stream.cuda_stream)
+    g.step(steps)
+    g.get_state(**out)
+    t1 = time.perf_counter()
+    g.close()
+    h2d = 2 * 8 * w.np + 4 * 8 * w.nx
+    d2h = 2 * 8 * w.np + 5 * 8 * w.nx
+    return {"s": t1 - t0, "h2d": h2d, "d2h": d2h}
+
+
+def reference_arm(args, ws, rank):
+    """The oracle (plain FP64 CPU program of the same scheme) on a bounded sample
+    of the workload: same grid, fewer markers, two steps."""
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    w = I.workload(WORKLOAD)
+    n_sample = int(os.environ.get("PIC_REF_SAMPLE", "200000"))
+    steps = max(1, min(args.steps, 2))
+    ws_ = I.workload(WORKLOAD, np=n_sample)
+    x, p = I.particles(ws_)
+    ay, az, ey, ez = I.fields(ws_)
+    orc = O.Oracle(w.L, w.nx, w.degree, ws_.weight, w.dt, w.tol, w.max_iter)
+    s = O.initial_state(orc, x, p, ay, az, ey, ez)
+    for _ in range(max(0, min(args.warmup, 1))):
+        s = orc.step(s)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s = orc.step(s)
+    dt = time.perf_counter() - t0
+    v = n_sample * steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: L=4pi, M=2048, k=3, Np=1e8, dt=0.05 (oracle sample)",
+                       "sample_np": n_sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_sample} markers on the M=2048 grid, {steps} steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(args):
+    from oracle import oracle as O
+    w = I.workload(WORKLOAD)
+    n_sample = int(os.environ.get("PIC_CPU_SAMPLE", "100000"))
+    ws_ = I.workload(WORKLOAD, np=n_sample)
+    x, p = I.particles(ws_)
+    ay, az, ey, ez = I.fields(ws_)
+    orc = O.Oracle(w.L, w.nx, w.degree, ws_.weight, w.dt, w.tol, w.max_iter)
+    s = O.initial_state(orc, x, p, ay, az, ey, ez)
+    t0 = time.perf_counter()
+    s = orc.step(s)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_sample} markers on the M=2048 grid, 1 step (single thread)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="libpic", choices=["libpic", "reference"])
+    ap.add_argument("--np", type=float, default=None, help="override N_p (smaller runs)")
+    ap.add_argument("--warm", default="explicit", choices=["none", "explicit", "mlp"])
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, ws, rank)
+
+    import torch
+    from paper_2203_06513_gb300 import pic
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = I.workload(WORKLOAD, seed=rank)
+    if args.np:
+        w = I.workload(WORKLOAD, seed=rank, np=int(args.np))
+    warm = {"none": pic.PIC_WARM_NONE, "explicit": pic.PIC_WARM_EXPLICIT,
+            "mlp": pic.PIC_WARM_MLP}[args.warm]
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    r32 = run_form(pic, torch, w, pic.PIC_FP32, warm, args.steps, args.warmup, stream)
+    clk = clocks.stop()
+    barrier()
+    k64 = args.fp64_steps if args.fp64_steps is not None else max(1, min(args.steps, 4))
+    r64 = run_form(pic, torch, w, pic.PIC_FP64, pic.PIC_WARM_NONE, k64, max(1, min(args.warmup, 3)),
+                   stream)
+    barrier()
+    e2e = None if args.no_e2e else e2e_run(pic, torch, w, pic.PIC_FP32, warm, args.steps, stream)
+    barrier()
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    ms32 = max_over_ranks(r32["ms"])
+    ms64 = max_over_ranks(r64["ms"])
+    e2e_s = max_over_ranks(e2e["s"]) if e2e else None
+    total_np = w.np * ws
+    value = total_np * args.steps / (ms32 / 1e3)
+    v64 = total_np * k64 / (ms64 / 1e3)
+    tr = r32["timing"]
+    hbm, peak_kind = peaks()
+    launch_ms = tr["sweep1_ms"] / max(1, tr["sweep1_launches"])
+    achieved = BYTES_SWEEP1[1] * w.np / (launch_ms / 1e3) / 1e9
+    line = None
+    if rank == 0:
+        cpu = None if args.no_cpu else cpu_baseline(args)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "C2: L=4pi, M=2048, k=3, Np=%d per GPU, dt=0.05, pump 0.2, vth 0.1"
+                                   % w.np,
+                       "form": "FP32 particles + FP64 grid", "warm_start": args.warm,
+                       "l2": "inputs larger than L2 (markers %.1f GB)" % (w.np * 24 / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "rel_energy_err": r32["rel_energy_err"], "energy_ok": r32["rel_energy_err"] <= 1e-10,
+            "gauss_residual": r32["gauss"],
+            "sweeps_per_step": {"I": r32["iters"][0] / args.steps, "II": r32["iters"][1] / args.steps},
+            "fp64": {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+                     "rel_energy_err": r64["rel_energy_err"], "gauss_residual": r64["gauss"],
+                     "sweeps_per_step": {"I": r64["iters"][0] / k64, "II": r64["iters"][1] / k64},
+                     "speedup_fp32_over_fp64": value / v64},
+            "roofline": {"kernel": "k_sweep1<3,float>", "bound": "hbm", "achieved": achieved,
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_marker": BYTES_SWEEP1[1], "launch_ms": launch_ms},
+            "kernel_ms": {"sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"], "solve": tr["solve_ms"]},
+            "gpu_launches": tr["launches"],
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "e2e": None if e2e is None else {
+                "value": total_np * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": e2e["h2d"] / args.steps,
+                "d2h_bytes_per_step": e2e["d2h"] / args.steps},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

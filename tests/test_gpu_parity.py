@@ -190,7 +190,11 @@ def test_fp32_form_against_oracle():
     compare_state(g, s, w.L, 2e-7, 2e-5, 2e-5)
     E = g.energy()
     assert abs(E["total"] - H0) / H0 < 1e-9
-    assert E["gauss"] < 1e-10
+    # Gauss law: each marker's path integral is formed in float (relative error
+    # eps ~ 1.2e-7) on a current w v dt; per node and step the residual grows by
+    # about eps w v dt sqrt(k Np / M) / dx, a random walk over steps.  Allow 20x.
+    est = 1.2e-7 * w.weight * w.vth * w.dt * math.sqrt(3 * w.np / w.nx) / w.dx * math.sqrt(5)
+    assert E["gauss"] < 20 * est
 
 
 def test_noconvergence_is_reported():
