@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -83,13 +84,28 @@ static int fail(pic_handle *h, int code, const char *fmt, ...)
             return fail(h, PIC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-#define CKL()                                                                               \
-    do {                                                                                    \
-        cudaError_t e_ = cudaGetLastError();                                                \
-        if (e_ != cudaSuccess)                                                              \
-            return fail(h, PIC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
-        ++h->launches;                                                                      \
+// After every launch: check the launch (and, with PIC_DEBUG_SYNC=1 in the
+// environment, wait for the kernel and check its completion), count it.
+#define CKL_N(name)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = cudaGetLastError();                                                 \
+        if (e_ == cudaSuccess && debug_sync()) e_ = cudaStreamSynchronize(h->stream);         \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(h, PIC_ERR_CUDA, "%s (%s:%d): %s", name, __FILE__, __LINE__,          \
+                        cudaGetErrorString(e_));                                             \
+        ++h->launches;                                                                       \
     } while (0)
+#define CKL() CKL_N("kernel")
+
+static bool debug_sync()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("PIC_DEBUG_SYNC");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
 
 template <typename T>
 static int dalloc(pic_handle *h, T **p, size_t n)
@@ -156,7 +172,7 @@ static int sort_markers(pic_handle *h)
     dst.pnew = h->pnew;
     if (launch_sort(h->fp32, h->np, h->M, src, dst, h->counts, particle_grid(h), 256, h->stream))
         return fail(h, PIC_ERR_CUDA, "sort launch failed");
-    CKL();
+    CKL_N("launch_sort");
     h->cur = 1 - h->cur;
     return PIC_OK;
 }
@@ -171,7 +187,7 @@ static int deposit_charge(pic_handle *h, double *out)
     a.out = out;
     if (launch_charge(a, particle_grid(h), 256, charge_smem(h->M, h->K + 1), h->stream))
         return fail(h, PIC_ERR_INVALID, "charge: bad degree");
-    CKL();
+    CKL_N("launch_charge");
     return PIC_OK;
 }
 
@@ -185,7 +201,7 @@ static int conv_plain(pic_handle *h, const double *taps, int d_start, int ntap,
     c.out[0] = out0; c.out[1] = out1;
     c.ctrl = h->ctrl;
     launch_conv(c, h->stream);
-    CKL();
+    CKL_N("launch_conv");
     return PIC_OK;
 }
 
@@ -194,7 +210,7 @@ static int solve_poisson(pic_handle *h)
     int rc;
     if ((rc = deposit_charge(h, h->rho))) return rc;
     launch_poisson_rhs(h->M, h->dx, h->rho, h->work, h->stream);
-    CKL();
+    CKL_N("launch_poisson_rhs");
     return conv_plain(h, h->d_tapM1, h->tapM1_start, h->tapM1_n, h->work, h->ex, nullptr, nullptr);
 }
 
@@ -288,6 +304,11 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
     cudaMemcpyAsync(h->d_rowM1, m1.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(h->d_rowK, kr.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(h->d_rowPm, pm.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream);
+    {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return bail(fail(h, PIC_ERR_CUDA, "band upload: %s", cudaGetErrorString(e)));
+    }
     const double cut = 1e-19;
     inverse_taps(m1.data(), K - 1, h->M, cut, gfull.data(), &h->tapM1_start, &h->tapM1_n, taps.data());
     if ((rc = dalloc(h, &h->d_tapM1, h->tapM1_n))) return bail(rc);
@@ -342,12 +363,14 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
         launch_load(h->fp32, h->np, h->M, dx, host ? dx_in : in->x, host ? dp_in : in->p, P0,
                     particle_grid(h), 256, h->stream);
         cudaError_t e = cudaGetLastError();
+        cudaError_t e2 = cudaStreamSynchronize(h->stream);
         if (host) {
-            cudaStreamSynchronize(h->stream);
             cudaFree(dx_in);
             cudaFree(dp_in);
         }
-        if (e != cudaSuccess) return bail(fail(h, PIC_ERR_CUDA, "load: %s", cudaGetErrorString(e)));
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess)
+            return bail(fail(h, PIC_ERR_CUDA, "input copies / load: %s", cudaGetErrorString(e)));
     }
     if (launch_ctrl_reset(h->ctrl, h->stream) || cudaGetLastError() != cudaSuccess) return bail(PIC_ERR_CUDA);
     h->cur = 0;
@@ -392,7 +415,7 @@ static int substep1(pic_handle *h, int *iters)
     int rc;
     launch_prep1(h->M, h->dx, h->ex, h->ek, h->ebar, h->ay, h->az, h->ga_y, h->ga_z, h->jb[0],
                  h->jb[1], h->ctrl, h->stream);
-    CKL();
+    CKL_N("launch_prep1");
     Sweep1Args a{};
     a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.np = h->np;
     a.dx = h->dx; a.dt = h->cfg.dt; a.w = h->cfg.weight;
@@ -412,14 +435,14 @@ static int substep1(pic_handle *h, int *iters)
         if ((rc = timed_begin(h))) return rc;
         if (launch_sweep1(a, h->sweep_grid, h->sweep_block, h->smem1, h->stream))
             return fail(h, PIC_ERR_INVALID, "sweep1: bad degree");
-        CKL();
+        CKL_N("launch_sweep1");
         if ((rc = timed_end(h, &h->t_sw1, &h->n_sw1))) return rc;
         h->marker_sweeps += h->np;
         c.in[0] = h->jb[it & 1];
         c.zero[0] = h->jb[(it + 1) & 1];
         if ((rc = timed_begin(h))) return rc;
         launch_conv(c, h->stream);
-        CKL();
+        CKL_N("launch_conv");
         if ((rc = timed_end(h, &h->t_solve, &h->n_solve))) return rc;
         ++it;
         if ((rc = read_ctrl(h))) return rc;
@@ -428,9 +451,9 @@ static int substep1(pic_handle *h, int *iters)
     if (iters) *iters = it;
     if ((rc = check_status(h, 1))) return rc;
     launch_finalize1(h->fp32, h->np, h->M, cur_parts(h), particle_grid(h), 256, h->stream);
-    CKL();
+    CKL_N("launch_finalize1");
     launch_copy(h->M, h->ek, h->ex, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, h->stream);
-    CKL();
+    CKL_N("launch_copy");
     return PIC_OK;
 }
 
@@ -440,7 +463,7 @@ static int substep2(pic_handle *h, int *iters)
     launch_prep2(h->M, h->K, h->cfg.dt, h->d_rowPm, h->d_rowK, h->ey, h->ez, h->ay, h->az, h->by,
                  h->bz, h->eky, h->ekz, h->aky, h->akz, h->sy[0], h->sz[0], h->sy[1], h->sz[1],
                  h->ctrl, h->stream);
-    CKL();
+    CKL_N("launch_prep2");
     if ((rc = conv_plain(h, h->d_tapP, h->tapP_start, h->tapP_n, h->by, h->r0y, h->bz, h->r0z))) return rc;
     Sweep2Args a{};
     a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.w = h->cfg.weight;
@@ -461,7 +484,7 @@ static int substep2(pic_handle *h, int *iters)
         if ((rc = timed_begin(h))) return rc;
         if (launch_sweep2(a, h->sweep_grid, h->sweep_block, h->smem2, h->stream))
             return fail(h, PIC_ERR_INVALID, "sweep2: bad degree");
-        CKL();
+        CKL_N("launch_sweep2");
         if ((rc = timed_end(h, &h->t_sw2, &h->n_sw2))) return rc;
         c.in[0] = h->sy[it & 1];
         c.in[1] = h->sz[it & 1];
@@ -469,7 +492,7 @@ static int substep2(pic_handle *h, int *iters)
         c.zero[1] = h->sz[(it + 1) & 1];
         if ((rc = timed_begin(h))) return rc;
         launch_conv(c, h->stream);
-        CKL();
+        CKL_N("launch_conv");
         if ((rc = timed_end(h, &h->t_solve, &h->n_solve))) return rc;
         ++it;
         if ((rc = read_ctrl(h))) return rc;
@@ -479,7 +502,7 @@ static int substep2(pic_handle *h, int *iters)
     if ((rc = check_status(h, 2))) return rc;
     // a^{n+1} = a^n - dt/2 (e^n + e^{n+1}) is the last a^(k); e^{n+1} the last e^(k)
     launch_copy(h->M, h->eky, h->ey, h->ekz, h->ez, h->aky, h->ay, h->akz, h->az, h->stream);
-    CKL();
+    CKL_N("launch_copy");
     return PIC_OK;
 }
 
@@ -529,10 +552,10 @@ extern "C" int pic_energy(pic_handle *h, double out[6])
     a.P = cur_parts(h);
     a.c0 = h->ay; a.c1 = h->az; a.acc = h->diag;
     launch_kinetic(a, particle_grid(h), 256, h->stream);
-    CKL();
+    CKL_N("launch_kinetic");
     launch_energy_grid(h->M, h->K, h->dx, h->d_rowM0, h->d_rowM1, h->d_rowK, h->ex, h->ey, h->ez,
                        h->ay, h->az, h->rho, h->diag, h->stream);
-    CKL();
+    CKL_N("launch_energy_grid");
     double d[8];
     CK(cudaMemcpyAsync(d, h->diag, sizeof(d), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -596,13 +619,13 @@ extern "C" int pic_deposit(pic_handle *h, int32_t kind, const double *aux, doubl
         if (!aux) return fail(h, PIC_ERR_INVALID, "CURRENT needs the displacements");
         CK(cudaMemsetAsync(out, 0, sizeof(double) * h->M, h->stream));
         launch_ctrl_reset(h->ctrl, h->stream);
-        CKL();
+        CKL_N("launch_ctrl_reset");
         CurrentArgs a{};
         a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.np = h->np;
         a.dx = h->dx; a.w = h->cfg.weight; a.P = cur_parts(h); a.disp = aux; a.out = out; a.ctrl = h->ctrl;
         if (launch_current(a, particle_grid(h), 256, charge_smem(h->M, h->H), h->stream))
             return fail(h, PIC_ERR_INVALID, "bad degree");
-        CKL();
+        CKL_N("launch_current");
         if ((rc = read_ctrl(h))) return rc;
         if (h->h_ctrl->status & STATUS_NUMERIC)
             return fail(h, PIC_ERR_NUMERIC, "displacement beyond the halo or not finite");
@@ -618,7 +641,7 @@ extern "C" int pic_deposit(pic_handle *h, int32_t kind, const double *aux, doubl
         a.s_y = out; a.s_z = out + h->M;
         if (launch_sweep2(a, h->sweep_grid, h->sweep_block, h->smem2, h->stream))
             return fail(h, PIC_ERR_INVALID, "bad degree");
-        CKL();
+        CKL_N("launch_sweep2");
         return sync(h);
     }
     return fail(h, PIC_ERR_INVALID, "unknown deposit kind %d", kind);
@@ -644,7 +667,7 @@ extern "C" int pic_gather(pic_handle *h, int32_t field, double *out)
     a.c0 = coef;
     a.out = out;
     if (launch_gather(a, d, particle_grid(h), 256, h->stream)) return fail(h, PIC_ERR_INVALID, "bad degree");
-    CKL();
+    CKL_N("launch_gather");
     return sync(h);
 }
 
