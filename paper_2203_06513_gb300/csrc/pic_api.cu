@@ -200,7 +200,7 @@ static int conv_plain(pic_handle *h, const double *taps, int d_start, int ntap,
     c.in[0] = in0; c.in[1] = in1;
     c.out[0] = out0; c.out[1] = out1;
     c.ctrl = h->ctrl;
-    launch_conv(c, h->stream);
+    if (launch_conv(c, h->stream)) return fail(h, PIC_ERR_CUDA, "k_conv shared-memory opt-in failed");
     CKL_N("launch_conv");
     return PIC_OK;
 }
@@ -309,7 +309,10 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return bail(fail(h, PIC_ERR_CUDA, "band upload: %s", cudaGetErrorString(e)));
     }
-    const double cut = 1e-19;
+    // truncate the inverse rows where they fall below 1e-17 of their largest entry:
+    // above the rounding noise of the double DFT that forms them (about 1e-18), and
+    // the dropped geometric tail changes a solve by far less than one double ulp
+    const double cut = 1e-17;
     inverse_taps(m1.data(), K - 1, h->M, cut, gfull.data(), &h->tapM1_start, &h->tapM1_n, taps.data());
     if ((rc = dalloc(h, &h->d_tapM1, h->tapM1_n))) return bail(rc);
     if (cudaMemcpy(h->d_tapM1, taps.data(), sizeof(double) * h->tapM1_n, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -441,7 +444,7 @@ static int substep1(pic_handle *h, int *iters)
         c.in[0] = h->jb[it & 1];
         c.zero[0] = h->jb[(it + 1) & 1];
         if ((rc = timed_begin(h))) return rc;
-        launch_conv(c, h->stream);
+        if (launch_conv(c, h->stream)) return fail(h, PIC_ERR_CUDA, "k_conv shared-memory opt-in failed");
         CKL_N("launch_conv");
         if ((rc = timed_end(h, &h->t_solve, &h->n_solve))) return rc;
         ++it;
@@ -491,7 +494,7 @@ static int substep2(pic_handle *h, int *iters)
         c.zero[0] = h->sy[(it + 1) & 1];
         c.zero[1] = h->sz[(it + 1) & 1];
         if ((rc = timed_begin(h))) return rc;
-        launch_conv(c, h->stream);
+        if (launch_conv(c, h->stream)) return fail(h, PIC_ERR_CUDA, "k_conv shared-memory opt-in failed");
         CKL_N("launch_conv");
         if ((rc = timed_end(h, &h->t_solve, &h->n_solve))) return rc;
         ++it;

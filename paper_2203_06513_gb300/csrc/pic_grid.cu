@@ -5,7 +5,7 @@
 //   M0 (degree k), M1 (degree k-1), K = G^T M1 G, P = M0 + dt^2/4 K.
 // Solves apply the exact inverse as a circulant convolution: the inverse of a
 // banded SPD circulant has a first row that decays geometrically, so it is
-// truncated where its entries fall below 1e-19 of the largest (or kept whole).
+// truncated where its entries fall below 1e-17 of the largest (or kept whole).
 #include <cmath>
 #include <vector>
 
@@ -207,6 +207,12 @@ int launch_conv(const ConvArgs &a, cudaStream_t s)
     const int threads = 64;
     dim3 grid((a.M + threads - 1) / threads, a.ncomp);
     const size_t smem = (2 * (size_t)a.M + (size_t)a.ntap) * sizeof(double);
+    static size_t opted = 0;   // largest dynamic shared memory opted in so far
+    if (smem > 48 * 1024 && smem > opted) {
+        if (cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return 1;
+        opted = smem;
+    }
     k_conv<<<grid, threads, smem, s>>>(a);
     return 0;
 }
