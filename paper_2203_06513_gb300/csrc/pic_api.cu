@@ -154,10 +154,27 @@ static int sync(pic_handle *h)
     return PIC_OK;
 }
 
+static bool debug_iters()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("PIC_DEBUG_ITERS");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
+
 static int read_ctrl(pic_handle *h)
 {
     CK(cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (debug_iters()) {
+        double d, e;
+        memcpy(&d, &h->h_ctrl->dprev_bits, sizeof(d));
+        memcpy(&e, &h->h_ctrl->eprev_bits, sizeof(e));
+        fprintf(stderr, "[libpic] iter %d dmax %.3e emax %.3e status %d converged %d\n", h->h_ctrl->iter, d,
+                e, h->h_ctrl->status, h->h_ctrl->converged);
+    }
     return PIC_OK;
 }
 
@@ -429,7 +446,7 @@ static int substep1(pic_handle *h, int *iters)
     c.M = h->M; c.d_start = h->tapM1_start; c.ntap = h->tapM1_n; c.mode = CONV_SOLVE1; c.ncomp = 1;
     c.taps = h->d_tapM1;
     c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
-    c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1.0 / (1 << 20);
+    c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6;   // FP32: estimated position error, cells relative to max(1, |delta|)
     c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 1; c.ctrl = h->ctrl;
     int it = 0;
     for (;;) {

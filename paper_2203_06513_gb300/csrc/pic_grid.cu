@@ -124,8 +124,24 @@ __device__ void decide(const ConvArgs &A)
     if (!A.fp32) {
         ok = (d * A.dx <= A.tol) && (e <= A.tol);
     } else {
-        const bool dok = (A.subsystem == 1) ? (d <= A.dtol) : true;
-        ok = dok && ((e <= A.tol) || (c->iter >= 3 && e >= 0.25 * ep && e <= 1e-6));
+        // Float iterates stop improving at rounding noise, so increments alone never
+        // reach a tight tolerance.  Estimate the remaining error of the new iterate
+        // from the increment v_k and the observed contraction r = v_k / v_{k-1}
+        // (geometric tail v_k r / (1 - r), r capped at 0.9), and stop when both the
+        // position and field estimates are below tolerance, or when both increments
+        // have stopped shrinking at noise level.
+        const double dp = bits_to_double(c->dprev_bits);
+        auto est = [](double v, double vprev) {
+            if (v == 0.0) return 0.0;
+            double r = v / vprev;
+            if (!(r < 0.9)) r = 0.9;
+            return v * r / (1.0 - r);
+        };
+        const bool dok = (A.subsystem == 1) ? (est(d, dp) <= A.dtol) : true;
+        const bool eok = est(e, ep) <= A.tol;
+        const bool dstag = (A.subsystem == 1) ? (d >= 0.5 * dp && d <= 1e-4) : true;
+        const bool estag = e >= 0.5 * ep && e <= 1e-8;
+        ok = (dok && eok) || (c->iter >= 3 && dstag && estag);
     }
     bool stop = ok;
     if (!ok && c->iter >= A.max_iter) {
