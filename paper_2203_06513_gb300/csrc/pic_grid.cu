@@ -133,7 +133,8 @@ __device__ void decide(const ConvArgs &A)
         const double dp = bits_to_double(c->dprev_bits);
         auto est = [](double v, double vprev) {
             if (v == 0.0) return 0.0;
-            double r = v / vprev;
+            // no previous increment (first sweep): no contraction estimate yet
+            double r = (vprev < 1e300) ? v / vprev : 0.9;
             if (!(r < 0.9)) r = 0.9;
             return v * r / (1.0 - r);
         };
