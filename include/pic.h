@@ -164,10 +164,34 @@ int pic_timing_read(pic_handle *h, double out[8]);
 int pic_destroy(pic_handle *h);
 
 /* Message of the last error on h; with h == NULL, the message of the last
- * failed pic_init on the calling thread. */
+ * failed pic_init or pic_deposit_current_noalloc on the calling thread. */
 /* Message of the last error on h; with h == NULL, the message of the last
- * failed pic_init on the calling thread. */
+ * failed pic_init or pic_deposit_current_noalloc on the calling thread. */
 const char *pic_last_error(const pic_handle *h);
+
+/* Path-integrated current deposit for callers that cannot allocate device
+ * memory (a memory pool that must not grow, a device heap owned by another
+ * component, a plugin not allowed to hold CUDA allocations).  The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ * It needs no handle and calls no allocator; its scratch is a fixed 2 MiB
+ * device array inside the library (one per GPU that loads the library, kept
+ * until the process exits).
+ *   out[nx] (device)  = sum_a weight * int_{x_a}^{x_a + disp_a} Lambda^1_i,
+ * the same quantity as pic_deposit(PIC_DEP_CURRENT), computed in double and
+ * reduced in a fixed order (deterministic).  x[np], disp[np]: device arrays of
+ * positions in [0, L) and signed displacements (length units, at most 64 cells).
+ * L > 0, 8 <= nx <= 8192 (larger grids exceed the scratch and are rejected with
+ * PIC_ERR_INVALID), 2 <= degree <= 5 (degree of V0; the deposit uses degree-1).
+ * Work is ordered on `stream` (cudaStream_t as void*); the call returns when
+ * out is complete.  The first call on a device (with that device current) sets
+ * up the scratch address and kernel attributes; make that first call before
+ * any stream capture.  All calls share the one scratch array, which keeps the
+ * last call's contents: calls whose kernels overlap on the GPU (other streams
+ * or threads) race and give wrong results.  Errors: PIC_ERR_INVALID,
+ * PIC_ERR_NUMERIC (a displacement not finite or beyond 64 cells), PIC_ERR_CUDA;
+ * message via pic_last_error(NULL). */
+int pic_deposit_current_noalloc(double L, int32_t nx, int32_t degree, int64_t np, double weight,
+                                const double *x, const double *disp, double *out, void *stream);
 
 /* Library version string, e.g. "libpic 1.0 sm_103a". */
 const char *pic_version(void);

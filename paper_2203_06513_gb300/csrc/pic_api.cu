@@ -17,6 +17,8 @@ using namespace pic;
 int pic_set_smem_attrs(size_t s1, size_t s2, size_t s3);
 static thread_local std::string g_init_error;
 
+void pic::set_thread_error(const char *msg) { g_init_error = msg ? msg : ""; }
+
 struct pic_handle {
     pic_config cfg{};
     cudaStream_t stream = nullptr;

@@ -113,6 +113,9 @@ int launch_energy_grid(int M, int K, double dx, const double *rowM0, const doubl
                        cudaStream_t s);
 int launch_ctrl_reset(DevCtrl *ctrl, cudaStream_t s);
 
+// message returned by pic_last_error(NULL) on the calling thread
+void set_thread_error(const char *msg);
+
 // host-side spline algebra (exact rows and inverse taps of the circulant matrices)
 void mass_band(int d, double dx, double *band /* d+1 */);
 void inverse_taps(const double *band, int bw, int M, double cut, double *g_full /* M */,
