@@ -200,6 +200,58 @@ __device__ __forceinline__ int walk_path(R t0, R d, Visit &&visit)
     return n;
 }
 
+// ---------------------------------------------------------------------------
+// Per-warp register window for deposits of cell-sorted markers.  Each lane keeps
+// NS partial sums for the consecutive grid nodes b0 .. b0+NS-1 around the warp's
+// base cell; a piece whose NV values fall on nodes cp - r (r = 0..NV-1) goes to
+// slots (cp - base) + OFF - r, chosen by a switch so that the array stays in
+// registers.  flush() sums each slot over the warp (butterfly) and adds it, in
+// double, to the block's shared-memory row; only lanes 0..NS-1 issue an atomic.
+// ---------------------------------------------------------------------------
+template <typename R, int NS, int NV, int OFF, int OMIN, int OMAX>
+struct DepWindow {
+    R acc[NS];
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) acc[s] = R(0);
+    }
+    template <int O>
+    __device__ __forceinline__ void add_at(const R *v)
+    {
+#pragma unroll
+        for (int r = 0; r < NV; ++r) acc[O + OFF - r] += v[r];
+    }
+    // returns false when the piece lies outside the window (caller takes the slow path)
+    __device__ __forceinline__ bool put(int o, const R *v)
+    {
+        static_assert(OMIN >= -2 && OMAX <= 2, "window offsets");
+        switch (o) {
+        case -2: if (OMIN <= -2) { add_at<(OMIN <= -2 ? -2 : 0)>(v); return true; } return false;
+        case -1: if (OMIN <= -1) { add_at<(OMIN <= -1 ? -1 : 0)>(v); return true; } return false;
+        case 0: add_at<0>(v); return true;
+        case 1: if (OMAX >= 1) { add_at<(OMAX >= 1 ? 1 : 0)>(v); return true; } return false;
+        case 2: if (OMAX >= 2) { add_at<(OMAX >= 2 ? 2 : 0)>(v); return true; } return false;
+        default: return false;
+        }
+    }
+    // all 32 lanes must call; row0 = shared-memory index of slot 0
+    __device__ __forceinline__ void flush(double *s_row, int row0)
+    {
+        const int lane = threadIdx.x & 31;
+        R mine = R(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            R v = acc[s];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == s) mine = v;
+            acc[s] = R(0);
+        }
+        if (lane < NS && mine != R(0)) atomicAdd(&s_row[row0 + lane], (double)mine);
+    }
+};
+
 template <typename T>
 __device__ __forceinline__ T warp_max(T v)
 {

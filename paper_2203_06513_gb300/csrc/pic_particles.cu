@@ -6,6 +6,7 @@
 // memory with a periodic halo of H cells on both sides, so no index is wrapped
 // in the inner loop.  Deposits are accumulated per block in double in shared
 // memory and added to the global grid with one double atomic per node.
+#include <climits>
 #include <type_traits>
 
 #include "pic_internal.h"
@@ -21,6 +22,77 @@ struct Real<double> { static constexpr bool fp32 = false; };
 
 __device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
 
+// Field tiles staged in shared memory, interleaved for vector loads.
+template <typename R> struct FieldTile;
+template <> struct FieldTile<float> {
+    float2 *a;      // (a_y, a_z)
+    float4 *f;      // (ebar, (G a_y), (G a_z), 0)
+    __device__ __forceinline__ void aa(int i, float &y, float &z) const { const float2 v = a[i]; y = v.x; z = v.y; }
+    __device__ __forceinline__ void eg(int i, float &e, float &gy, float &gz) const
+    {
+        const float4 v = f[i];
+        e = v.x; gy = v.y; gz = v.z;
+    }
+    __device__ __forceinline__ void store(int i, double ay, double az, double e, double gy, double gz)
+    {
+        a[i] = make_float2((float)ay, (float)az);
+        f[i] = make_float4((float)e, (float)gy, (float)gz, 0.f);
+    }
+    static __host__ __device__ size_t bytes(size_t W) { return W * (sizeof(float2) + sizeof(float4)); }
+};
+template <> struct FieldTile<double> {
+    double2 *a;     // (a_y, a_z)
+    double2 *g;     // ((G a_y), (G a_z))
+    double *e;      // ebar
+    __device__ __forceinline__ void aa(int i, double &y, double &z) const { const double2 v = a[i]; y = v.x; z = v.y; }
+    __device__ __forceinline__ void eg(int i, double &ev, double &gy, double &gz) const
+    {
+        const double2 v = g[i];
+        ev = e[i]; gy = v.x; gz = v.y;
+    }
+    __device__ __forceinline__ void store(int i, double ay, double az, double ev, double gy, double gz)
+    {
+        a[i] = make_double2(ay, az);
+        g[i] = make_double2(gy, gz);
+        e[i] = ev;
+    }
+    static __host__ __device__ size_t bytes(size_t W) { return W * (2 * sizeof(double2) + sizeof(double)); }
+};
+
+template <typename R>
+__device__ __forceinline__ FieldTile<R> carve_tile(unsigned char *p, int W);
+template <>
+__device__ __forceinline__ FieldTile<float> carve_tile<float>(unsigned char *p, int W)
+{
+    FieldTile<float> t;
+    t.f = reinterpret_cast<float4 *>(p);
+    t.a = reinterpret_cast<float2 *>(t.f + W);
+    return t;
+}
+template <>
+__device__ __forceinline__ FieldTile<double> carve_tile<double>(unsigned char *p, int W)
+{
+    FieldTile<double> t;
+    t.a = reinterpret_cast<double2 *>(p);
+    t.g = t.a + W;
+    t.e = reinterpret_cast<double *>(t.g + W);
+    return t;
+}
+
+template <typename R> __device__ __forceinline__ R fdiv_(R a, R b);
+template <> __device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
+
+// Contiguous chunk of markers owned by one block (a multiple of 32, so every
+// warp's lanes see consecutive, cell-sorted markers).
+__device__ __forceinline__ void block_chunk(long long np, long long &beg, long long &end)
+{
+    long long chunk = (np + gridDim.x - 1) / gridDim.x;
+    chunk = (chunk + 31) & ~31LL;
+    beg = (long long)blockIdx.x * chunk;
+    end = beg + chunk < np ? beg + chunk : np;
+}
+
 // ---------------------------------------------------------------------------
 // Subsystem I: one Picard sweep (Sec. 4.2).  Per marker, with x^n = (c0, t0),
 // the iterate x^(k) = x^n + delta^(k) and ebar = (e^n + e^(k))/2:
@@ -29,6 +101,9 @@ __device__ __forceinline__ double nan_max(double a, double b) { return (b > a ||
 //   p^(k+1) = p^n + dt Ebar - dt (A1+A0).D / (g(p^n,A1) + g(p^n,A0)),
 //   delta^(k+1) = dt (p^n + p^(k+1)) / (g(p^n,A1) + g(p^(k+1),A1)) / dx,
 //   j_i += w int_{x^n}^{x^n+delta^(k+1)} Lambda^1_i.
+// Each block owns a contiguous chunk of the cell-sorted markers; the deposit
+// goes through a per-warp register window (DepWindow), then the block's
+// shared-memory row (double), then one global double atomic per touched node.
 // ---------------------------------------------------------------------------
 template <int K, typename R>
 __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
@@ -38,18 +113,10 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     const int W = A.M + 2 * H;
     double *s_acc = reinterpret_cast<double *>(smem);
     double *s_red = s_acc + W;
-    R *s_e = reinterpret_cast<R *>(s_red + 32);
-    R *s_gy = s_e + W;
-    R *s_gz = s_gy + W;
-    R *s_ay = s_gz + W;
-    R *s_az = s_ay + W;
+    FieldTile<R> F = carve_tile<R>(reinterpret_cast<unsigned char *>(s_red + 32), W);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
-        s_e[i] = (R)A.ebar[g];
-        s_gy[i] = (R)A.ga_y[g];
-        s_gz[i] = (R)A.ga_z[g];
-        s_ay[i] = (R)A.ay[g];
-        s_az[i] = (R)A.az[g];
+        F.store(i, A.ay[g], A.az[g], A.ebar[g], A.ga_y[g], A.ga_z[g]);
         s_acc[i] = 0.0;
     }
     __syncthreads();
@@ -61,15 +128,28 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     R *__restrict__ pnp = static_cast<R *>(A.P.pnew);
     const R dt = (R)A.dt;
     const R dtdx = (R)(A.dt / A.dx);
-    const double wdx = A.w * A.dx;
+    const R wdx = (R)(A.w * A.dx);
     const R dlim = (R)A.Dlim;
     const R one = R(1);
-    double dmax = 0.0;
+    R dmax = R(0);
     bool bad = false;
+    DepWindow<R, K + 4, K, K + 1, -2, 2> win;
+    win.clear();
+    int wb = INT_MIN;
 
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
-        const int c0 = cellp[a];
+    long long beg, end;
+    block_chunk(A.np, beg, end);
+    for (long long base = beg; base < end; base += blockDim.x) {
+        const long long a = base + threadIdx.x;
+        const bool act = a < end;
+        const int c0 = act ? cellp[a] : 0;
+        const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
+        if (lead == INT_MAX) break;                    // whole warp past the chunk end
+        if (lead != wb) {
+            if (wb != INT_MIN) win.flush(s_acc, wb - K - 1 + H);
+            wb = lead;
+        }
+        if (!act) continue;
         const R t0 = tp[a];
         const R pn = pp[a];
         R v[K + 1];
@@ -77,12 +157,13 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
         R A0y = R(0), A0z = R(0);
 #pragma unroll
         for (int r = 0; r <= K; ++r) {
-            const int i = c0 - r + H;
-            A0y += s_ay[i] * v[r];
-            A0z += s_az[i] * v[r];
+            R y, z;
+            F.aa(c0 - r + H, y, z);
+            A0y += y * v[r];
+            A0z += z * v[r];
         }
         const R g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
-        R dold = A.warm ? dtdx * pn / g0 : dp[a];
+        R dold = A.warm ? fdiv_(dtdx * pn, g0) : dp[a];
         if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
 
         const R s = t0 + dold;
@@ -92,9 +173,10 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
         R A1y = R(0), A1z = R(0);
 #pragma unroll
         for (int r = 0; r <= K; ++r) {
-            const int i = c1 - r + H;
-            A1y += s_ay[i] * v[r];
-            A1z += s_az[i] * v[r];
+            R y, z;
+            F.aa(c1 - r + H, y, z);
+            A1y += y * v[r];
+            A1z += z * v[r];
         }
 
         R Eb = R(0), Dy = R(0), Dz = R(0);
@@ -103,10 +185,11 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
             R e = R(0), gy = R(0), gz = R(0);
 #pragma unroll
             for (int r = 0; r < K; ++r) {
-                const int i = c0 + c - r + H;
-                e += m[r] * s_e[i];
-                gy += m[r] * s_gy[i];
-                gz += m[r] * s_gz[i];
+                R ev, y, z;
+                F.eg(c0 + c - r + H, ev, y, z);
+                e += m[r] * ev;
+                gy += m[r] * y;
+                gz += m[r] * z;
             }
             const R f = single ? one : h * invd;
             Eb += f * e;
@@ -116,35 +199,41 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
 
         const R q1 = one + A1y * A1y + A1z * A1z;
         const R g1 = sqrt_(q1 + pn * pn);
-        const R pnew = pn + dt * Eb - dt * ((A1y + A0y) * Dy + (A1z + A0z) * Dz) / (g1 + g0);
+        const R pnew = pn + dt * Eb - dt * fdiv_((A1y + A0y) * Dy + (A1z + A0z) * Dz, g1 + g0);
         const R g2 = sqrt_(q1 + pnew * pnew);
-        R dnew = dtdx * (pn + pnew) / (g1 + g2);
+        R dnew = fdiv_(dtdx * (pn + pnew), g1 + g2);
         if (!(fabs(dnew) <= dlim)) { bad = true; dnew = R(0); }
 
         walk_path<K, R>(t0, dnew, [&](int c, R h, const R *m, bool) {
-            const double hw = wdx * (double)h;
+            const R hw = wdx * h;
+            R val[K];
 #pragma unroll
-            for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], hw * (double)m[r]);
+            for (int r = 0; r < K; ++r) val[r] = hw * m[r];
+            if (!win.put(c0 + c - wb, val)) {
+#pragma unroll
+                for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], (double)val[r]);
+            }
         });
 
-        double inc = fabs((double)dnew - (double)dold);
-        if (Real<R>::fp32) inc /= fmax(1.0, fabs((double)dnew));
-        dmax = nan_max(dmax, inc);
+        R inc = fabs(dnew - dold);
+        if (Real<R>::fp32) inc = inc / fmax(one, fabs(dnew));
+        dmax = (inc > dmax || inc != inc) ? inc : dmax;
         dp[a] = dnew;
         pnp[a] = pnew;
     }
+    if (wb != INT_MIN) win.flush(s_acc, wb - K - 1 + H);
     if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
-    block_max_to(&A.ctrl->dmax_bits, dmax, s_red);
+    block_max_to(&A.ctrl->dmax_bits, (double)dmax, s_red);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
-        const double v = s_acc[i];
-        if (v != 0.0) atomicAdd(&A.j[wrap_cell(i - H, A.M)], v);
+        const double val = s_acc[i];
+        if (val != 0.0) atomicAdd(&A.j[wrap_cell(i - H, A.M)], val);
     }
 }
 
 size_t sweep1_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
-    return (W + 32) * sizeof(double) + 5 * W * (fp32 ? sizeof(float) : sizeof(double));
+    return (W + 32) * sizeof(double) + (fp32 ? FieldTile<float>::bytes(W) : FieldTile<double>::bytes(W));
 }
 
 template <typename R>
@@ -225,6 +314,7 @@ int launch_current(const CurrentArgs &a, int grid, int block, size_t smem, cudaS
 // Subsystem II: one fixed-point sweep (Sec. 4.2).  Markers frozen at x; with
 // A0 = A^n_h(x), A1 = A^(k)_h(x):
 //   s_i += w (A0 + A1) Lambda^0_i(x) / (g(p,A0) + g(p,A1))   (y and z).
+// Same chunking and per-warp register windows as the subsystem-I sweep.
 // ---------------------------------------------------------------------------
 template <int K, typename R>
 __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
@@ -234,16 +324,15 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
     const int W = A.M + 2 * H;
     double *s_sy = reinterpret_cast<double *>(smem);
     double *s_sz = s_sy + W;
-    R *s_any = reinterpret_cast<R *>(s_sz + W);
-    R *s_anz = s_any + W;
-    R *s_aky = s_anz + W;
-    R *s_akz = s_aky + W;
+    using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
+    R2 *s_an = reinterpret_cast<R2 *>(s_sz + W);
+    R2 *s_ak = s_an + W;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
-        s_any[i] = (R)A.an_y[g];
-        s_anz[i] = (R)A.an_z[g];
-        s_aky[i] = (R)A.ak_y[g];
-        s_akz[i] = (R)A.ak_z[g];
+        s_an[i].x = (R)A.an_y[g];
+        s_an[i].y = (R)A.an_z[g];
+        s_ak[i].x = (R)A.ak_y[g];
+        s_ak[i].y = (R)A.ak_z[g];
         s_sy[i] = 0.0;
         s_sz[i] = 0.0;
     }
@@ -253,9 +342,26 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
     const R *__restrict__ pp = static_cast<const R *>(A.P.p);
     const R w = (R)A.w;
     const R one = R(1);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
-        const int c = cellp[a];
+    DepWindow<R, K + 3, K + 1, K + 1, -1, 1> wy, wz;
+    wy.clear();
+    wz.clear();
+    int wb = INT_MIN;
+    long long beg, end;
+    block_chunk(A.np, beg, end);
+    for (long long base = beg; base < end; base += blockDim.x) {
+        const long long a = base + threadIdx.x;
+        const bool act = a < end;
+        const int c = act ? cellp[a] : 0;
+        const int lead = __reduce_min_sync(0xffffffffu, act ? c : INT_MAX);
+        if (lead == INT_MAX) break;
+        if (lead != wb) {
+            if (wb != INT_MIN) {
+                wy.flush(s_sy, wb - K - 1 + H);
+                wz.flush(s_sz, wb - K - 1 + H);
+            }
+            wb = lead;
+        }
+        if (!act) continue;
         const R t = tp[a];
         const R p = pp[a];
         R v[K + 1];
@@ -263,23 +369,35 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
         R A0y = R(0), A0z = R(0), A1y = R(0), A1z = R(0);
 #pragma unroll
         for (int r = 0; r <= K; ++r) {
-            const int i = c - r + H;
-            A0y += s_any[i] * v[r];
-            A0z += s_anz[i] * v[r];
-            A1y += s_aky[i] * v[r];
-            A1z += s_akz[i] * v[r];
+            const R2 an = s_an[c - r + H], ak = s_ak[c - r + H];
+            A0y += an.x * v[r];
+            A0z += an.y * v[r];
+            A1y += ak.x * v[r];
+            A1z += ak.y * v[r];
         }
         const R pp1 = one + p * p;
         const R g0 = sqrt_(pp1 + A0y * A0y + A0z * A0z);
         const R g1 = sqrt_(pp1 + A1y * A1y + A1z * A1z);
-        const R cf = w / (g0 + g1);
+        const R cf = fdiv_(w, g0 + g1);
         const R fy = cf * (A0y + A1y), fz = cf * (A0z + A1z);
+        R vy[K + 1], vz[K + 1];
 #pragma unroll
         for (int r = 0; r <= K; ++r) {
-            const int i = c - r + H;
-            atomicAdd(&s_sy[i], (double)(fy * v[r]));
-            atomicAdd(&s_sz[i], (double)(fz * v[r]));
+            vy[r] = fy * v[r];
+            vz[r] = fz * v[r];
         }
+        if (!wy.put(c - wb, vy)) {
+#pragma unroll
+            for (int r = 0; r <= K; ++r) atomicAdd(&s_sy[c - r + H], (double)vy[r]);
+        }
+        if (!wz.put(c - wb, vz)) {
+#pragma unroll
+            for (int r = 0; r <= K; ++r) atomicAdd(&s_sz[c - r + H], (double)vz[r]);
+        }
+    }
+    if (wb != INT_MIN) {
+        wy.flush(s_sy, wb - K - 1 + H);
+        wz.flush(s_sz, wb - K - 1 + H);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -293,7 +411,7 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
 size_t sweep2_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
-    return 2 * W * sizeof(double) + 4 * W * (fp32 ? sizeof(float) : sizeof(double));
+    return 2 * W * sizeof(double) + 2 * W * (fp32 ? sizeof(float2) : sizeof(double2));
 }
 
 template <typename R>
