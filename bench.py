@@ -121,7 +121,7 @@ def run_form(pic, torch, w, precision, warm, steps, warmup, stream, timing=True)
     x, p = I.particles(w)
     ay, az, ey, ez = I.fields(w)
     tol = 1e-13 if precision == pic.PIC_FP64 else 1e-13
-    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=8, tol=tol)
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2, tol=tol)
     g = pic.Pic(cfg, x, p, ay, az, ey, ez, stream=stream.cuda_stream)
     del x, p
     H0 = g.energy()["total"]
@@ -152,7 +152,7 @@ def e2e_run(pic, torch, w, precision, warm, steps, stream):
     del x, p
     out = {k: torch.empty(w.np, dtype=torch.float64).pin_memory().numpy() for k in ("x", "p")}
     out.update({k: np.empty(w.nx) for k in ("ex", "ey", "ez", "ay", "az")})
-    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=8)
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = pic.Pic(cfg, hx, hp, ay, az, ey, ez, stream=stream.cuda_stream)

@@ -225,18 +225,21 @@ struct DepWindow {
     // returns false when the piece lies outside the window (caller takes the slow path)
     __device__ __forceinline__ bool put(int o, const R *v)
     {
-        static_assert(OMIN >= -2 && OMAX <= 2, "window offsets");
+        static_assert(OMIN >= -3 && OMAX <= 3 && OMIN <= 0 && OMAX >= 0, "window offsets");
         switch (o) {
+        case -3: if (OMIN <= -3) { add_at<(OMIN <= -3 ? -3 : 0)>(v); return true; } return false;
         case -2: if (OMIN <= -2) { add_at<(OMIN <= -2 ? -2 : 0)>(v); return true; } return false;
         case -1: if (OMIN <= -1) { add_at<(OMIN <= -1 ? -1 : 0)>(v); return true; } return false;
         case 0: add_at<0>(v); return true;
         case 1: if (OMAX >= 1) { add_at<(OMAX >= 1 ? 1 : 0)>(v); return true; } return false;
         case 2: if (OMAX >= 2) { add_at<(OMAX >= 2 ? 2 : 0)>(v); return true; } return false;
+        case 3: if (OMAX >= 3) { add_at<(OMAX >= 3 ? 3 : 0)>(v); return true; } return false;
         default: return false;
         }
     }
-    // all 32 lanes must call; row0 = shared-memory index of slot 0
-    __device__ __forceinline__ void flush(double *s_row, int row0)
+    // all 32 lanes must call; row0 = shared-memory index of slot 0; the warp sums
+    // are multiplied by `scale` in double (the marker weight enters here)
+    __device__ __forceinline__ void flush(double *s_row, int row0, double scale)
     {
         const int lane = threadIdx.x & 31;
         R mine = R(0);
@@ -248,9 +251,43 @@ struct DepWindow {
             if (lane == s) mine = v;
             acc[s] = R(0);
         }
-        if (lane < NS && mine != R(0)) atomicAdd(&s_row[row0 + lane], (double)mine);
+        if (lane < NS && mine != R(0)) atomicAdd(&s_row[row0 + lane], scale * (double)mine);
     }
 };
+
+// Number of pieces of the path from local offset t0 by d cells: 1 + knots crossed.
+template <typename R>
+__device__ __forceinline__ int path_pieces(R t0, R d)
+{
+    return abs((int)floor_(t0 + d)) + 1;
+}
+
+template <typename R> __device__ __forceinline__ R clamp01(R v) { return v < R(0) ? R(0) : (v > R(1) ? R(1) : v); }
+
+// Branch-free walk of the path t0 -> t0 + d split at knots: piece p (p = 0..npc-1)
+// lies in cell c = sign(d) p relative to the start cell, on the local interval
+// [lo, hi] = clamp([min(t0,s), max(t0,s)] - c, 0, 1).  The caller passes the warp
+// maximum of the piece counts, so every lane runs the same trip count; pieces
+// beyond a lane's own count have zero length.  visit(c, h, m, p) gets the signed
+// piece length h (cells) and the means m[r] of the degree-(K-1) pieces over it.
+template <int K, typename R, class Visit>
+__device__ __forceinline__ void walk_uniform(R t0, R d, int npc, Visit &&visit)
+{
+    constexpr int D = K - 1;
+    const R s = t0 + d;
+    const R umin = s < t0 ? s : t0;
+    const R umax = s < t0 ? t0 : s;
+    const int sg = d < R(0) ? -1 : 1;
+    R m[D + 1];
+    for (int p = 0; p < npc; ++p) {
+        const int c = sg * p;
+        const R lo = clamp01(umin - R(c));
+        const R hi = clamp01(umax - R(c));
+        const R len = hi - lo;
+        piece_means<D, R>(R(0.5) * (lo + hi), len, m);
+        visit(c, sg > 0 ? len : -len, m, p);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_max(T v)

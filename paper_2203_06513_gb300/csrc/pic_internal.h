@@ -8,6 +8,9 @@
 
 namespace pic {
 
+// velocity bins of the marker sort key (cell, bin)
+constexpr int kVelBins = 16;
+
 // ---------------------------------------------------------------- particles
 struct PartPtrs {
     int32_t *cell;      // cell index in [0, M)
@@ -15,7 +18,7 @@ struct PartPtrs {
     void *p;            // momentum
     void *delta;        // subsystem-I iterate: displacement x^(k) - x^n, cell units
     void *pnew;         // subsystem-I iterate p^(k+1)
-    int64_t *id;        // caller index of each stored marker
+    int32_t *id;        // caller index of each stored marker
 };
 
 struct Sweep1Args {
@@ -73,8 +76,8 @@ int launch_load(int fp32, long long np, int M, double dx, const double *x, const
 int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, double *p,
                  int grid, int block, cudaStream_t s);
 int sweep_blocks_per_sm(int K, int fp32, int which, int block, size_t smem);
-int launch_sort(int fp32, long long np, int M, PartPtrs src, PartPtrs dst, int32_t *counts,
-                int grid, int block, cudaStream_t s);
+int launch_sort(int fp32, long long np, int M, double tau, PartPtrs src, PartPtrs dst,
+                int32_t *counts, int grid, int block, cudaStream_t s);
 
 // ---------------------------------------------------------------- grid
 enum ConvMode { CONV_PLAIN = 0, CONV_SOLVE1 = 1, CONV_SOLVE2 = 2 };

@@ -1,11 +1,20 @@
 // pic_particles.cu -- marker kernels of libpic (sm_103a).
 //
-// Every kernel is a persistent grid-stride loop over the structure-of-arrays
-// marker state (cell int32, offset t, momentum p, iterates delta and p_new),
-// read coalesced.  Field coefficients are staged once per block into shared
-// memory with a periodic halo of H cells on both sides, so no index is wrapped
-// in the inner loop.  Deposits are accumulated per block in double in shared
-// memory and added to the global grid with one double atomic per node.
+// Markers are stored as structure-of-arrays (cell int32, offset t, momentum p,
+// iterates delta and p_new, caller index id) and kept sorted by the key
+// (cell, velocity bin), so the 32 lanes of a warp hold markers of one or two
+// cells with similar displacements.  Each sweep block owns one contiguous chunk
+// of markers, reads it coalesced, stages the field coefficients once in shared
+// memory (periodic halo of H cells, so no index wraps in the inner loop), and
+// deposits through a per-warp register window (DepWindow) into a double row in
+// shared memory, flushed to the global grid with one double atomic per node.
+//
+// Precision discipline of the FP32 form: per-marker arithmetic is float; the
+// marker weight w and the cell width dx enter only when a window is flushed, in
+// double; the momentum and position updates share one float factor
+// tau = dt/dx (fields are staged as e dx and a_j - a_{j-1}), so the discrete
+// work identity (p^(k+1) - p^n) vbar = (Ebar - F)(x^(k+1) - x^n) of Sec. 4.2
+// holds with the same rounded factor on both sides.
 #include <climits>
 #include <type_traits>
 
@@ -20,13 +29,11 @@ struct Real<float> { static constexpr bool fp32 = true; };
 template <>
 struct Real<double> { static constexpr bool fp32 = false; };
 
-__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
-
 // Field tiles staged in shared memory, interleaved for vector loads.
 template <typename R> struct FieldTile;
 template <> struct FieldTile<float> {
     float2 *a;      // (a_y, a_z)
-    float4 *f;      // (ebar, (G a_y), (G a_z), 0)
+    float4 *f;      // (ebar dx, a_y,j - a_y,j-1, a_z,j - a_z,j-1, 0)
     __device__ __forceinline__ void aa(int i, float &y, float &z) const { const float2 v = a[i]; y = v.x; z = v.y; }
     __device__ __forceinline__ void eg(int i, float &e, float &gy, float &gz) const
     {
@@ -38,12 +45,12 @@ template <> struct FieldTile<float> {
         a[i] = make_float2((float)ay, (float)az);
         f[i] = make_float4((float)e, (float)gy, (float)gz, 0.f);
     }
-    static __host__ __device__ size_t bytes(size_t W) { return W * (sizeof(float2) + sizeof(float4)); }
+    static size_t bytes(size_t W) { return W * (sizeof(float2) + sizeof(float4)); }
 };
 template <> struct FieldTile<double> {
     double2 *a;     // (a_y, a_z)
-    double2 *g;     // ((G a_y), (G a_z))
-    double *e;      // ebar
+    double2 *g;     // (a_y,j - a_y,j-1, a_z,j - a_z,j-1)
+    double *e;      // ebar dx
     __device__ __forceinline__ void aa(int i, double &y, double &z) const { const double2 v = a[i]; y = v.x; z = v.y; }
     __device__ __forceinline__ void eg(int i, double &ev, double &gy, double &gz) const
     {
@@ -56,7 +63,7 @@ template <> struct FieldTile<double> {
         g[i] = make_double2(gy, gz);
         e[i] = ev;
     }
-    static __host__ __device__ size_t bytes(size_t W) { return W * (2 * sizeof(double2) + sizeof(double)); }
+    static size_t bytes(size_t W) { return W * (2 * sizeof(double2) + sizeof(double)); }
 };
 
 template <typename R>
@@ -84,7 +91,7 @@ template <> __device__ __forceinline__ float fdiv_(float a, float b) { return __
 template <> __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
 
 // Contiguous chunk of markers owned by one block (a multiple of 32, so every
-// warp's lanes see consecutive, cell-sorted markers).
+// warp's lanes see consecutive, sorted markers).
 __device__ __forceinline__ void block_chunk(long long np, long long &beg, long long &end)
 {
     long long chunk = (np + gridDim.x - 1) / gridDim.x;
@@ -101,9 +108,7 @@ __device__ __forceinline__ void block_chunk(long long np, long long &beg, long l
 //   p^(k+1) = p^n + dt Ebar - dt (A1+A0).D / (g(p^n,A1) + g(p^n,A0)),
 //   delta^(k+1) = dt (p^n + p^(k+1)) / (g(p^n,A1) + g(p^(k+1),A1)) / dx,
 //   j_i += w int_{x^n}^{x^n+delta^(k+1)} Lambda^1_i.
-// Each block owns a contiguous chunk of the cell-sorted markers; the deposit
-// goes through a per-warp register window (DepWindow), then the block's
-// shared-memory row (double), then one global double atomic per touched node.
+// In cell units with tau = dt/dx: p^(k+1) = p^n + tau (Ebar dx - (A1+A0).D dx/(...)).
 // ---------------------------------------------------------------------------
 template <int K, typename R>
 __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
@@ -116,7 +121,8 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     FieldTile<R> F = carve_tile<R>(reinterpret_cast<unsigned char *>(s_red + 32), W);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
-        F.store(i, A.ay[g], A.az[g], A.ebar[g], A.ga_y[g], A.ga_z[g]);
+        const int gm = g == 0 ? A.M - 1 : g - 1;
+        F.store(i, A.ay[g], A.az[g], A.ebar[g] * A.dx, A.ay[g] - A.ay[gm], A.az[g] - A.az[gm]);
         s_acc[i] = 0.0;
     }
     __syncthreads();
@@ -126,14 +132,14 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     const R *__restrict__ pp = static_cast<const R *>(A.P.p);
     R *__restrict__ dp = static_cast<R *>(A.P.delta);
     R *__restrict__ pnp = static_cast<R *>(A.P.pnew);
-    const R dt = (R)A.dt;
-    const R dtdx = (R)(A.dt / A.dx);
-    const R wdx = (R)(A.w * A.dx);
+    const R tau = (R)(A.dt / A.dx);
+    const double wdx = A.w * A.dx;
     const R dlim = (R)A.Dlim;
     const R one = R(1);
     R dmax = R(0);
     bool bad = false;
-    DepWindow<R, K + 4, K, K + 1, -2, 2> win;
+    // window: pieces in cells wb-3 .. wb+3, V1 nodes wb-K-2 .. wb+3
+    DepWindow<R, K + 6, K, K + 2, -3, 3> win;
     win.clear();
     int wb = INT_MIN;
 
@@ -146,9 +152,10 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
         const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
         if (lead == INT_MAX) break;                    // whole warp past the chunk end
         if (lead != wb) {
-            if (wb != INT_MIN) win.flush(s_acc, wb - K - 1 + H);
+            if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
             wb = lead;
         }
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
         if (!act) continue;
         const R t0 = tp[a];
         const R pn = pp[a];
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
             A0z += z * v[r];
         }
         const R g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
-        R dold = A.warm ? fdiv_(dtdx * pn, g0) : dp[a];
+        R dold = A.warm ? fdiv_(tau * pn, g0) : dp[a];
         if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
 
         const R s = t0 + dold;
@@ -181,7 +188,8 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
 
         R Eb = R(0), Dy = R(0), Dz = R(0);
         const R invd = (dold != R(0)) ? one / dold : R(0);
-        walk_path<K, R>(t0, dold, [&](int c, R h, const R *m, bool single) {
+        const int n1 = __reduce_max_sync(amask, path_pieces(t0, dold));
+        walk_uniform<K, R>(t0, dold, n1, [&](int c, R h, const R *m, int p) {
             R e = R(0), gy = R(0), gz = R(0);
 #pragma unroll
             for (int r = 0; r < K; ++r) {
@@ -191,7 +199,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
                 gy += m[r] * y;
                 gz += m[r] * z;
             }
-            const R f = single ? one : h * invd;
+            const R f = (dold != R(0)) ? h * invd : (p == 0 ? one : R(0));
             Eb += f * e;
             Dy += f * gy;
             Dz += f * gz;
@@ -199,19 +207,19 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
 
         const R q1 = one + A1y * A1y + A1z * A1z;
         const R g1 = sqrt_(q1 + pn * pn);
-        const R pnew = pn + dt * Eb - dt * fdiv_((A1y + A0y) * Dy + (A1z + A0z) * Dz, g1 + g0);
+        const R pnew = pn + tau * (Eb - fdiv_((A1y + A0y) * Dy + (A1z + A0z) * Dz, g1 + g0));
         const R g2 = sqrt_(q1 + pnew * pnew);
-        R dnew = fdiv_(dtdx * (pn + pnew), g1 + g2);
+        R dnew = fdiv_(tau * (pn + pnew), g1 + g2);
         if (!(fabs(dnew) <= dlim)) { bad = true; dnew = R(0); }
 
-        walk_path<K, R>(t0, dnew, [&](int c, R h, const R *m, bool) {
-            const R hw = wdx * h;
+        const int n2 = __reduce_max_sync(amask, path_pieces(t0, dnew));
+        walk_uniform<K, R>(t0, dnew, n2, [&](int c, R h, const R *m, int) {
             R val[K];
 #pragma unroll
-            for (int r = 0; r < K; ++r) val[r] = hw * m[r];
+            for (int r = 0; r < K; ++r) val[r] = h * m[r];
             if (!win.put(c0 + c - wb, val)) {
 #pragma unroll
-                for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], (double)val[r]);
+                for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], wdx * (double)val[r]);
             }
         });
 
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
         dp[a] = dnew;
         pnp[a] = pnew;
     }
-    if (wb != INT_MIN) win.flush(s_acc, wb - K - 1 + H);
+    if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
     if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
     block_max_to(&A.ctrl->dmax_bits, (double)dmax, s_red);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -277,10 +285,9 @@ __global__ void __launch_bounds__(256) k_current(CurrentArgs A)
         const R t0 = tp[a];
         R d = (R)(A.disp[A.P.id[a]] / A.dx);
         if (!(fabs(d) <= (R)A.Dlim)) { bad = true; continue; }
-        walk_path<K, R>(t0, d, [&](int c, R h, const R *m, bool) {
-            const double hw = wdx * (double)h;
+        walk_uniform<K, R>(t0, d, path_pieces(t0, d), [&](int c, R h, const R *m, int) {
 #pragma unroll
-            for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], hw * (double)m[r]);
+            for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], wdx * (double)(h * m[r]));
         });
     }
     if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
@@ -313,8 +320,8 @@ int launch_current(const CurrentArgs &a, int grid, int block, size_t smem, cudaS
 // ---------------------------------------------------------------------------
 // Subsystem II: one fixed-point sweep (Sec. 4.2).  Markers frozen at x; with
 // A0 = A^n_h(x), A1 = A^(k)_h(x):
-//   s_i += w (A0 + A1) Lambda^0_i(x) / (g(p,A0) + g(p,A1))   (y and z).
-// Same chunking and per-warp register windows as the subsystem-I sweep.
+//   s_i += w (A0 + A1) Lambda^0_i(x) / (g(p,A0) + g(p,A1))   (y and z);
+// the weight w enters at the window flush, in double.
 // ---------------------------------------------------------------------------
 template <int K, typename R>
 __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
@@ -340,9 +347,10 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
     const int32_t *__restrict__ cellp = A.P.cell;
     const R *__restrict__ tp = static_cast<const R *>(A.P.t);
     const R *__restrict__ pp = static_cast<const R *>(A.P.p);
-    const R w = (R)A.w;
+    const double w = A.w;
     const R one = R(1);
-    DepWindow<R, K + 3, K + 1, K + 1, -1, 1> wy, wz;
+    // window: marker cells wb .. wb+3 (wb = the warp's lowest), V0 nodes wb-K .. wb+3
+    DepWindow<R, K + 4, K + 1, K, 0, 3> wy, wz;
     wy.clear();
     wz.clear();
     int wb = INT_MIN;
@@ -356,8 +364,8 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
         if (lead == INT_MAX) break;
         if (lead != wb) {
             if (wb != INT_MIN) {
-                wy.flush(s_sy, wb - K - 1 + H);
-                wz.flush(s_sz, wb - K - 1 + H);
+                wy.flush(s_sy, wb - K + H, w);
+                wz.flush(s_sz, wb - K + H, w);
             }
             wb = lead;
         }
@@ -378,7 +386,7 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
         const R pp1 = one + p * p;
         const R g0 = sqrt_(pp1 + A0y * A0y + A0z * A0z);
         const R g1 = sqrt_(pp1 + A1y * A1y + A1z * A1z);
-        const R cf = fdiv_(w, g0 + g1);
+        const R cf = fdiv_(one, g0 + g1);
         const R fy = cf * (A0y + A1y), fz = cf * (A0z + A1z);
         R vy[K + 1], vz[K + 1];
 #pragma unroll
@@ -388,16 +396,16 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
         }
         if (!wy.put(c - wb, vy)) {
 #pragma unroll
-            for (int r = 0; r <= K; ++r) atomicAdd(&s_sy[c - r + H], (double)vy[r]);
+            for (int r = 0; r <= K; ++r) atomicAdd(&s_sy[c - r + H], w * (double)vy[r]);
         }
         if (!wz.put(c - wb, vz)) {
 #pragma unroll
-            for (int r = 0; r <= K; ++r) atomicAdd(&s_sz[c - r + H], (double)vz[r]);
+            for (int r = 0; r <= K; ++r) atomicAdd(&s_sz[c - r + H], w * (double)vz[r]);
         }
     }
     if (wb != INT_MIN) {
-        wy.flush(s_sy, wb - K - 1 + H);
-        wz.flush(s_sz, wb - K - 1 + H);
+        wy.flush(s_sy, wb - K + H, w);
+        wz.flush(s_sz, wb - K + H, w);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -618,7 +626,7 @@ __global__ void __launch_bounds__(256) k_load(long long np, int M, double dx, co
         pp[a] = (R)p[a];
         pnp[a] = (R)p[a];
         dp[a] = R(0);
-        P.id[a] = a;
+        P.id[a] = (int32_t)a;
     }
 }
 
@@ -652,43 +660,58 @@ int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Counting sort of the markers by cell (between steps; delta = 0, p_new = p).
-// counts: 2*M int32 scratch (histogram, then cursors).
+// Counting sort of the markers by key = cell * kVelBins + velocity bin, the
+// bin being the expected displacement tau p in whole cells (clamped), so that a
+// warp's markers share cells and piece counts.  Runs between steps (delta = 0,
+// p_new = p).  Atomics are aggregated per warp over equal keys.
+// counts: 2 * nkeys int32 (histogram, then cursors).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_hist(long long np, int M, const int32_t *cell, int32_t *counts)
+template <typename R>
+__device__ __forceinline__ int sort_key(int c, R p, float tau)
 {
-    extern __shared__ int32_t s_h[];
-    for (int i = threadIdx.x; i < M; i += blockDim.x) s_h[i] = 0;
-    __syncthreads();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < np; a += stride)
-        atomicAdd(&s_h[cell[a]], 1);
-    __syncthreads();
-    for (int i = threadIdx.x; i < M; i += blockDim.x)
-        if (s_h[i]) atomicAdd(&counts[i], s_h[i]);
-}
-
-__global__ void k_scan(int M, int32_t *counts)
-{
-    // exclusive scan of M counts into cursors (single block; M <= 8192)
-    __shared__ long long s_part[1024];
-    const int per = (M + blockDim.x - 1) / blockDim.x;
-    const int lo = threadIdx.x * per, hi = min(M, lo + per);
-    long long s = 0;
-    for (int i = lo; i < hi; ++i) s += counts[i];
-    s_part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long run = 0;
-        for (int i = 0; i < (int)blockDim.x; ++i) { long long v = s_part[i]; s_part[i] = run; run += v; }
-    }
-    __syncthreads();
-    long long run = s_part[threadIdx.x];
-    for (int i = lo; i < hi; ++i) { const int v = counts[i]; counts[M + i] = (int32_t)run; run += v; }
+    int b = (int)floorf((float)p * tau) + kVelBins / 2;
+    b = b < 0 ? 0 : (b >= kVelBins ? kVelBins - 1 : b);
+    return c * kVelBins + b;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_scatter(long long np, int M, PartPtrs S, PartPtrs D, int32_t *cursor)
+__global__ void __launch_bounds__(256) k_hist(long long np, float tau, PartPtrs S, int32_t *counts)
+{
+    const R *ps = static_cast<const R *>(S.p);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long a = base + threadIdx.x;
+        const bool act = a < np;
+        const int key = act ? sort_key(S.cell[a], ps[a], tau) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        if (act && lane == __ffs(grp) - 1) atomicAdd(&counts[key], __popc(grp));
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan(int nkeys, int32_t *counts)
+{
+    // exclusive scan of nkeys counts into cursors (single block)
+    __shared__ int s_part[1024];
+    const int per = (nkeys + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(nkeys, lo + per);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += counts[i];
+    s_part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const int v = threadIdx.x >= (unsigned)off ? s_part[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = s_part[threadIdx.x] - s;     // exclusive prefix of this thread's range
+    for (int i = lo; i < hi; ++i) { const int v = counts[i]; counts[nkeys + i] = run; run += v; }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_scatter(long long np, float tau, PartPtrs S, PartPtrs D,
+                                                 int32_t *cursor)
 {
     const R *ts = static_cast<const R *>(S.t);
     const R *ps = static_cast<const R *>(S.p);
@@ -697,12 +720,22 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, int M, PartPtrs S
     R *pnd = static_cast<R *>(D.pnew);
     R *dd = static_cast<R *>(D.delta);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < np; a += stride) {
-        const int c = S.cell[a];
-        const long long j = atomicAdd(&cursor[c], 1);
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long a = base + threadIdx.x;
+        const bool act = a < np;
+        const int c = act ? S.cell[a] : 0;
+        const R p = act ? ps[a] : R(0);
+        const int key = act ? sort_key(c, p, tau) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(grp) - 1;
+        int first = 0;
+        if (act && lane == leader) first = atomicAdd(&cursor[key], __popc(grp));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (!act) continue;
+        const long long j = (long long)first + __popc(grp & ((1u << lane) - 1u));
         D.cell[j] = c;
         td[j] = ts[a];
-        const R p = ps[a];
         pd[j] = p;
         pnd[j] = p;
         dd[j] = R(0);
@@ -710,17 +743,18 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, int M, PartPtrs S
     }
 }
 
-int launch_sort(int fp32, long long np, int M, PartPtrs src, PartPtrs dst, int32_t *counts,
-                int grid, int block, cudaStream_t s)
+int launch_sort(int fp32, long long np, int M, double tau, PartPtrs src, PartPtrs dst,
+                int32_t *counts, int grid, int block, cudaStream_t s)
 {
-    if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * (size_t)M, s) != cudaSuccess) return 1;
-    k_hist<<<grid, block, sizeof(int32_t) * M, s>>>(np, M, src.cell, counts);
-    k_scan<<<1, 1024, 0, s>>>(M, counts);
-    if (fp32) k_scatter<float><<<grid, block, 0, s>>>(np, M, src, dst, counts + M);
-    else k_scatter<double><<<grid, block, 0, s>>>(np, M, src, dst, counts + M);
+    const int nkeys = M * kVelBins;
+    if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * (size_t)nkeys, s) != cudaSuccess) return 1;
+    if (fp32) k_hist<float><<<grid, block, 0, s>>>(np, (float)tau, src, counts);
+    else k_hist<double><<<grid, block, 0, s>>>(np, (float)tau, src, counts);
+    k_scan<<<1, 1024, 0, s>>>(nkeys, counts);
+    if (fp32) k_scatter<float><<<grid, block, 0, s>>>(np, (float)tau, src, dst, counts + nkeys);
+    else k_scatter<double><<<grid, block, 0, s>>>(np, (float)tau, src, dst, counts + nkeys);
     return 0;
 }
-
 
 // ---------------------------------------------------------------------------
 // Dynamic shared-memory opt-in (per kernel instantiation) and occupancy.
@@ -762,6 +796,3 @@ int pic_set_smem_attrs(size_t s1, size_t s2, size_t s3)
 {
     return pic::set_attrs_r<float>(s1, s2, s3) | pic::set_attrs_r<double>(s1, s2, s3);
 }
-
-namespace pic {
-}  // namespace pic
