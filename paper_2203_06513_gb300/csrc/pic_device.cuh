@@ -264,28 +264,49 @@ __device__ __forceinline__ int path_pieces(R t0, R d)
 
 template <typename R> __device__ __forceinline__ R clamp01(R v) { return v < R(0) ? R(0) : (v > R(1) ? R(1) : v); }
 
-// Branch-free walk of the path t0 -> t0 + d split at knots: piece p (p = 0..npc-1)
-// lies in cell c = sign(d) p relative to the start cell, on the local interval
-// [lo, hi] = clamp([min(t0,s), max(t0,s)] - c, 0, 1).  The caller passes the warp
-// maximum of the piece counts, so every lane runs the same trip count; pieces
-// beyond a lane's own count have zero length.  visit(c, h, m, p) gets the signed
-// piece length h (cells) and the means m[r] of the degree-(K-1) pieces over it.
+// Branch-free walk of the path t0 -> s = t0 + d split at knots.  Piece p lies in
+// cell c = sign(d) p relative to the start cell.  The piece lengths are formed
+// from d and the knot distances, never as differences of clamped coordinates,
+// so a single-piece path has length exactly d:
+//   one piece:   t0 -> s                       (h = d)
+//   first piece: t0 -> the knot ahead           (h = 1 - t0, or -t0 moving left)
+//   middle:      a whole cell                   (h = +-1, midpoint 1/2)
+//   last piece:  the knot behind -> tl = s - floor(s)  (h = tl, or tl - 1 moving left)
+// The caller passes the warp maximum of the piece counts, so every lane runs the
+// same trip count; pieces beyond a lane's own count have zero length.
+// visit(c, h, m, p) gets the signed piece length h (cells) and the means m[r] of
+// the degree-(K-1) pieces over it.
 template <int K, typename R, class Visit>
 __device__ __forceinline__ void walk_uniform(R t0, R d, int npc, Visit &&visit)
 {
     constexpr int D = K - 1;
     const R s = t0 + d;
-    const R umin = s < t0 ? s : t0;
-    const R umax = s < t0 ? t0 : s;
-    const int sg = d < R(0) ? -1 : 1;
+    const R fl = floor_(s);
+    const int n = abs((int)fl) + 1;          // this lane's piece count
+    const R tl = s - fl;                     // local offset of the end point
+    const bool right = d >= R(0);
+    const int sg = right ? 1 : -1;
     R m[D + 1];
     for (int p = 0; p < npc; ++p) {
-        const int c = sg * p;
-        const R lo = clamp01(umin - R(c));
-        const R hi = clamp01(umax - R(c));
-        const R len = hi - lo;
-        piece_means<D, R>(R(0.5) * (lo + hi), len, m);
-        visit(c, sg > 0 ? len : -len, m, p);
+        R h, tm;
+        if (n == 1) {
+            h = (p == 0) ? d : R(0);
+            tm = R(0.5) * (t0 + s);
+        } else if (p == 0) {
+            h = right ? R(1) - t0 : -t0;
+            tm = t0 + R(0.5) * h;
+        } else if (p == n - 1) {
+            h = right ? tl : tl - R(1);
+            tm = R(0.5) * (right ? tl : R(1) + tl);
+        } else if (p < n) {
+            h = R(sg);
+            tm = R(0.5);
+        } else {
+            h = R(0);
+            tm = R(0.5);
+        }
+        piece_means<D, R>(tm, h, m);
+        visit(sg * p, h, m, p);
     }
 }
 
