@@ -163,6 +163,41 @@ int pic_timing_read(pic_handle *h, double out[8]);
 /* Release the handle and all memory it owns.  NULL is allowed. */
 int pic_destroy(pic_handle *h);
 
+/* ---------------------------------------------------------------------
+ * Learned warm start of the subsystem-I fixed point.  The paper solves each
+ * implicit substep by fixed-point iteration from x^(0) = x^n (Sec. 4.2); a
+ * small network can propose x^(0) instead.  The iteration still runs to the
+ * same tolerance, so the converged state does not depend on the proposal.
+ * Network: 6 inputs (cell-relative x, p, E_x(x^n), A_y(x^n), A_z(x^n), dt),
+ * normalised by (v - shift) * scale; three hidden layers of width 64, GELU
+ * (tanh form); 2 outputs times out_scale, read as
+ *   y0 = (x^{n+1} - x^n - dt p / gamma(p, A(x^n))) / dt^2,
+ *   y1 = (p^{n+1} - p^n - dt E_x(x^n)) / dt^2.
+ * Parameters: 8898 floats, W1 (64x6 row-major [out][in]), b1, W2 (64x64), b2,
+ * W3, b3, W4 (2x64), b4.  norm: 14 floats, shift[6], scale[6], out_scale[2].
+ * Inference: bf16 tensor cores with fp32 accumulation; training: fp32.
+ * All X / T / Y / grad arrays are device pointers, row-major per sample.
+ * --------------------------------------------------------------------- */
+typedef struct pic_mlp pic_mlp;
+
+/* Create a network on the current device.  params: 8898 host floats or NULL
+ * (zeros); norm: 14 host floats (required). */
+int pic_mlp_create(const float *params, const float *norm, void *stream, pic_mlp **out);
+int pic_mlp_destroy(pic_mlp *m);
+/* Copy the current fp32 parameters to host memory (8898 floats). */
+int pic_mlp_get_params(pic_mlp *m, float *params_host);
+/* Loss and its gradient on a batch: loss = mean_b sum_o (y_o - T_o / out_scale_o)^2
+ * with y the normalised outputs of the fp32 network on X[B][6]; grad_out (device,
+ * 8898 floats) and loss_out (host) may be NULL. */
+int pic_mlp_grad(pic_mlp *m, const float *X, const float *T, int64_t B, float *grad_out, double *loss_out);
+/* One Adam step (beta 0.9/0.999, eps 1e-8) on the batch loss above. */
+int pic_mlp_train_step(pic_mlp *m, const float *X, const float *T, int64_t B, float lr, double *loss_out);
+/* Y[B][2] = scaled outputs of the bf16 tensor-core network on raw features X[B][6]. */
+int pic_mlp_infer(pic_mlp *m, const float *X, int64_t B, float *Y);
+/* Attach a network to a handle created with warm_start = PIC_WARM_MLP (the
+ * handle borrows it: keep it alive while the handle steps).  NULL detaches. */
+int pic_set_warm_mlp(pic_handle *h, pic_mlp *m);
+
 /* Message of the last error on h; with h == NULL, the message of the last
  * failed pic_init or pic_deposit_current_noalloc on the calling thread. */
 /* Message of the last error on h; with h == NULL, the message of the last

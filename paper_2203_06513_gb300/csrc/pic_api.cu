@@ -14,6 +14,10 @@
 
 using namespace pic;
 
+// warm-start network accessors (pic_mlp.cu)
+const float *mlp_params(const pic_mlp *m);
+const float *mlp_norm(const pic_mlp *m);
+
 int pic_set_smem_attrs(size_t s1, size_t s2, size_t s3);
 static thread_local std::string g_init_error;
 
@@ -60,6 +64,10 @@ struct pic_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double t_sw1 = 0, t_sw2 = 0, t_solve = 0;
     long long n_sw1 = 0, n_sw2 = 0, n_solve = 0, launches = 0, marker_sweeps = 0;
+
+    double t_warm = 0;
+    long long n_warm = 0;
+    pic_mlp *mlp = nullptr;         // borrowed warm-start network
 
     std::string err;
 };
@@ -451,6 +459,20 @@ static int substep1(pic_handle *h, int *iters)
     c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
     c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6;   // FP32: estimated position error, cells relative to max(1, |delta|)
     c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 1; c.ctrl = h->ctrl;
+    if (h->cfg.warm_start == PIC_WARM_MLP) {
+        // learned proposal for delta^(0), written over the zero iterate
+        if (!h->mlp) return fail(h, PIC_ERR_INVALID, "warm_start = PIC_WARM_MLP but no network attached");
+        WarmArgs wa{};
+        wa.M = h->M; wa.K = h->K; wa.fp32 = h->fp32; wa.np = h->np; wa.dx = h->dx; wa.dt = h->cfg.dt;
+        wa.P = cur_parts(h);
+        wa.ex = h->ex; wa.ay = h->ay; wa.az = h->az;
+        wa.params = mlp_params(h->mlp); wa.norm = mlp_norm(h->mlp);
+        if ((rc = timed_begin(h))) return rc;
+        if (launch_warm_mlp(wa, h->num_sms * 2, h->stream))
+            return fail(h, PIC_ERR_CUDA, "warm-start network: launch setup failed");
+        CKL_N("launch_warm_mlp");
+        if ((rc = timed_end(h, &h->t_warm, &h->n_warm))) return rc;
+    }
     int it = 0;
     for (;;) {
         a.j = h->jb[it & 1];
@@ -692,6 +714,13 @@ extern "C" int pic_gather(pic_handle *h, int32_t field, double *out)
     if (launch_gather(a, d, particle_grid(h), 256, h->stream)) return fail(h, PIC_ERR_INVALID, "bad degree");
     CKL_N("launch_gather");
     return sync(h);
+}
+
+extern "C" int pic_set_warm_mlp(pic_handle *h, pic_mlp *m)
+{
+    if (!h) return PIC_ERR_INVALID;
+    h->mlp = m;
+    return PIC_OK;
 }
 
 extern "C" int pic_timing_enable(pic_handle *h, int32_t on)

@@ -116,6 +116,17 @@ int launch_energy_grid(int M, int K, double dx, const double *rowM0, const doubl
                        cudaStream_t s);
 int launch_ctrl_reset(DevCtrl *ctrl, cudaStream_t s);
 
+// learned warm start (pic_mlp.cu)
+struct WarmArgs {
+    int M, K, fp32;
+    long long np;
+    double dx, dt;
+    PartPtrs P;
+    const double *ex, *ay, *az;
+    const float *params, *norm;
+};
+int launch_warm_mlp(const WarmArgs &a, int grid, cudaStream_t s);
+
 // message returned by pic_last_error(NULL) on the calling thread
 void set_thread_error(const char *msg);
 

@@ -122,7 +122,12 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
         const int gm = g == 0 ? A.M - 1 : g - 1;
-        F.store(i, A.ay[g], A.az[g], A.ebar[g] * A.dx, A.ay[g] - A.ay[gm], A.az[g] - A.az[gm]);
+        // the differences (G a)_j dx are formed from the coefficients as staged
+        // (rounded to R), so that sum_j m_j (G a)_j dx (x1 - x0)/dx equals
+        // A(x1) - A(x0) of the staged field: the discrete gradient of the A-term
+        // stays exact for the field the markers see
+        const R ay = (R)A.ay[g], aym = (R)A.ay[gm], az = (R)A.az[g], azm = (R)A.az[gm];
+        F.store(i, ay, az, A.ebar[g] * A.dx, (double)(ay - aym), (double)(az - azm));
         s_acc[i] = 0.0;
     }
     __syncthreads();

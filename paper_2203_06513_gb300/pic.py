@@ -229,3 +229,76 @@ class Pic:
 
 def version() -> str:
     return load().pic_version().decode()
+
+
+N_MLP_PARAMS = 8898
+
+
+class Mlp:
+    """The warm-start network (see pic_mlp_* in include/pic.h).  X, T, Y are torch
+    float32 CUDA tensors of shape (B, 6), (B, 2), (B, 2)."""
+
+    def __init__(self, norm, params=None, stream=None):
+        L = load()
+        self._lib = L
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.pic_mlp_create.argtypes = [fp, fp, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        L.pic_mlp_destroy.argtypes = [ctypes.c_void_p]
+        L.pic_mlp_get_params.argtypes = [ctypes.c_void_p, fp]
+        L.pic_mlp_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+        L.pic_mlp_train_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+        L.pic_mlp_infer.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        L.pic_set_warm_mlp.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        norm = np.ascontiguousarray(norm, dtype=np.float32)
+        assert norm.size == 14
+        self.norm = norm
+        pr = None
+        if params is not None:
+            pr = np.ascontiguousarray(params, dtype=np.float32)
+            assert pr.size == N_MLP_PARAMS
+        h = ctypes.c_void_p()
+        rc = L.pic_mlp_create(None if pr is None else pr.ctypes.data_as(fp), norm.ctypes.data_as(fp),
+                              ctypes.c_void_p(0 if stream is None else int(stream)), ctypes.byref(h))
+        if rc != PIC_OK:
+            raise PicError(rc, L.pic_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc != PIC_OK:
+            raise PicError(rc, self._lib.pic_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pic_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(N_MLP_PARAMS, dtype=np.float32)
+        self._check(self._lib.pic_mlp_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def grad(self, X, T, grad_out=None) -> float:
+        loss = ctypes.c_double()
+        self._check(self._lib.pic_mlp_grad(self._h, _vptr(X), _vptr(T), X.shape[0], _vptr(grad_out),
+                                           ctypes.byref(loss)))
+        return loss.value
+
+    def train_step(self, X, T, lr: float) -> float:
+        loss = ctypes.c_double()
+        self._check(self._lib.pic_mlp_train_step(self._h, _vptr(X), _vptr(T), X.shape[0], lr,
+                                                 ctypes.byref(loss)))
+        return loss.value
+
+    def infer(self, X, Y):
+        self._check(self._lib.pic_mlp_infer(self._h, _vptr(X), X.shape[0], _vptr(Y)))
+
+    def attach(self, sim: "Pic"):
+        self._check(self._lib.pic_set_warm_mlp(sim._h, self._h))
