@@ -255,6 +255,102 @@ struct DepWindow {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Scaled B-spline arithmetic for the sweep kernels.  A rounded reciprocal such
+// as 1/3 (in float 1 + 3e-8 too large) would scale every basis value by the same
+// factor; through the discrete-gradient identity such a systematic bias becomes a
+// steady energy drift.  So the kernels use integer-coefficient forms and fold all
+// normalisations into the double-precision staging of the fields and the
+// double-precision flush of the deposits:
+//   bspline_scaled<D>:  v[r] = D! N^D(r + t)  (triangle without the 1/n factors)
+//   piece_means_scaled<D>: m[r] = S_D * (mean of N^D(r + t) over the piece), with
+//   S_D = X_D D! chosen so that every coefficient of the midpoint formula is a
+//   dyadic rational (X_1 = 1, X_2 = 3, X_3 = 1, X_4 = 5); whole-cell means are
+//   then small integers, e.g. (1, 4, 1) for D = 2.
+// ---------------------------------------------------------------------------
+template <int D> struct MeanScale;
+template <> struct MeanScale<0> { static constexpr int X = 1, S = 1; };
+template <> struct MeanScale<1> { static constexpr int X = 1, S = 1; };
+template <> struct MeanScale<2> { static constexpr int X = 3, S = 6; };
+template <> struct MeanScale<3> { static constexpr int X = 1, S = 6; };
+template <> struct MeanScale<4> { static constexpr int X = 5, S = 120; };
+
+template <int D> struct Fact { static constexpr int v = D * Fact<D - 1>::v; };
+template <> struct Fact<0> { static constexpr int v = 1; };
+
+template <int D, typename R>
+__device__ __forceinline__ void bspline_scaled(R t, R *v)
+{
+    v[0] = R(1);
+#pragma unroll
+    for (int n = 1; n <= D; ++n) {
+        v[n] = (R(1) - t) * v[n - 1];
+#pragma unroll
+        for (int r = n - 1; r >= 1; --r) v[r] = (t + R(r)) * v[r] + (R(n + 1 - r) - t) * v[r - 1];
+        v[0] = t * v[0];
+    }
+}
+
+// m[r] = S_D * mean over [tm - h/2, tm + h/2] of N^D(r + t), exact for D <= 4:
+// mean = f(tm) + f'' h^2/24 + f'''' h^4/1920 with f'' and f'''' from the
+// second and fourth differences of the lower levels of the (scaled) triangle.
+template <int D, typename R>
+__device__ __forceinline__ void piece_means_scaled(R tm, R h, R *m)
+{
+    static_assert(D >= 1 && D <= 4, "piece degree");
+    constexpr int X = MeanScale<D>::X;
+    R l2[D + 1], l4[D + 1];
+    m[0] = R(1);
+    if (D == 2) l2[0] = R(1);
+    if (D == 4) l4[0] = R(1);
+#pragma unroll
+    for (int n = 1; n <= D; ++n) {
+        m[n] = (R(1) - tm) * m[n - 1];
+#pragma unroll
+        for (int r = n - 1; r >= 1; --r) m[r] = (tm + R(r)) * m[r] + (R(n + 1 - r) - tm) * m[r - 1];
+        m[0] = tm * m[0];
+        if (n == D - 2) {
+#pragma unroll
+            for (int r = 0; r <= (D - 2 > 0 ? D - 2 : 0); ++r) l2[r] = m[r];
+        }
+        if (n == D - 4) {
+#pragma unroll
+            for (int r = 0; r <= (D - 4 > 0 ? D - 4 : 0); ++r) l4[r] = m[r];
+        }
+    }
+    if (D >= 2) {
+        // X D! N'' h^2/24 = h^2 * (X D (D-1) / 24) * (second difference of (D-2)! N^{D-2})
+        const R c2 = R(X * D * (D - 1)) / R(24);           // 1/4, 1/4, 5/2: dyadic
+        const R hh = h * h * c2;
+#pragma unroll
+        for (int r = 0; r <= D; ++r) {
+            R a0 = (r <= D - 2) ? l2[r] : R(0);
+            R a1 = (r - 1 >= 0 && r - 1 <= D - 2) ? l2[r - 1] : R(0);
+            R a2 = (r - 2 >= 0 && r - 2 <= D - 2) ? l2[r - 2] : R(0);
+            m[r] = R(X) * m[r] + hh * (a0 - R(2) * a1 + a2);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r <= D; ++r) m[r] = R(X) * m[r];
+    }
+    if (D >= 4) {
+        // X D! N'''' h^4/1920 = h^4 * (X D(D-1)(D-2)(D-3) / 1920) * (fourth difference of N^0)
+        const R c4 = R(X * D * (D - 1) * (D - 2) * (D - 3)) / R(1920);   // 1/16
+        const R h4 = h * h * h * h * c4;
+        const R d4[5] = {R(1), R(-4), R(6), R(-4), R(1)};
+#pragma unroll
+        for (int r = 0; r <= D; ++r) {
+            R s = R(0);
+#pragma unroll
+            for (int q = 0; q <= 4; ++q) {
+                const int i = r - q;
+                if (i >= 0 && i <= D - 4) s += d4[q] * l4[i];
+            }
+            m[r] += h4 * s;
+        }
+    }
+}
+
 // Number of pieces of the path from local offset t0 by d cells: 1 + knots crossed.
 template <typename R>
 __device__ __forceinline__ int path_pieces(R t0, R d)
@@ -274,8 +370,8 @@ template <typename R> __device__ __forceinline__ R clamp01(R v) { return v < R(0
 //   last piece:  the knot behind -> tl = s - floor(s)  (h = tl, or tl - 1 moving left)
 // The caller passes the warp maximum of the piece counts, so every lane runs the
 // same trip count; pieces beyond a lane's own count have zero length.
-// visit(c, h, m, p) gets the signed piece length h (cells) and the means m[r] of
-// the degree-(K-1) pieces over it.
+// visit(c, h, m, p) gets the signed piece length h (cells) and the scaled means
+// m[r] = S_{K-1} * mean of the degree-(K-1) pieces over it (piece_means_scaled).
 template <int K, typename R, class Visit>
 __device__ __forceinline__ void walk_uniform(R t0, R d, int npc, Visit &&visit)
 {
@@ -305,7 +401,7 @@ __device__ __forceinline__ void walk_uniform(R t0, R d, int npc, Visit &&visit)
             h = R(0);
             tm = R(0.5);
         }
-        piece_means<D, R>(tm, h, m);
+        piece_means_scaled<D, R>(tm, h, m);
         visit(sg * p, h, m, p);
     }
 }

@@ -119,15 +119,23 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     double *s_acc = reinterpret_cast<double *>(smem);
     double *s_red = s_acc + W;
     FieldTile<R> F = carve_tile<R>(reinterpret_cast<unsigned char *>(s_red + 32), W);
+    // scaled arithmetic (see piece_means_scaled): the basis is K! N^K, the path
+    // means are S1 = S_{K-1} times the means of N^{K-1}; so the staged fields are
+    // a / K! and ebar dx / S1, the A-term sum is multiplied by K!/S1 = DK, and the
+    // deposit by w dx / S1 when flushed
+    constexpr int S1 = MeanScale<K - 1>::S;
+    constexpr int DK = K / MeanScale<K - 1>::X;
+    const double inv_fact = 1.0 / (double)Fact<K>::v;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
         const int gm = g == 0 ? A.M - 1 : g - 1;
-        // the differences (G a)_j dx are formed from the coefficients as staged
-        // (rounded to R), so that sum_j m_j (G a)_j dx (x1 - x0)/dx equals
-        // A(x1) - A(x0) of the staged field: the discrete gradient of the A-term
-        // stays exact for the field the markers see
-        const R ay = (R)A.ay[g], aym = (R)A.ay[gm], az = (R)A.az[g], azm = (R)A.az[gm];
-        F.store(i, ay, az, A.ebar[g] * A.dx, (double)(ay - aym), (double)(az - azm));
+        // the differences of a are formed from the coefficients as staged (rounded
+        // to R), so that the path mean of dA/dx times (x1 - x0) equals A(x1) - A(x0)
+        // of the staged field: the discrete gradient of the A-term stays exact for
+        // the field the markers see
+        const R ay = (R)(A.ay[g] * inv_fact), aym = (R)(A.ay[gm] * inv_fact);
+        const R az = (R)(A.az[g] * inv_fact), azm = (R)(A.az[gm] * inv_fact);
+        F.store(i, ay, az, A.ebar[g] * A.dx / S1, (double)(ay - aym), (double)(az - azm));
         s_acc[i] = 0.0;
     }
     __syncthreads();
@@ -138,7 +146,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     R *__restrict__ dp = static_cast<R *>(A.P.delta);
     R *__restrict__ pnp = static_cast<R *>(A.P.pnew);
     const R tau = (R)(A.dt / A.dx);
-    const double wdx = A.w * A.dx;
+    const double wdx = A.w * A.dx / S1;      // deposit flush scale
     const R dlim = (R)A.Dlim;
     const R one = R(1);
     R dmax = R(0);
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
         const R t0 = tp[a];
         const R pn = pp[a];
         R v[K + 1];
-        bspline_vals<K, R>(t0, v);
+        bspline_scaled<K, R>(t0, v);
         R A0y = R(0), A0z = R(0);
 #pragma unroll
         for (int r = 0; r <= K; ++r) {
@@ -181,7 +189,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
         const R s = t0 + dold;
         const R fs = floor_(s);
         const int c1 = c0 + (int)fs;
-        bspline_vals<K, R>(s - fs, v);
+        bspline_scaled<K, R>(s - fs, v);
         R A1y = R(0), A1z = R(0);
 #pragma unroll
         for (int r = 0; r <= K; ++r) {
@@ -209,6 +217,8 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
             Dy += f * gy;
             Dz += f * gz;
         });
+        Dy *= R(DK);
+        Dz *= R(DK);
 
         const R q1 = one + A1y * A1y + A1z * A1z;
         const R g1 = sqrt_(q1 + pn * pn);
@@ -229,7 +239,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
         });
 
         R inc = fabs(dnew - dold);
-        if (Real<R>::fp32) inc = inc / fmax(one, fabs(dnew));
+        if (Real<R>::fp32) inc = __fdividef(inc, fmax(one, fabs(dnew)));   // convergence metric only
         dmax = (inc > dmax || inc != inc) ? inc : dmax;
         dp[a] = dnew;
         pnp[a] = pnew;
@@ -282,7 +292,7 @@ __global__ void __launch_bounds__(256) k_current(CurrentArgs A)
     for (int i = threadIdx.x; i < W; i += blockDim.x) s_acc[i] = 0.0;
     __syncthreads();
     const R *tp = static_cast<const R *>(A.P.t);
-    const double wdx = A.w * A.dx;
+    const double wdx = A.w * A.dx / MeanScale<K - 1>::S;   // walk_uniform returns scaled means
     bool bad = false;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
@@ -339,12 +349,14 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
     using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
     R2 *s_an = reinterpret_cast<R2 *>(s_sz + W);
     R2 *s_ak = s_an + W;
+    // scaled basis K! N^K: coefficients staged as a / K!, deposits flushed times w / K!
+    const double inv_fact = 1.0 / (double)Fact<K>::v;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
-        s_an[i].x = (R)A.an_y[g];
-        s_an[i].y = (R)A.an_z[g];
-        s_ak[i].x = (R)A.ak_y[g];
-        s_ak[i].y = (R)A.ak_z[g];
+        s_an[i].x = (R)(A.an_y[g] * inv_fact);
+        s_an[i].y = (R)(A.an_z[g] * inv_fact);
+        s_ak[i].x = (R)(A.ak_y[g] * inv_fact);
+        s_ak[i].y = (R)(A.ak_z[g] * inv_fact);
         s_sy[i] = 0.0;
         s_sz[i] = 0.0;
     }
@@ -352,7 +364,7 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
     const int32_t *__restrict__ cellp = A.P.cell;
     const R *__restrict__ tp = static_cast<const R *>(A.P.t);
     const R *__restrict__ pp = static_cast<const R *>(A.P.p);
-    const double w = A.w;
+    const double w = A.w * inv_fact;
     const R one = R(1);
     // window: marker cells wb .. wb+3 (wb = the warp's lowest), V0 nodes wb-K .. wb+3
     DepWindow<R, K + 4, K + 1, K, 0, 3> wy, wz;
@@ -378,7 +390,7 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
         const R t = tp[a];
         const R p = pp[a];
         R v[K + 1];
-        bspline_vals<K, R>(t, v);
+        bspline_scaled<K, R>(t, v);
         R A0y = R(0), A0z = R(0), A1y = R(0), A1z = R(0);
 #pragma unroll
         for (int r = 0; r <= K; ++r) {
