@@ -289,17 +289,20 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
         return bail(PIC_ERR_CUDA);
 
     const size_t np = (size_t)h->np, M = (size_t)h->M;
+    // marker arrays are padded by 64 entries: the sweeps' bulk copies round a
+    // tile's byte count up to a multiple of 16 and may read up to 3 entries past N_p
+    const size_t npa = np + 64;
     for (int b = 0; b < 2; ++b) {
-        if ((rc = dalloc(h, &h->P[b].cell, np))) return bail(rc);
-        if ((rc = dalloc(h, (char **)&h->P[b].t, np * h->rsize))) return bail(rc);
-        if ((rc = dalloc(h, (char **)&h->P[b].p, np * h->rsize))) return bail(rc);
-        if ((rc = dalloc(h, &h->P[b].id, np))) return bail(rc);
+        if ((rc = dalloc(h, &h->P[b].cell, npa))) return bail(rc);
+        if ((rc = dalloc(h, (char **)&h->P[b].t, npa * h->rsize))) return bail(rc);
+        if ((rc = dalloc(h, (char **)&h->P[b].p, npa * h->rsize))) return bail(rc);
+        if ((rc = dalloc(h, &h->P[b].id, npa))) return bail(rc);
         if ((rc = dalloc(h, &h->jb[b], M))) return bail(rc);
         if ((rc = dalloc(h, &h->sy[b], M))) return bail(rc);
         if ((rc = dalloc(h, &h->sz[b], M))) return bail(rc);
     }
-    if ((rc = dalloc(h, (char **)&h->delta, np * h->rsize))) return bail(rc);
-    if ((rc = dalloc(h, (char **)&h->pnew, np * h->rsize))) return bail(rc);
+    if ((rc = dalloc(h, (char **)&h->delta, npa * h->rsize))) return bail(rc);
+    if ((rc = dalloc(h, (char **)&h->pnew, npa * h->rsize))) return bail(rc);
     double **grid_arrays[] = {&h->ex, &h->ey, &h->ez, &h->ay, &h->az, &h->ek, &h->ebar, &h->ga_y,
                               &h->ga_z, &h->eky, &h->ekz, &h->aky, &h->akz, &h->by, &h->bz,
                               &h->r0y, &h->r0z, &h->rho, &h->work};
@@ -415,6 +418,8 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
 // ------------------------------------------------------------------ substeps
 static int check_status(pic_handle *h, int which)
 {
+    if (h->h_ctrl->status & STATUS_TIMEOUT)
+        return fail(h, PIC_ERR_CUDA, "subsystem %d: a bounded wait on a bulk copy gave up", which);
     if (h->h_ctrl->status & STATUS_NUMERIC)
         return fail(h, PIC_ERR_NUMERIC, "subsystem %d: non-finite value or displacement beyond c dt", which);
     if (h->h_ctrl->status & STATUS_NOCONV)
@@ -511,6 +516,7 @@ static int substep2(pic_handle *h, int *iters)
     CKL_N("launch_prep2");
     if ((rc = conv_plain(h, h->d_tapP, h->tapP_start, h->tapP_n, h->by, h->r0y, h->bz, h->r0z))) return rc;
     Sweep2Args a{};
+    a.status = &h->ctrl->status;
     a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.w = h->cfg.weight;
     a.P = cur_parts(h);
     a.an_y = h->ay; a.an_z = h->az; a.ak_y = h->aky; a.ak_z = h->akz;
@@ -680,6 +686,7 @@ extern "C" int pic_deposit(pic_handle *h, int32_t kind, const double *aux, doubl
         if (!aux) return fail(h, PIC_ERR_INVALID, "SUSCEPT needs a*");
         CK(cudaMemsetAsync(out, 0, sizeof(double) * 2 * h->M, h->stream));
         Sweep2Args a{};
+        a.status = &h->ctrl->status;
         a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.w = h->cfg.weight;
         a.P = cur_parts(h);
         a.an_y = h->ay; a.an_z = h->az; a.ak_y = aux; a.ak_z = aux + h->M;

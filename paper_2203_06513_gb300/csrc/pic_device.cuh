@@ -31,7 +31,65 @@ struct DevCtrl {
 enum : int {
     STATUS_NUMERIC = 1,    // NaN/Inf or displacement beyond the halo
     STATUS_NOCONV  = 2,
+    STATUS_TIMEOUT = 4,    // a bounded wait on a bulk copy gave up
 };
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (the TMA engine's 1-D bulk mode) into shared memory,
+// completed on an mbarrier.  Every wait is bounded: after kMaxWaitTries polls it
+// returns false and the caller records STATUS_TIMEOUT and leaves.  Addresses and
+// sizes must be multiples of 16 bytes.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kMaxWaitTries = 1ull << 26;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (unsigned long long i = 0; i < kMaxWaitTries; ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v)
 {

@@ -149,7 +149,7 @@ __device__ void decide(const ConvArgs &A)
         c->status |= STATUS_NOCONV;
         stop = true;
     }
-    if (c->status & STATUS_NUMERIC) stop = true;
+    if (c->status & (STATUS_NUMERIC | STATUS_TIMEOUT)) stop = true;
     c->converged = stop ? 1 : 0;
     c->dprev_bits = c->dmax_bits;
     c->eprev_bits = c->emax_bits;

@@ -39,6 +39,7 @@ struct Sweep2Args {
     PartPtrs P;
     const double *an_y, *an_z, *ak_y, *ak_z;
     double *s_y, *s_z;
+    int *status;        // error bits (STATUS_TIMEOUT)
 };
 
 struct CurrentArgs {

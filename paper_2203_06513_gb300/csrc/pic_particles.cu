@@ -100,6 +100,32 @@ __device__ __forceinline__ void block_chunk(long long np, long long &beg, long l
     end = beg + chunk < np ? beg + chunk : np;
 }
 
+// Markers stream through shared memory in tiles of kTile (a block's chunk is cut
+// into tiles; tile i goes to stage i % 2).  One thread issues the bulk copies of
+// a tile's arrays (cp.async.bulk, completed on the stage's mbarrier) two tiles
+// ahead of the consumers, so the DRAM latency of the next tile overlaps the
+// arithmetic on the current one.  The marker arrays are allocated with padding,
+// so a tile's byte count may be rounded up to a multiple of 16.
+constexpr int kTileU = 4;                      // markers per thread per tile
+constexpr int kTile = 256 * kTileU;            // markers per tile (block of 256)
+
+struct TileBars {
+    unsigned long long full[2];
+};
+
+// Returns false (block-uniform) when a bounded wait gave up; the caller then
+// drains the copies it has in flight (bounded) and leaves.
+__device__ __forceinline__ bool tile_wait(TileBars &B, long long i)
+{
+    const bool ok = mbar_wait(&B.full[i & 1], (unsigned)((i >> 1) & 1));
+    return !__syncthreads_or(!ok);
+}
+
+__device__ __forceinline__ void tile_drain(TileBars &B, long long i, long long ntile)
+{
+    for (long long k = i; k < ntile && k < i + 2; ++k) mbar_wait(&B.full[k & 1], (unsigned)((k >> 1) & 1));
+}
+
 // ---------------------------------------------------------------------------
 // Subsystem I: one Picard sweep (Sec. 4.2).  Per marker, with x^n = (c0, t0),
 // the iterate x^(k) = x^n + delta^(k) and ebar = (e^n + e^(k))/2:
@@ -113,12 +139,52 @@ __device__ __forceinline__ void block_chunk(long long np, long long &beg, long l
 template <int K, typename R>
 __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int H = A.H;
     const int W = A.M + 2 * H;
-    double *s_acc = reinterpret_cast<double *>(smem);
+    TileBars &Bars = *reinterpret_cast<TileBars *>(smem);
+    unsigned char *st = smem + 128;
+    int32_t *s_cell[2];
+    R *s_t[2], *s_p[2], *s_d[2];
+    for (int b = 0; b < 2; ++b) {
+        s_cell[b] = reinterpret_cast<int32_t *>(st);
+        s_t[b] = reinterpret_cast<R *>(st + kTile * sizeof(int32_t));
+        s_p[b] = s_t[b] + kTile;
+        s_d[b] = s_p[b] + kTile;
+        st += kTile * (sizeof(int32_t) + 3 * sizeof(R));
+    }
+    double *s_acc = reinterpret_cast<double *>(st);
     double *s_red = s_acc + W;
     FieldTile<R> F = carve_tile<R>(reinterpret_cast<unsigned char *>(s_red + 32), W);
+
+    long long beg, end;
+    block_chunk(A.np, beg, end);
+    const long long ntile = end > beg ? (end - beg + kTile - 1) / kTile : 0;
+    const bool need_delta = !A.warm;
+    auto issue = [&](long long i) {            // one thread: copies of tile i into stage i % 2
+        const long long s0 = beg + i * kTile;
+        long long n = end - s0 < kTile ? end - s0 : kTile;
+        n = (n + 3) & ~3LL;
+        const int b = (int)(i & 1);
+        const unsigned bi = (unsigned)(n * sizeof(int32_t)), br = (unsigned)(n * sizeof(R));
+        fence_proxy_async();
+        mbar_expect_tx(&Bars.full[b], bi + 2 * br + (need_delta ? br : 0u));
+        bulk_g2s(s_cell[b], A.P.cell + s0, bi, &Bars.full[b]);
+        bulk_g2s(s_t[b], static_cast<const R *>(A.P.t) + s0, br, &Bars.full[b]);
+        bulk_g2s(s_p[b], static_cast<const R *>(A.P.p) + s0, br, &Bars.full[b]);
+        if (need_delta) bulk_g2s(s_d[b], static_cast<const R *>(A.P.delta) + s0, br, &Bars.full[b]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&Bars.full[0], 1);
+        mbar_init(&Bars.full[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (ntile > 0) issue(0);
+        if (ntile > 1) issue(1);
+    }
+
     // scaled arithmetic (see piece_means_scaled): the basis is K! N^K, the path
     // means are S1 = S_{K-1} times the means of N^{K-1}; so the staged fields are
     // a / K! and ebar dx / S1, the A-term sum is multiplied by K!/S1 = DK, and the
@@ -140,9 +206,6 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     }
     __syncthreads();
 
-    const int32_t *__restrict__ cellp = A.P.cell;
-    const R *__restrict__ tp = static_cast<const R *>(A.P.t);
-    const R *__restrict__ pp = static_cast<const R *>(A.P.p);
     R *__restrict__ dp = static_cast<R *>(A.P.delta);
     R *__restrict__ pnp = static_cast<R *>(A.P.pnew);
     const R tau = (R)(A.dt / A.dx);
@@ -150,102 +213,114 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     const R dlim = (R)A.Dlim;
     const R one = R(1);
     R dmax = R(0);
-    bool bad = false;
+    bool bad = false, timeout = false;
     // window: pieces in cells wb-3 .. wb+3, V1 nodes wb-K-2 .. wb+3
     DepWindow<R, K + 6, K, K + 2, -3, 3> win;
     win.clear();
     int wb = INT_MIN;
 
-    long long beg, end;
-    block_chunk(A.np, beg, end);
-    for (long long base = beg; base < end; base += blockDim.x) {
-        const long long a = base + threadIdx.x;
-        const bool act = a < end;
-        const int c0 = act ? cellp[a] : 0;
-        const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
-        if (lead == INT_MAX) break;                    // whole warp past the chunk end
-        if (lead != wb) {
-            if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
-            wb = lead;
+    for (long long i = 0; i < ntile; ++i) {
+        if (!tile_wait(Bars, i)) {
+            timeout = true;
+            tile_drain(Bars, i, ntile);
+            break;
         }
-        const unsigned amask = __ballot_sync(0xffffffffu, act);
-        if (!act) continue;
-        const R t0 = tp[a];
-        const R pn = pp[a];
-        R v[K + 1];
-        bspline_scaled<K, R>(t0, v);
-        R A0y = R(0), A0z = R(0);
-#pragma unroll
-        for (int r = 0; r <= K; ++r) {
-            R y, z;
-            F.aa(c0 - r + H, y, z);
-            A0y += y * v[r];
-            A0z += z * v[r];
-        }
-        const R g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
-        R dold = A.warm ? fdiv_(tau * pn, g0) : dp[a];
-        if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
-
-        const R s = t0 + dold;
-        const R fs = floor_(s);
-        const int c1 = c0 + (int)fs;
-        bspline_scaled<K, R>(s - fs, v);
-        R A1y = R(0), A1z = R(0);
-#pragma unroll
-        for (int r = 0; r <= K; ++r) {
-            R y, z;
-            F.aa(c1 - r + H, y, z);
-            A1y += y * v[r];
-            A1z += z * v[r];
-        }
-
-        R Eb = R(0), Dy = R(0), Dz = R(0);
-        const R invd = (dold != R(0)) ? one / dold : R(0);
-        const int n1 = __reduce_max_sync(amask, path_pieces(t0, dold));
-        walk_uniform<K, R>(t0, dold, n1, [&](int c, R h, const R *m, int p) {
-            R e = R(0), gy = R(0), gz = R(0);
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-                R ev, y, z;
-                F.eg(c0 + c - r + H, ev, y, z);
-                e += m[r] * ev;
-                gy += m[r] * y;
-                gz += m[r] * z;
+        const int b = (int)(i & 1);
+        const long long s0 = beg + i * kTile;
+#pragma unroll 1
+        for (int u = 0; u < kTileU; ++u) {
+            const int jl = u * 256 + threadIdx.x;
+            const long long a = s0 + jl;
+            const bool act = a < end;
+            const int c0 = act ? s_cell[b][jl] : 0;
+            const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
+            if (lead == INT_MAX) break;                    // whole warp past the chunk end
+            if (lead != wb) {
+                if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
+                wb = lead;
             }
-            const R f = (dold != R(0)) ? h * invd : (p == 0 ? one : R(0));
-            Eb += f * e;
-            Dy += f * gy;
-            Dz += f * gz;
-        });
-        Dy *= R(DK);
-        Dz *= R(DK);
-
-        const R q1 = one + A1y * A1y + A1z * A1z;
-        const R g1 = sqrt_(q1 + pn * pn);
-        const R pnew = pn + tau * (Eb - fdiv_((A1y + A0y) * Dy + (A1z + A0z) * Dz, g1 + g0));
-        const R g2 = sqrt_(q1 + pnew * pnew);
-        R dnew = fdiv_(tau * (pn + pnew), g1 + g2);
-        if (!(fabs(dnew) <= dlim)) { bad = true; dnew = R(0); }
-
-        const int n2 = __reduce_max_sync(amask, path_pieces(t0, dnew));
-        walk_uniform<K, R>(t0, dnew, n2, [&](int c, R h, const R *m, int) {
-            R val[K];
+            const unsigned amask = __ballot_sync(0xffffffffu, act);
+            if (!act) continue;
+            const R t0 = s_t[b][jl];
+            const R pn = s_p[b][jl];
+            R v[K + 1];
+            bspline_scaled<K, R>(t0, v);
+            R A0y = R(0), A0z = R(0);
 #pragma unroll
-            for (int r = 0; r < K; ++r) val[r] = h * m[r];
-            if (!win.put(c0 + c - wb, val)) {
-#pragma unroll
-                for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], wdx * (double)val[r]);
+            for (int r = 0; r <= K; ++r) {
+                R y, z;
+                F.aa(c0 - r + H, y, z);
+                A0y += y * v[r];
+                A0z += z * v[r];
             }
-        });
+            const R g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
+            R dold = A.warm ? fdiv_(tau * pn, g0) : s_d[b][jl];
+            if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
 
-        R inc = fabs(dnew - dold);
-        if (Real<R>::fp32) inc = __fdividef(inc, fmax(one, fabs(dnew)));   // convergence metric only
-        dmax = (inc > dmax || inc != inc) ? inc : dmax;
-        dp[a] = dnew;
-        pnp[a] = pnew;
+            const R s = t0 + dold;
+            const R fs = floor_(s);
+            const int c1 = c0 + (int)fs;
+            bspline_scaled<K, R>(s - fs, v);
+            R A1y = R(0), A1z = R(0);
+#pragma unroll
+            for (int r = 0; r <= K; ++r) {
+                R y, z;
+                F.aa(c1 - r + H, y, z);
+                A1y += y * v[r];
+                A1z += z * v[r];
+            }
+
+            R Eb = R(0), Dy = R(0), Dz = R(0);
+            const R invd = (dold != R(0)) ? one / dold : R(0);
+            const int n1 = __reduce_max_sync(amask, path_pieces(t0, dold));
+            walk_uniform<K, R>(t0, dold, n1, [&](int c, R h, const R *m, int p) {
+                R e = R(0), gy = R(0), gz = R(0);
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    R ev, y, z;
+                    F.eg(c0 + c - r + H, ev, y, z);
+                    e += m[r] * ev;
+                    gy += m[r] * y;
+                    gz += m[r] * z;
+                }
+                const R f = (dold != R(0)) ? h * invd : (p == 0 ? one : R(0));
+                Eb += f * e;
+                Dy += f * gy;
+                Dz += f * gz;
+            });
+            Dy *= R(DK);
+            Dz *= R(DK);
+
+            const R q1 = one + A1y * A1y + A1z * A1z;
+            const R g1 = sqrt_(q1 + pn * pn);
+            const R pnew = pn + tau * (Eb - fdiv_((A1y + A0y) * Dy + (A1z + A0z) * Dz, g1 + g0));
+            const R g2 = sqrt_(q1 + pnew * pnew);
+            R dnew = fdiv_(tau * (pn + pnew), g1 + g2);
+            if (!(fabs(dnew) <= dlim)) { bad = true; dnew = R(0); }
+
+            const int n2 = __reduce_max_sync(amask, path_pieces(t0, dnew));
+            walk_uniform<K, R>(t0, dnew, n2, [&](int c, R h, const R *m, int) {
+                R val[K];
+#pragma unroll
+                for (int r = 0; r < K; ++r) val[r] = h * m[r];
+                if (!win.put(c0 + c - wb, val)) {
+#pragma unroll
+                    for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], wdx * (double)val[r]);
+                }
+            });
+
+            R inc = fabs(dnew - dold);
+            if (Real<R>::fp32) inc = __fdividef(inc, fmax(one, fabs(dnew)));   // convergence metric only
+            dmax = (inc > dmax || inc != inc) ? inc : dmax;
+            dp[a] = dnew;
+            pnp[a] = pnew;
+        }
+        __syncthreads();                          // stage b fully consumed
+        if (threadIdx.x == 0 && i + 2 < ntile) issue(i + 2);
     }
     if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
     if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
+    if (timeout && threadIdx.x == 0) atomicOr(&A.ctrl->status, STATUS_TIMEOUT);
     block_max_to(&A.ctrl->dmax_bits, (double)dmax, s_red);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const double val = s_acc[i];
@@ -256,7 +331,9 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
 size_t sweep1_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
-    return (W + 32) * sizeof(double) + (fp32 ? FieldTile<float>::bytes(W) : FieldTile<double>::bytes(W));
+    const size_t stages = 2 * (size_t)kTile * (sizeof(int32_t) + 3 * (fp32 ? sizeof(float) : sizeof(double)));
+    return 128 + stages + (W + 32) * sizeof(double) +
+           (fp32 ? FieldTile<float>::bytes(W) : FieldTile<double>::bytes(W));
 }
 
 template <typename R>
@@ -336,19 +413,56 @@ int launch_current(const CurrentArgs &a, int grid, int block, size_t smem, cudaS
 // Subsystem II: one fixed-point sweep (Sec. 4.2).  Markers frozen at x; with
 // A0 = A^n_h(x), A1 = A^(k)_h(x):
 //   s_i += w (A0 + A1) Lambda^0_i(x) / (g(p,A0) + g(p,A1))   (y and z);
-// the weight w enters at the window flush, in double.
+// the weight w enters at the window flush, in double.  Same tile pipeline
+// (bulk copies of cell, t, p two tiles ahead) as the subsystem-I sweep.
 // ---------------------------------------------------------------------------
 template <int K, typename R>
 __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int H = A.H;
     const int W = A.M + 2 * H;
-    double *s_sy = reinterpret_cast<double *>(smem);
+    TileBars &Bars = *reinterpret_cast<TileBars *>(smem);
+    unsigned char *st = smem + 128;
+    int32_t *s_cell[2];
+    R *s_t[2], *s_p[2];
+    for (int b = 0; b < 2; ++b) {
+        s_cell[b] = reinterpret_cast<int32_t *>(st);
+        s_t[b] = reinterpret_cast<R *>(st + kTile * sizeof(int32_t));
+        s_p[b] = s_t[b] + kTile;
+        st += kTile * (sizeof(int32_t) + 2 * sizeof(R));
+    }
+    double *s_sy = reinterpret_cast<double *>(st);
     double *s_sz = s_sy + W;
     using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
     R2 *s_an = reinterpret_cast<R2 *>(s_sz + W);
     R2 *s_ak = s_an + W;
+
+    long long beg, end;
+    block_chunk(A.np, beg, end);
+    const long long ntile = end > beg ? (end - beg + kTile - 1) / kTile : 0;
+    auto issue = [&](long long i) {
+        const long long s0 = beg + i * kTile;
+        long long n = end - s0 < kTile ? end - s0 : kTile;
+        n = (n + 3) & ~3LL;
+        const int b = (int)(i & 1);
+        const unsigned bi = (unsigned)(n * sizeof(int32_t)), br = (unsigned)(n * sizeof(R));
+        fence_proxy_async();
+        mbar_expect_tx(&Bars.full[b], bi + 2 * br);
+        bulk_g2s(s_cell[b], A.P.cell + s0, bi, &Bars.full[b]);
+        bulk_g2s(s_t[b], static_cast<const R *>(A.P.t) + s0, br, &Bars.full[b]);
+        bulk_g2s(s_p[b], static_cast<const R *>(A.P.p) + s0, br, &Bars.full[b]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&Bars.full[0], 1);
+        mbar_init(&Bars.full[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (ntile > 0) issue(0);
+        if (ntile > 1) issue(1);
+    }
     // scaled basis K! N^K: coefficients staged as a / K!, deposits flushed times w / K!
     const double inv_fact = 1.0 / (double)Fact<K>::v;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -361,69 +475,79 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
         s_sz[i] = 0.0;
     }
     __syncthreads();
-    const int32_t *__restrict__ cellp = A.P.cell;
-    const R *__restrict__ tp = static_cast<const R *>(A.P.t);
-    const R *__restrict__ pp = static_cast<const R *>(A.P.p);
     const double w = A.w * inv_fact;
     const R one = R(1);
+    bool timeout = false;
     // window: marker cells wb .. wb+3 (wb = the warp's lowest), V0 nodes wb-K .. wb+3
     DepWindow<R, K + 4, K + 1, K, 0, 3> wy, wz;
     wy.clear();
     wz.clear();
     int wb = INT_MIN;
-    long long beg, end;
-    block_chunk(A.np, beg, end);
-    for (long long base = beg; base < end; base += blockDim.x) {
-        const long long a = base + threadIdx.x;
-        const bool act = a < end;
-        const int c = act ? cellp[a] : 0;
-        const int lead = __reduce_min_sync(0xffffffffu, act ? c : INT_MAX);
-        if (lead == INT_MAX) break;
-        if (lead != wb) {
-            if (wb != INT_MIN) {
-                wy.flush(s_sy, wb - K + H, w);
-                wz.flush(s_sz, wb - K + H, w);
+    for (long long i = 0; i < ntile; ++i) {
+        if (!tile_wait(Bars, i)) {
+            timeout = true;
+            tile_drain(Bars, i, ntile);
+            break;
+        }
+        const int b = (int)(i & 1);
+        const long long s0 = beg + i * kTile;
+#pragma unroll 1
+        for (int u = 0; u < kTileU; ++u) {
+            const int jl = u * 256 + threadIdx.x;
+            const long long a = s0 + jl;
+            const bool act = a < end;
+            const int c = act ? s_cell[b][jl] : 0;
+            const int lead = __reduce_min_sync(0xffffffffu, act ? c : INT_MAX);
+            if (lead == INT_MAX) break;
+            if (lead != wb) {
+                if (wb != INT_MIN) {
+                    wy.flush(s_sy, wb - K + H, w);
+                    wz.flush(s_sz, wb - K + H, w);
+                }
+                wb = lead;
             }
-            wb = lead;
-        }
-        if (!act) continue;
-        const R t = tp[a];
-        const R p = pp[a];
-        R v[K + 1];
-        bspline_scaled<K, R>(t, v);
-        R A0y = R(0), A0z = R(0), A1y = R(0), A1z = R(0);
+            if (!act) continue;
+            const R t = s_t[b][jl];
+            const R p = s_p[b][jl];
+            R v[K + 1];
+            bspline_scaled<K, R>(t, v);
+            R A0y = R(0), A0z = R(0), A1y = R(0), A1z = R(0);
 #pragma unroll
-        for (int r = 0; r <= K; ++r) {
-            const R2 an = s_an[c - r + H], ak = s_ak[c - r + H];
-            A0y += an.x * v[r];
-            A0z += an.y * v[r];
-            A1y += ak.x * v[r];
-            A1z += ak.y * v[r];
-        }
-        const R pp1 = one + p * p;
-        const R g0 = sqrt_(pp1 + A0y * A0y + A0z * A0z);
-        const R g1 = sqrt_(pp1 + A1y * A1y + A1z * A1z);
-        const R cf = fdiv_(one, g0 + g1);
-        const R fy = cf * (A0y + A1y), fz = cf * (A0z + A1z);
-        R vy[K + 1], vz[K + 1];
+            for (int r = 0; r <= K; ++r) {
+                const R2 an = s_an[c - r + H], ak = s_ak[c - r + H];
+                A0y += an.x * v[r];
+                A0z += an.y * v[r];
+                A1y += ak.x * v[r];
+                A1z += ak.y * v[r];
+            }
+            const R pp1 = one + p * p;
+            const R g0 = sqrt_(pp1 + A0y * A0y + A0z * A0z);
+            const R g1 = sqrt_(pp1 + A1y * A1y + A1z * A1z);
+            const R cf = fdiv_(one, g0 + g1);
+            const R fy = cf * (A0y + A1y), fz = cf * (A0z + A1z);
+            R vy[K + 1], vz[K + 1];
 #pragma unroll
-        for (int r = 0; r <= K; ++r) {
-            vy[r] = fy * v[r];
-            vz[r] = fz * v[r];
-        }
-        if (!wy.put(c - wb, vy)) {
+            for (int r = 0; r <= K; ++r) {
+                vy[r] = fy * v[r];
+                vz[r] = fz * v[r];
+            }
+            if (!wy.put(c - wb, vy)) {
 #pragma unroll
-            for (int r = 0; r <= K; ++r) atomicAdd(&s_sy[c - r + H], w * (double)vy[r]);
-        }
-        if (!wz.put(c - wb, vz)) {
+                for (int r = 0; r <= K; ++r) atomicAdd(&s_sy[c - r + H], w * (double)vy[r]);
+            }
+            if (!wz.put(c - wb, vz)) {
 #pragma unroll
-            for (int r = 0; r <= K; ++r) atomicAdd(&s_sz[c - r + H], w * (double)vz[r]);
+                for (int r = 0; r <= K; ++r) atomicAdd(&s_sz[c - r + H], w * (double)vz[r]);
+            }
         }
+        __syncthreads();
+        if (threadIdx.x == 0 && i + 2 < ntile) issue(i + 2);
     }
     if (wb != INT_MIN) {
         wy.flush(s_sy, wb - K + H, w);
         wz.flush(s_sz, wb - K + H, w);
     }
+    if (timeout && threadIdx.x == 0) atomicOr(A.status, STATUS_TIMEOUT);
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
@@ -436,7 +560,8 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
 size_t sweep2_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
-    return 2 * W * sizeof(double) + 2 * W * (fp32 ? sizeof(float2) : sizeof(double2));
+    const size_t stages = 2 * (size_t)kTile * (sizeof(int32_t) + 2 * (fp32 ? sizeof(float) : sizeof(double)));
+    return 128 + stages + 2 * W * sizeof(double) + 2 * W * (fp32 ? sizeof(float2) : sizeof(double2));
 }
 
 template <typename R>
