@@ -1,12 +1,16 @@
 """Benchmark: particle-steps/s of the energy-conserving PIC step on one GB300.
 
-Workload (default): L = 4 pi, M = 2048 cells, cubic splines, N_p = 1e8 markers,
-density 1 + 0.01 cos(0.5 x), Maxwellian p with v_th = 0.1, pump A_y = 0.2 cos(2x),
-dt = 0.05 -- float particle state with double grid accumulation, solves and
-energy sums ("FP32" form), beside the plain all-double form on the same shape.
-A step is one full Lie--Trotter step (subsystem I then II, every fixed-point
-sweep included).  Inputs are synthetic and seeded; markers (1.2-2 GB) exceed
-the 129 MB L2, so no flush is needed between steps.
+Workload: L = 4 pi, M = 2048 cells, cubic splines, N_p = 1e8 markers, density
+1 + 0.01 cos(0.5 x), Maxwellian p with v_th = 0.1, pump A_y = 0.2 cos(2x),
+dt = 0.05.  Forms measured on the same seeded markers:
+  * FP32 + learned warm start (the headline): float marker state and arithmetic,
+    double deposits / solves / convergence / energy, network proposals for the
+    subsystem-I fixed point (weights trained by train_warm.py, shipped in
+    paper_2203_06513_gb300/data/warm_mlp.npz);
+  * FP32 + explicit predictor x^(0) = x^n + dt p / gamma;
+  * plain FP64 (all double, no warm start).
+A step is one full Lie--Trotter step (subsystem I then II, all fixed-point
+sweeps).  Markers (>= 2.4 GB) exceed the 129 MB L2: no flush between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -23,7 +27,6 @@ for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
 
 import argparse
 import json
-import math
 import statistics
 import subprocess
 import sys
@@ -40,10 +43,10 @@ from paper_2203_06513_gb300 import inputs as I  # noqa: E402
 METRIC = "particle-steps/s at rel. energy err ≤1e-10: FP32+learned vs plain FP64"
 UNIT = "particle-steps/s"
 WORKLOAD = "C2"
+WEIGHTS = os.path.join(ROOT, "paper_2203_06513_gb300", "data", "warm_mlp.npz")
 # algorithmic bytes per marker per subsystem-I sweep: read cell, offset, p, delta;
 # write delta, p_new (float form 6 x 4 B; double form 4 + 5 x 8 B)
 BYTES_SWEEP1 = {1: 24, 0: 44}
-BYTES_SWEEP2 = {1: 12, 0: 20}
 
 
 def peaks():
@@ -116,17 +119,16 @@ def dist_env():
     return ws, rank, local
 
 
-def run_form(pic, torch, w, precision, warm, steps, warmup, stream, timing=True):
-    """Advance one replica; returns timings and diagnostics."""
-    x, p = I.particles(w)
-    ay, az, ey, ez = I.fields(w)
-    tol = 1e-13 if precision == pic.PIC_FP64 else 1e-13
-    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2, tol=tol)
+def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=None):
+    """Advance one replica from host arrays; CUDA-event timing of `steps` steps."""
+    x, p, ay, az, ey, ez = arrays
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2)
     g = pic.Pic(cfg, x, p, ay, az, ey, ez, stream=stream.cuda_stream)
-    del x, p
+    if mlp is not None:
+        mlp.attach(g)
     H0 = g.energy()["total"]
     it_warm = g.step(warmup)
-    g.timing_enable(timing)
+    g.timing_enable(True)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -142,20 +144,20 @@ def run_form(pic, torch, w, precision, warm, steps, warmup, stream, timing=True)
             "gauss": E["gauss"], "rel_energy_err": abs(E["total"] - H0) / abs(H0)}
 
 
-def e2e_run(pic, torch, w, precision, warm, steps, stream):
+def e2e_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None):
     """Whole job through the public API with host buffers: pic_init from pinned
     host arrays (H2D), `steps` steps, pic_get_state back to pinned host (D2H)."""
-    x, p = I.particles(w)
-    ay, az, ey, ez = I.fields(w)
+    x, p, ay, az, ey, ez = arrays
     hx = torch.from_numpy(x).pin_memory().numpy()
     hp = torch.from_numpy(p).pin_memory().numpy()
-    del x, p
     out = {k: torch.empty(w.np, dtype=torch.float64).pin_memory().numpy() for k in ("x", "p")}
     out.update({k: np.empty(w.nx) for k in ("ex", "ey", "ez", "ay", "az")})
     cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = pic.Pic(cfg, hx, hp, ay, az, ey, ez, stream=stream.cuda_stream)
+    if mlp is not None:
+        mlp.attach(g)
     g.step(steps)
     g.get_state(**out)
     t1 = time.perf_counter()
@@ -165,54 +167,43 @@ def e2e_run(pic, torch, w, precision, warm, steps, stream):
     return {"s": t1 - t0, "h2d": h2d, "d2h": d2h}
 
 
-def reference_arm(args, ws, rank):
-    """The oracle (plain FP64 CPU program of the same scheme) on a bounded sample
-    of the workload: same grid, fewer markers, two steps."""
-    if rank != 0:
-        return 0
+def oracle_sample(n_sample: int, steps: int, warmup: int):
+    """The FP64 CPU oracle on n_sample markers of the workload's grid."""
     from oracle import oracle as O
     w = I.workload(WORKLOAD)
-    n_sample = int(os.environ.get("PIC_REF_SAMPLE", "200000"))
-    steps = max(1, min(args.steps, 2))
     ws_ = I.workload(WORKLOAD, np=n_sample)
     x, p = I.particles(ws_)
     ay, az, ey, ez = I.fields(ws_)
     orc = O.Oracle(w.L, w.nx, w.degree, ws_.weight, w.dt, w.tol, w.max_iter)
     s = O.initial_state(orc, x, p, ay, az, ey, ez)
-    for _ in range(max(0, min(args.warmup, 1))):
+    for _ in range(warmup):
         s = orc.step(s)
     t0 = time.perf_counter()
     for _ in range(steps):
         s = orc.step(s)
-    dt = time.perf_counter() - t0
-    v = n_sample * steps / dt
+    return n_sample * steps / (time.perf_counter() - t0)
+
+
+def reference_arm(args, ws, rank):
+    """The reference arm: the oracle (plain FP64 CPU program of the same scheme) on
+    a bounded sample of the workload (same grid, fewer markers), host cores."""
+    if rank != 0:
+        return 0
+    n_sample = int(os.environ.get("PIC_REF_SAMPLE", "100000"))
+    steps = max(1, min(args.steps, 2))
+    warmup = max(0, min(args.warmup, 1))
+    v = oracle_sample(n_sample, steps, warmup)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
-            "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / steps,
+            "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * n_sample / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: L=4pi, M=2048, k=3, Np=1e8, dt=0.05 (oracle sample)",
-                       "sample_np": n_sample},
+            "config": {"workload": "C2: L=4pi, M=2048, k=3, dt=0.05, pump 0.2, vth 0.1 "
+                                   "(oracle on a marker sample)", "sample_np": n_sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{n_sample} markers on the M=2048 grid, {steps} steps"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
-
-
-def cpu_baseline(args):
-    from oracle import oracle as O
-    w = I.workload(WORKLOAD)
-    n_sample = int(os.environ.get("PIC_CPU_SAMPLE", "100000"))
-    ws_ = I.workload(WORKLOAD, np=n_sample)
-    x, p = I.particles(ws_)
-    ay, az, ey, ez = I.fields(ws_)
-    orc = O.Oracle(w.L, w.nx, w.degree, ws_.weight, w.dt, w.tol, w.max_iter)
-    s = O.initial_state(orc, x, p, ay, az, ey, ez)
-    t0 = time.perf_counter()
-    s = orc.step(s)
-    dt = time.perf_counter() - t0
-    return {"value": n_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_sample} markers on the M=2048 grid, 1 step (single thread)"}
 
 
 def main():
@@ -222,7 +213,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libpic", choices=["libpic", "reference"])
     ap.add_argument("--np", type=float, default=None, help="override N_p (smaller runs)")
-    ap.add_argument("--warm", default="explicit", choices=["none", "explicit", "mlp"])
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -237,30 +227,23 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = I.workload(WORKLOAD, seed=rank)
+    kw = {"seed": rank}
     if args.np:
-        w = I.workload(WORKLOAD, seed=rank, np=int(args.np))
-    warm = {"none": pic.PIC_WARM_NONE, "explicit": pic.PIC_WARM_EXPLICIT,
-            "mlp": pic.PIC_WARM_MLP}[args.warm]
+        kw["np"] = int(args.np)
+    w = I.workload(WORKLOAD, **kw)
+    x, p = I.particles(w)
+    ay, az, ey, ez = I.fields(w)
+    arrays = (x, p, ay, az, ey, ez)
     stream = torch.cuda.Stream()
+    mlp = None
+    if os.path.exists(WEIGHTS):
+        d = np.load(WEIGHTS)
+        mlp = pic.Mlp(d["norm"], d["params"], stream=stream.cuda_stream)
 
     def barrier():
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-
-    clocks = ClockSampler(local)
-    barrier()
-    clocks.start()
-    r32 = run_form(pic, torch, w, pic.PIC_FP32, warm, args.steps, args.warmup, stream)
-    clk = clocks.stop()
-    barrier()
-    k64 = args.fp64_steps if args.fp64_steps is not None else max(1, min(args.steps, 4))
-    r64 = run_form(pic, torch, w, pic.PIC_FP64, pic.PIC_WARM_NONE, k64, max(1, min(args.warmup, 3)),
-                   stream)
-    barrier()
-    e2e = None if args.no_e2e else e2e_run(pic, torch, w, pic.PIC_FP32, warm, args.steps, stream)
-    barrier()
 
     def max_over_ranks(v):
         if ws == 1:
@@ -269,39 +252,70 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    ms32 = max_over_ranks(r32["ms"])
+    head_warm = pic.PIC_WARM_MLP if mlp is not None else pic.PIC_WARM_EXPLICIT
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    r_head = run_form(pic, torch, w, arrays, pic.PIC_FP32, head_warm, args.steps, args.warmup, stream,
+                      mlp if mlp is not None else None)
+    clk = clocks.stop()
+    barrier()
+    r_expl = run_form(pic, torch, w, arrays, pic.PIC_FP32, pic.PIC_WARM_EXPLICIT, args.steps,
+                      args.warmup, stream)
+    barrier()
+    k64 = args.fp64_steps if args.fp64_steps is not None else max(1, min(args.steps, 4))
+    r64 = run_form(pic, torch, w, arrays, pic.PIC_FP64, pic.PIC_WARM_NONE, k64, max(1, min(args.warmup, 3)),
+                   stream)
+    barrier()
+    e2e = None if args.no_e2e else e2e_run(pic, torch, w, arrays, pic.PIC_FP32, head_warm, args.steps,
+                                           stream, mlp)
+    barrier()
+
+    ms_head = max_over_ranks(r_head["ms"])
+    ms_expl = max_over_ranks(r_expl["ms"])
     ms64 = max_over_ranks(r64["ms"])
     e2e_s = max_over_ranks(e2e["s"]) if e2e else None
     total_np = w.np * ws
-    value = total_np * args.steps / (ms32 / 1e3)
+    value = total_np * args.steps / (ms_head / 1e3)
+    v_expl = total_np * args.steps / (ms_expl / 1e3)
     v64 = total_np * k64 / (ms64 / 1e3)
-    tr = r32["timing"]
+    tr = r_head["timing"]
     hbm, peak_kind = peaks()
     launch_ms = tr["sweep1_ms"] / max(1, tr["sweep1_launches"])
     achieved = BYTES_SWEEP1[1] * w.np / (launch_ms / 1e3) / 1e9
-    line = None
     if rank == 0:
-        cpu = None if args.no_cpu else cpu_baseline(args)
+        cpu = None
+        if not args.no_cpu:
+            n_cpu = int(os.environ.get("PIC_CPU_SAMPLE", "100000"))
+            cpu = {"value": oracle_sample(n_cpu, 1, 0), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{n_cpu} markers on the M=2048 grid, 1 step (single thread)"}
+
+        def sweeps(r, k):
+            return {"I": r["iters"][0] / k, "II": r["iters"][1] / k}
+
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_head / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "C2: L=4pi, M=2048, k=3, Np=%d per GPU, dt=0.05, pump 0.2, vth 0.1"
                                    % w.np,
-                       "form": "FP32 particles + FP64 grid", "warm_start": args.warm,
+                       "form": "FP32 particles + FP64 grid",
+                       "warm_start": "learned (MLP)" if mlp is not None else "explicit (no weights file)",
                        "l2": "inputs larger than L2 (markers %.1f GB)" % (w.np * 24 / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "rel_energy_err": r32["rel_energy_err"], "energy_ok": r32["rel_energy_err"] <= 1e-10,
-            "gauss_residual": r32["gauss"],
-            "sweeps_per_step": {"I": r32["iters"][0] / args.steps, "II": r32["iters"][1] / args.steps},
+            "rel_energy_err": r_head["rel_energy_err"], "energy_ok": r_head["rel_energy_err"] <= 1e-10,
+            "gauss_residual": r_head["gauss"], "sweeps_per_step": sweeps(r_head, args.steps),
+            "warm_start_ms": tr.get("warm_ms"),
+            "fp32_explicit": {"value": v_expl, "unit": UNIT, "ms_per_step": ms_expl / args.steps,
+                              "rel_energy_err": r_expl["rel_energy_err"],
+                              "sweeps_per_step": sweeps(r_expl, args.steps)},
             "fp64": {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
                      "rel_energy_err": r64["rel_energy_err"], "gauss_residual": r64["gauss"],
-                     "sweeps_per_step": {"I": r64["iters"][0] / k64, "II": r64["iters"][1] / k64},
-                     "speedup_fp32_over_fp64": value / v64},
+                     "sweeps_per_step": sweeps(r64, k64),
+                     "speedup_fp32_learned_over_fp64": value / v64},
             "roofline": {"kernel": "k_sweep1<3,float>", "bound": "hbm", "achieved": achieved,
-                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "peak_kind": peak_kind, "traffic": None,
-                         "bytes_per_marker": BYTES_SWEEP1[1], "launch_ms": launch_ms},
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                         "traffic": None, "bytes_per_marker": BYTES_SWEEP1[1], "launch_ms": launch_ms},
             "kernel_ms": {"sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"], "solve": tr["solve_ms"]},
             "gpu_launches": tr["launches"],
             "clocks": clk,

@@ -156,9 +156,10 @@ int pic_energy(pic_handle *h, double out[6]);
  * out[2] = ms in subsystem-II sweep kernels, out[3] = launches,
  * out[4] = ms in grid solve kernels, out[5] = launches,
  * out[6] = total kernel launches issued by the library since enable,
- * out[7] = marker-sweeps done by subsystem-I sweep kernels (sum of N_p per launch). */
+ * out[7] = marker-sweeps done by subsystem-I sweep kernels (sum of N_p per launch),
+ * out[8] = ms in warm-start network kernels, out[9] = their launches. */
 int pic_timing_enable(pic_handle *h, int32_t on);
-int pic_timing_read(pic_handle *h, double out[8]);
+int pic_timing_read(pic_handle *h, double out[10]);
 
 /* Release the handle and all memory it owns.  NULL is allowed. */
 int pic_destroy(pic_handle *h);

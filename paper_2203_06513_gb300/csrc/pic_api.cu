@@ -56,7 +56,7 @@ struct pic_handle {
     int *h_flag = nullptr;          // pinned: converged flag readback
     DevCtrl *h_ctrl = nullptr;      // pinned: full control block readback
 
-    int sweep_grid = 0, sweep_block = 256;
+    int sweep_grid = 0, sweep_block = kSweepThreads;
     size_t smem1 = 0, smem2 = 0;
 
     // timing
@@ -734,14 +734,15 @@ extern "C" int pic_timing_enable(pic_handle *h, int32_t on)
 {
     if (!h) return PIC_ERR_INVALID;
     h->timing = on ? 1 : 0;
-    h->t_sw1 = h->t_sw2 = h->t_solve = 0.0;
+    h->t_sw1 = h->t_sw2 = h->t_solve = h->t_warm = 0.0;
+    h->n_warm = 0;
     h->n_sw1 = h->n_sw2 = h->n_solve = 0;
     h->launches = 0;
     h->marker_sweeps = 0;
     return PIC_OK;
 }
 
-extern "C" int pic_timing_read(pic_handle *h, double out[8])
+extern "C" int pic_timing_read(pic_handle *h, double out[10])
 {
     if (!h || !out) return PIC_ERR_INVALID;
     out[0] = h->t_sw1;
@@ -752,6 +753,8 @@ extern "C" int pic_timing_read(pic_handle *h, double out[8])
     out[5] = (double)h->n_solve;
     out[6] = (double)h->launches;
     out[7] = (double)h->marker_sweeps;
+    out[8] = h->t_warm;
+    out[9] = (double)h->n_warm;
     return PIC_OK;
 }
 

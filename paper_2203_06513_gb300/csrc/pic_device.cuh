@@ -21,6 +21,7 @@ struct DevCtrl {
     unsigned long long emax_bits;      // max field increment of this sweep
     unsigned long long dprev_bits;     // previous sweep's values (stagnation test)
     unsigned long long eprev_bits;
+    unsigned long long emag_bits;      // max |e^(k+1)| of this sweep (field scale)
     int iter;                          // sweeps done in the current loop
     int converged;                     // 1 once the test passed
     int status;                        // error bits, see STATUS_*

@@ -138,8 +138,13 @@ __device__ void decide(const ConvArgs &A)
             if (!(r < 0.9)) r = 0.9;
             return v * r / (1.0 - r);
         };
+        // field tolerance: the absolute tol, or 1e-10 of the field's max-norm when
+        // that is larger (float markers resolve the field to about 1e-7 relative,
+        // so a tighter absolute target only waits for noise)
+        const double emag = bits_to_double(c->emag_bits);
+        const double etol = fmax(A.tol, 1e-10 * emag);
         const bool dok = (A.subsystem == 1) ? (est(d, dp) <= A.dtol) : true;
-        const bool eok = est(e, ep) <= A.tol;
+        const bool eok = est(e, ep) <= etol;
         const bool dstag = (A.subsystem == 1) ? (d >= 0.5 * dp && d <= 1e-4) : true;
         const bool estag = e >= 0.5 * ep && e <= 1e-8;
         ok = (dok && eok) || (c->iter >= 3 && dstag && estag);
@@ -155,8 +160,10 @@ __device__ void decide(const ConvArgs &A)
     c->eprev_bits = c->emax_bits;
     c->dmax_bits = 0ull;
     c->emax_bits = 0ull;
+    c->emag_bits = 0ull;
     c->ticket = 0u;
     __threadfence();
+    if (A.graph) cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond_handle, stop ? 0u : 1u);
 }
 
 // y_i = sum_n taps[n] in[(i - (d_start + n)) mod M], one output per thread,
@@ -170,6 +177,12 @@ __global__ void __launch_bounds__(64) k_conv(ConvArgs A)
     double *s_in = s_conv;              // 2M
     double *s_tap = s_conv + 2 * M;     // ntap
     const double *in = A.in[comp];
+    double *zero = A.zero[comp];
+    if (A.graph && A.mode != CONV_PLAIN) {   // replayed by a graph: buffers by sweep parity
+        const int it = *reinterpret_cast<volatile const int *>(&A.ctrl->iter);
+        in = A.pair[comp][it & 1];
+        zero = A.pair[comp][(it + 1) & 1];
+    }
     const int off = M / 2;              // s_in[q] = in[(q - off) mod M], q in [0, 2M)
     for (int q = threadIdx.x; q < 2 * M; q += blockDim.x) {
         int g = q - off;
@@ -179,7 +192,7 @@ __global__ void __launch_bounds__(64) k_conv(ConvArgs A)
     for (int n = threadIdx.x; n < A.ntap; n += blockDim.x) s_tap[n] = A.taps[n];
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double diff = 0.0;
+    double diff = 0.0, mag = 0.0;
     if (i < M) {
         // offsets d = d_start + n lie in [-(M-1)/2, M/2], so i - d + off is in [0, 2M)
         const double *base = s_in + (i - A.d_start + off);
@@ -197,20 +210,23 @@ __global__ void __launch_bounds__(64) k_conv(ConvArgs A)
             const double en = A.en[0][i];
             const double enew = en - y;                  // e^(k+1) = e^n - M1^{-1} j
             diff = fabs(enew - A.ek[0][i]);
+            mag = fabs(enew);
             A.ek[0][i] = enew;
             A.aux[0][i] = 0.5 * (en + enew);             // ebar for the next sweep
-            A.zero[0][i] = 0.0;
+            zero[i] = 0.0;
         } else {                                         // CONV_SOLVE2
             const double en = A.en[comp][i];
             const double enew = A.r0[comp][i] + A.dt * y;   // P e^(k+1) = b + dt s
             diff = fabs(enew - A.ek[comp][i]);
+            mag = fabs(enew);
             A.ek[comp][i] = enew;
             A.aux[comp][i] = A.an[comp][i] - 0.5 * A.dt * (en + enew);   // a^(k+1)
-            A.zero[comp][i] = 0.0;
+            zero[i] = 0.0;
         }
     }
     if (A.mode == CONV_PLAIN) return;
     block_max_to(&A.ctrl->emax_bits, diff, s_red);
+    block_max_to(&A.ctrl->emag_bits, mag, s_red);
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int nblk = gridDim.x * gridDim.y;
@@ -255,6 +271,7 @@ __global__ void k_prep1(int M, double dx, const double *ex, double *ek, double *
     if (i == 0) {
         ctrl->dmax_bits = 0ull;
         ctrl->emax_bits = 0ull;
+        ctrl->emag_bits = 0ull;
         ctrl->dprev_bits = 0x7ff0000000000000ull;
         ctrl->eprev_bits = 0x7ff0000000000000ull;
         ctrl->iter = 0;
@@ -300,6 +317,7 @@ __global__ void k_prep2(int M, int K, double dt, const double *rowPm, const doub
     if (i == 0) {
         ctrl->dmax_bits = 0ull;
         ctrl->emax_bits = 0ull;
+        ctrl->emag_bits = 0ull;
         ctrl->dprev_bits = 0x7ff0000000000000ull;
         ctrl->eprev_bits = 0x7ff0000000000000ull;
         ctrl->iter = 0;
@@ -424,6 +442,7 @@ __global__ void k_ctrl_reset(DevCtrl *c)
 {
     c->dmax_bits = 0ull;
     c->emax_bits = 0ull;
+    c->emag_bits = 0ull;
     c->dprev_bits = 0x7ff0000000000000ull;
     c->eprev_bits = 0x7ff0000000000000ull;
     c->iter = 0;

@@ -10,6 +10,8 @@ namespace pic {
 
 // velocity bins of the marker sort key (cell, bin)
 constexpr int kVelBins = 16;
+// threads per block of the sweep kernels (two blocks per SM)
+constexpr int kSweepThreads = 512;
 
 // ---------------------------------------------------------------- particles
 struct PartPtrs {
@@ -29,7 +31,12 @@ struct Sweep1Args {
     const double *ebar, *ga_y, *ga_z, *ay, *az;
     double *j;
     DevCtrl *ctrl;
-    int warm;           // 1: delta^(0) = explicit predictor, computed in-kernel
+    int warm;           // 1: delta^(0) = explicit predictor, computed in-kernel (first sweep)
+    // graph mode (the launch is replayed by a CUDA graph): the deposit buffer is
+    // jpair[iter & 1] and the explicit warm start applies when iter == 0, with
+    // iter read from ctrl at kernel start
+    int graph;
+    double *jpair[2];
 };
 
 struct Sweep2Args {
@@ -40,6 +47,10 @@ struct Sweep2Args {
     const double *an_y, *an_z, *ak_y, *ak_z;
     double *s_y, *s_z;
     int *status;        // error bits (STATUS_TIMEOUT)
+    // graph mode: deposits go to sypair/szpair[iter & 1], iter read from ctrl
+    int graph;
+    const DevCtrl *ctrl;
+    double *sypair[2], *szpair[2];
 };
 
 struct CurrentArgs {
@@ -97,7 +108,12 @@ struct ConvArgs {
     double dt, dx, tol, dtol;
     int max_iter, fp32, subsystem;
     DevCtrl *ctrl;
-    unsigned long long cond_handle;   // graph conditional handle (0: none)
+    // graph mode: in[c] = pair[c][iter & 1], zero[c] = pair[c][(iter + 1) & 1]
+    // (iter read from ctrl at kernel start), and the decision sets the loop's
+    // conditional handle (1 = run another sweep)
+    int graph;
+    double *pair[2][2];
+    unsigned long long cond_handle;
 };
 
 int launch_conv(const ConvArgs &a, cudaStream_t s);

@@ -106,8 +106,8 @@ __device__ __forceinline__ void block_chunk(long long np, long long &beg, long l
 // ahead of the consumers, so the DRAM latency of the next tile overlaps the
 // arithmetic on the current one.  The marker arrays are allocated with padding,
 // so a tile's byte count may be rounded up to a multiple of 16.
-constexpr int kTileU = 4;                      // markers per thread per tile
-constexpr int kTile = 256 * kTileU;            // markers per tile (block of 256)
+constexpr int kTileU = 2;                      // markers per thread per tile
+constexpr int kTile = kSweepThreads * kTileU;  // markers per tile
 
 struct TileBars {
     unsigned long long full[2];
@@ -137,7 +137,7 @@ __device__ __forceinline__ void tile_drain(TileBars &B, long long i, long long n
 // In cell units with tau = dt/dx: p^(k+1) = p^n + tau (Ebar dx - (A1+A0).D dx/(...)).
 // ---------------------------------------------------------------------------
 template <int K, typename R>
-__global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
+__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1(Sweep1Args A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int H = A.H;
@@ -160,7 +160,14 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     long long beg, end;
     block_chunk(A.np, beg, end);
     const long long ntile = end > beg ? (end - beg + kTile - 1) / kTile : 0;
-    const bool need_delta = !A.warm;
+    double *jout = A.j;
+    bool warm = A.warm != 0;
+    if (A.graph) {                          // replayed by a graph: buffers by sweep parity
+        const int it = *reinterpret_cast<volatile const int *>(&A.ctrl->iter);
+        jout = A.jpair[it & 1];
+        warm = warm && it == 0;
+    }
+    const bool need_delta = !warm;
     auto issue = [&](long long i) {            // one thread: copies of tile i into stage i % 2
         const long long s0 = beg + i * kTile;
         long long n = end - s0 < kTile ? end - s0 : kTile;
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
         const long long s0 = beg + i * kTile;
 #pragma unroll 1
         for (int u = 0; u < kTileU; ++u) {
-            const int jl = u * 256 + threadIdx.x;
+            const int jl = u * kSweepThreads + threadIdx.x;
             const long long a = s0 + jl;
             const bool act = a < end;
             const int c0 = act ? s_cell[b][jl] : 0;
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
                 A0z += z * v[r];
             }
             const R g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
-            R dold = A.warm ? fdiv_(tau * pn, g0) : s_d[b][jl];
+            R dold = warm ? fdiv_(tau * pn, g0) : s_d[b][jl];
             if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
 
             const R s = t0 + dold;
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(256) k_sweep1(Sweep1Args A)
     block_max_to(&A.ctrl->dmax_bits, (double)dmax, s_red);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const double val = s_acc[i];
-        if (val != 0.0) atomicAdd(&A.j[wrap_cell(i - H, A.M)], val);
+        if (val != 0.0) atomicAdd(&jout[wrap_cell(i - H, A.M)], val);
     }
 }
 
@@ -417,7 +424,7 @@ int launch_current(const CurrentArgs &a, int grid, int block, size_t smem, cudaS
 // (bulk copies of cell, t, p two tiles ahead) as the subsystem-I sweep.
 // ---------------------------------------------------------------------------
 template <int K, typename R>
-__global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
+__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2(Sweep2Args A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int H = A.H;
@@ -493,7 +500,7 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
         const long long s0 = beg + i * kTile;
 #pragma unroll 1
         for (int u = 0; u < kTileU; ++u) {
-            const int jl = u * 256 + threadIdx.x;
+            const int jl = u * kSweepThreads + threadIdx.x;
             const long long a = s0 + jl;
             const bool act = a < end;
             const int c = act ? s_cell[b][jl] : 0;
@@ -548,12 +555,18 @@ __global__ void __launch_bounds__(256) k_sweep2(Sweep2Args A)
         wz.flush(s_sz, wb - K + H, w);
     }
     if (timeout && threadIdx.x == 0) atomicOr(A.status, STATUS_TIMEOUT);
+    double *syo = A.s_y, *szo = A.s_z;
+    if (A.graph) {                          // replayed by a graph: buffers by sweep parity
+        const int it = *reinterpret_cast<volatile const int *>(&A.ctrl->iter);
+        syo = A.sypair[it & 1];
+        szo = A.szpair[it & 1];
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
         const double vy = s_sy[i], vz = s_sz[i];
-        if (vy != 0.0) atomicAdd(&A.s_y[g], vy);
-        if (vz != 0.0) atomicAdd(&A.s_z[g], vz);
+        if (vy != 0.0) atomicAdd(&syo[g], vy);
+        if (vz != 0.0) atomicAdd(&szo[g], vz);
     }
 }
 

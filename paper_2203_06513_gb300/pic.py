@@ -220,11 +220,12 @@ class Pic:
         self._check(self._lib.pic_timing_enable(self._h, 1 if on else 0))
 
     def timing_read(self) -> dict:
-        out = (ctypes.c_double * 8)()
+        out = (ctypes.c_double * 10)()
         self._check(self._lib.pic_timing_read(self._h, out))
         return {"sweep1_ms": out[0], "sweep1_launches": int(out[1]), "sweep2_ms": out[2],
                 "sweep2_launches": int(out[3]), "solve_ms": out[4], "solve_launches": int(out[5]),
-                "launches": int(out[6]), "marker_sweeps1": out[7]}
+                "launches": int(out[6]), "marker_sweeps1": out[7], "warm_ms": out[8],
+                "warm_launches": int(out[9])}
 
 
 def version() -> str:
