@@ -167,6 +167,62 @@ def e2e_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None):
     return {"s": t1 - t0, "h2d": h2d, "d2h": d2h}
 
 
+def _member_inputs(w):
+    x, p = I.particles(w)
+    ay, az, ey, ez = I.fields(w)
+    return x, p, ay, az, ey, ez
+
+
+def ensemble_inputs(n_runs: int, np_scale: float, seed: int):
+    """Inputs of the batched-ensemble workload, generated by a pool of host
+    processes (spawned before any CUDA call)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ws_ = I.ensemble_members(n_runs, seed=seed, np_scale=np_scale)
+    workers = max(1, min(16, (os.cpu_count() or 1)))
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        ins = list(ex.map(_member_inputs, ws_, chunksize=4))
+    return ws_, ins
+
+
+def ensemble_run(pic, torch, ws_, ins, steps, warmup, stream):
+    """All runs in one ensemble (FP32 form, explicit predictor), schedule picked
+    by the autotuner; device-timed steps, each one graph launch."""
+    cfgs = [pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=pic.PIC_WARM_EXPLICIT, sort_every=2)
+            for w in ws_]
+    t0 = time.perf_counter()
+    ens = pic.Ensemble(cfgs, ins, stream=stream.cuda_stream)
+    t_create = time.perf_counter() - t0
+    H0 = [ens.run(r).energy()["total"] for r in range(len(ws_))]
+    cache = os.path.join(ROOT, "paper_2203_06513_gb300", "_build", "ensemble_tune.txt")
+    im, bps, cached = ens.tune(cache)
+    ens.step(warmup)
+    l0 = ens.launches
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sw, st = ens.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = ens.launches - l0
+    H = [ens.run(r).energy()["total"] for r in range(len(ws_))]
+    err = max(abs(a - b) / abs(b) for a, b in zip(H, H0))
+    nps = np.array([w.np for w in ws_], dtype=np.float64)
+    ens.close()
+    total = float(nps.sum())
+    return {"value": total * steps / (ms / 1e3), "unit": UNIT, "runs": len(ws_), "total_np": int(total),
+            "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+            "schedule": {"item_markers": im, "blocks_per_sm": bps, "from_cache": cached},
+            "sweeps_per_step_mean": {"I": float(sw[:, 0].mean() / steps), "II": float(sw[:, 1].mean() / steps)},
+            "sweeps_per_step_max": {"I": float(sw[:, 0].max() / steps), "II": float(sw[:, 1].max() / steps)},
+            "max_rel_energy_err": err, "failed_runs": int((st != 0).sum()),
+            "gpu_launches": int(launches), "create_s": t_create,
+            "workload": "C4: %d runs, nx in {256,512,1024,2048}, Np log-uniform [1e5,4e6], pump U[0.01,0.3], "
+                        "vth U[0.02,0.15], k=3, dt=0.05, FP32 form" % len(ws_)}
+
+
 def oracle_sample(n_sample: int, steps: int, warmup: int):
     """The FP64 CPU oracle on n_sample markers of the workload's grid."""
     from oracle import oracle as O
@@ -216,10 +272,15 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ensemble-runs", type=int, default=256, help="0: skip the batched-ensemble line")
+    ap.add_argument("--ensemble-scale", type=float, default=1.0, help="scale of the runs' marker counts")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
+    ens_in = None
+    if args.ensemble_runs > 0:          # host inputs first: the pool starts before any CUDA call
+        ens_in = ensemble_inputs(args.ensemble_runs, args.ensemble_scale, seed=rank)
 
     import torch
     from paper_2203_06513_gb300 import pic
@@ -270,6 +331,12 @@ def main():
     e2e = None if args.no_e2e else e2e_run(pic, torch, w, arrays, pic.PIC_FP32, head_warm, args.steps,
                                            stream, mlp)
     barrier()
+    ens = None
+    if ens_in is not None:
+        del arrays, x, p
+        ens = ensemble_run(pic, torch, ens_in[0], ens_in[1], max(1, min(args.steps, 10)), 1, stream)
+        ens_in = None
+        barrier()
 
     ms_head = max_over_ranks(r_head["ms"])
     ms_expl = max_over_ranks(r_expl["ms"])
@@ -286,7 +353,7 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu:
-            n_cpu = int(os.environ.get("PIC_CPU_SAMPLE", "100000"))
+            n_cpu = int(os.environ.get("PIC_CPU_SAMPLE", "2000000"))
             cpu = {"value": oracle_sample(n_cpu, 1, 0), "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{n_cpu} markers on the M=2048 grid, 1 step (single thread)"}
 
@@ -320,6 +387,7 @@ def main():
             "gpu_launches": tr["launches"],
             "clocks": clk,
             "cpu_baseline": cpu,
+            "ensemble": ens,
             "e2e": None if e2e is None else {
                 "value": total_np * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d"] / args.steps,

@@ -201,8 +201,6 @@ int pic_set_warm_mlp(pic_handle *h, pic_mlp *m);
 
 /* Message of the last error on h; with h == NULL, the message of the last
  * failed pic_init or pic_deposit_current_noalloc on the calling thread. */
-/* Message of the last error on h; with h == NULL, the message of the last
- * failed pic_init or pic_deposit_current_noalloc on the calling thread. */
 const char *pic_last_error(const pic_handle *h);
 
 /* Path-integrated current deposit for callers that cannot allocate device
@@ -228,6 +226,65 @@ const char *pic_last_error(const pic_handle *h);
  * message via pic_last_error(NULL). */
 int pic_deposit_current_noalloc(double L, int32_t nx, int32_t degree, int64_t np, double weight,
                                 const double *x, const double *disp, double *out, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Batched ensembles.  Many independent runs of the method (each its own
+ * configuration, grid and markers: Sec. 4.2 applied to each) advance together:
+ * one step of the ensemble is one CUDA-graph launch in which every kernel
+ * covers all runs.  Each run keeps its own fixed-point loops; the particle
+ * sweeps are persistent kernels that take work items (a run and a range of its
+ * markers) from a queue rebuilt before every sweep from the runs still
+ * iterating, so a run that has converged drops out while the others go on.
+ * The two loops are conditional (WHILE) graph nodes, ended on the device.
+ * All runs must share degree, precision and warm start (PIC_WARM_NONE or
+ * PIC_WARM_EXPLICIT); grid size, marker count, weight, dt, tolerances and
+ * sort interval may differ.  1 <= nruns <= 1024.
+ * --------------------------------------------------------------------- */
+typedef struct pic_ensemble pic_ensemble;
+
+/* Create the runs (as pic_init with cfgs[r], ins[r], mem) on `stream`.
+ * use_graph = 1: steps run as one graph launch; 0: the same kernels with
+ * the loops driven from the host (one readback per sweep), for checking.
+ * Errors: PIC_ERR_INVALID (mixed degree / precision, an MLP warm start,
+ * nruns out of range, or a run's own pic_init error), PIC_ERR_NOMEM,
+ * PIC_ERR_CUDA; message via pic_last_error(NULL). */
+int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins, int32_t nruns, int32_t mem,
+                        int32_t use_graph, void *stream, pic_ensemble **out);
+
+/* Advance every run by nsteps steps (I then II, then each run's periodic
+ * sort).  sweeps (host, may be NULL): 2*nruns counts, added to, of the
+ * subsystem-I and -II sweeps of each run; status (host, may be NULL): nruns
+ * values, 0 or PIC_ERR_NUMERIC / PIC_ERR_NOCONVERGE / PIC_ERR_CUDA (a bounded
+ * wait gave up) per run; the bits stay set for the life of the ensemble.  A run
+ * with PIC_ERR_NUMERIC or PIC_ERR_CUDA is stopped (keeps its state, takes no
+ * more work); a run with PIC_ERR_NOCONVERGE goes on from its last iterate,
+ * its loops capped at max_iter sweeps.  The other runs are not affected.
+ * Returns the first failing run's error, or PIC_OK. */
+int pic_ensemble_step(pic_ensemble *e, int32_t nsteps, int64_t *sweeps, int32_t *status);
+
+/* Autotuner: pick the work-item size of the batched sweeps (markers per item)
+ * and the number of persistent sweep blocks per SM by timing one ensemble step
+ * per candidate (the steps are real steps: the runs advance) and keeping the
+ * fastest per marker-sweep.  cache_path (may be NULL): a text file of earlier
+ * choices keyed by device and ensemble shape; a hit skips the timing, a new
+ * choice is appended.  choice (host, may be NULL): [markers per item, blocks
+ * per SM, 1 if taken from the cache]. */
+int pic_ensemble_tune(pic_ensemble *e, const char *cache_path, int32_t choice[3]);
+
+/* Set the schedule by hand (markers per item: a positive multiple of 1024;
+ * blocks per SM >= 1, at most what fits). */
+int pic_ensemble_set_schedule(pic_ensemble *e, int32_t item_markers, int32_t blocks_per_sm);
+
+/* The handle of run r (borrowed; valid until pic_ensemble_destroy): use it
+ * with pic_energy, pic_get_state, pic_gather, pic_deposit. */
+pic_handle *pic_ensemble_run(pic_ensemble *e, int32_t r);
+
+/* Kernel launches issued by pic_ensemble_step since creation (graph nodes
+ * executed, counted from the device's loop counters). */
+int64_t pic_ensemble_launches(const pic_ensemble *e);
+
+int pic_ensemble_destroy(pic_ensemble *e);
+const char *pic_ensemble_last_error(const pic_ensemble *e);
 
 /* Library version string, e.g. "libpic 1.0 sm_103a". */
 const char *pic_version(void);

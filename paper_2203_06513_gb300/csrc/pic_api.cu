@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "pic.h"
+#include "pic_handle.h"
 #include "pic_internal.h"
 
 using namespace pic;
@@ -23,54 +24,6 @@ static thread_local std::string g_init_error;
 
 void pic::set_thread_error(const char *msg) { g_init_error = msg ? msg : ""; }
 
-struct pic_handle {
-    pic_config cfg{};
-    cudaStream_t stream = nullptr;
-    int device = 0, num_sms = 0;
-    int M = 0, K = 0, H = 0, Dlim = 0, fp32 = 0;
-    long long np = 0;
-    double dx = 0.0;
-    size_t rsize = 8;               // bytes of one particle real
-    long long steps_done = 0;
-
-    // marker state: two copies of (cell, t, p, id) for the counting sort
-    PartPtrs P[2]{};
-    int cur = 0;
-    void *delta = nullptr, *pnew = nullptr;
-
-    // grid state (double)
-    double *ex = nullptr, *ey = nullptr, *ez = nullptr, *ay = nullptr, *az = nullptr;
-    double *ek = nullptr, *ebar = nullptr, *ga_y = nullptr, *ga_z = nullptr, *jb[2] = {nullptr, nullptr};
-    double *eky = nullptr, *ekz = nullptr, *aky = nullptr, *akz = nullptr;
-    double *by = nullptr, *bz = nullptr, *r0y = nullptr, *r0z = nullptr;
-    double *sy[2] = {nullptr, nullptr}, *sz[2] = {nullptr, nullptr};
-    double *rho = nullptr, *work = nullptr, *diag = nullptr;
-    int32_t *counts = nullptr;
-
-    // circulant bands and inverse taps
-    double *d_rowM0 = nullptr, *d_rowM1 = nullptr, *d_rowK = nullptr, *d_rowPm = nullptr;
-    double *d_tapM1 = nullptr, *d_tapP = nullptr;
-    int tapM1_start = 0, tapM1_n = 0, tapP_start = 0, tapP_n = 0;
-
-    DevCtrl *ctrl = nullptr;
-    int *h_flag = nullptr;          // pinned: converged flag readback
-    DevCtrl *h_ctrl = nullptr;      // pinned: full control block readback
-
-    int sweep_grid = 0, sweep_block = kSweepThreads;
-    size_t smem1 = 0, smem2 = 0;
-
-    // timing
-    int timing = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double t_sw1 = 0, t_sw2 = 0, t_solve = 0;
-    long long n_sw1 = 0, n_sw2 = 0, n_solve = 0, launches = 0, marker_sweeps = 0;
-
-    double t_warm = 0;
-    long long n_warm = 0;
-    pic_mlp *mlp = nullptr;         // borrowed warm-start network
-
-    std::string err;
-};
 
 static const char *kVersion = "libpic 1.0 sm_103a";
 
@@ -204,6 +157,9 @@ static int sort_markers(pic_handle *h)
     h->cur = 1 - h->cur;
     return PIC_OK;
 }
+
+int pic::handle_sort(pic_handle *h) { return sort_markers(h); }
+PartPtrs pic::handle_parts(pic_handle *h) { return cur_parts(h); }
 
 // ------------------------------------------------------------------ charge + Poisson
 static int deposit_charge(pic_handle *h, double *out)

@@ -138,11 +138,15 @@ __device__ void decide(const ConvArgs &A)
             if (!(r < 0.9)) r = 0.9;
             return v * r / (1.0 - r);
         };
-        // field tolerance: the absolute tol, or 1e-10 of the field's max-norm when
-        // that is larger (float markers resolve the field to about 1e-7 relative,
-        // so a tighter absolute target only waits for noise)
+        // field tolerance.  Subsystem I: the absolute tol, or 1e-10 of the field's
+        // max-norm when that is larger (markers at float positions resolve e_x to
+        // about 1e-7 relative, so a tighter target only waits for noise).
+        // Subsystem II: the absolute tol.  Its markers do not move, the sweep is
+        // deterministic, and the remaining field error enters the transverse
+        // energy directly (a field error of 1e-10 relative already shows as a
+        // 1e-11 energy drift per step).
         const double emag = bits_to_double(c->emag_bits);
-        const double etol = fmax(A.tol, 1e-10 * emag);
+        const double etol = (A.subsystem == 1) ? fmax(A.tol, 1e-10 * emag) : A.tol;
         const bool dok = (A.subsystem == 1) ? (est(d, dp) <= A.dtol) : true;
         const bool eok = est(e, ep) <= etol;
         const bool dstag = (A.subsystem == 1) ? (d >= 0.5 * dp && d <= 1e-4) : true;
@@ -163,17 +167,17 @@ __device__ void decide(const ConvArgs &A)
     c->emag_bits = 0ull;
     c->ticket = 0u;
     __threadfence();
-    if (A.graph) cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond_handle, stop ? 0u : 1u);
+    if (A.graph && A.cond_handle)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond_handle, stop ? 0u : 1u);
 }
 
 // y_i = sum_n taps[n] in[(i - (d_start + n)) mod M], one output per thread,
 // input and taps staged in shared memory (input twice, so no index wraps).
-__global__ void __launch_bounds__(64) k_conv(ConvArgs A)
+// Block bx of component comp; returns true in the one block that finished the
+// run's solve last (after the convergence decision, in the solve modes).
+__device__ bool conv_block(const ConvArgs &A, int bx, int comp, double *s_conv, double *s_red)
 {
-    extern __shared__ __align__(16) double s_conv[];
-    __shared__ double s_red[32];
     const int M = A.M;
-    const int comp = blockIdx.y;
     double *s_in = s_conv;              // 2M
     double *s_tap = s_conv + 2 * M;     // ntap
     const double *in = A.in[comp];
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(64) k_conv(ConvArgs A)
     }
     for (int n = threadIdx.x; n < A.ntap; n += blockDim.x) s_tap[n] = A.taps[n];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     double diff = 0.0, mag = 0.0;
     if (i < M) {
         // offsets d = d_start + n lie in [-(M-1)/2, M/2], so i - d + off is in [0, 2M)
@@ -224,15 +228,83 @@ __global__ void __launch_bounds__(64) k_conv(ConvArgs A)
             zero[i] = 0.0;
         }
     }
-    if (A.mode == CONV_PLAIN) return;
+    if (A.mode == CONV_PLAIN) return false;
     block_max_to(&A.ctrl->emax_bits, diff, s_red);
     block_max_to(&A.ctrl->emag_bits, mag, s_red);
+    __shared__ int s_last;
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned int nblk = gridDim.x * gridDim.y;
+        const unsigned int nblk = (unsigned)(((M + blockDim.x - 1) / blockDim.x) * A.ncomp);
         const unsigned int t = atomicAdd(&A.ctrl->ticket, 1u);
-        if (t == nblk - 1) decide(A);
+        s_last = (t == nblk - 1) ? 1 : 0;
+        if (s_last) decide(A);
     }
+    __syncthreads();
+    return s_last != 0;
+}
+
+__global__ void __launch_bounds__(64) k_conv(ConvArgs A)
+{
+    extern __shared__ __align__(16) double s_conv[];
+    __shared__ double s_red[32];
+    conv_block(A, blockIdx.x, blockIdx.y, s_conv, s_red);
+}
+
+// Batched solves of an ensemble: block (bx, run, comp).  Runs that are not in
+// the current sweep (converged, or stopped by an error) are skipped.  After a
+// run's decision, the last run to decide in this sweep records whether any run
+// goes on, and sets the loop's conditional handle (graph mode).
+__global__ void __launch_bounds__(64) k_conv_ens(const ConvArgs *runs, EnsQueue *Q, int *sweeps,
+                                                 unsigned long long cond)
+{
+    extern __shared__ __align__(16) double s_conv[];
+    __shared__ double s_red[32];
+    const int r = blockIdx.y, comp = blockIdx.z;
+    const ConvArgs &A = runs[r];
+    if (A.mode != CONV_PLAIN && !Q->active[r]) return;
+    if (comp >= A.ncomp || (int)(blockIdx.x * blockDim.x) >= A.M) return;
+    const bool last = conv_block(A, blockIdx.x, comp, s_conv, s_red);
+    if (!last || threadIdx.x != 0) return;
+    atomicAdd(&sweeps[2 * r + A.subsystem - 1], 1);
+    if (!A.ctrl->converged) atomicAdd(&Q->n_continue, 1);
+    __threadfence();
+    const int t = atomicAdd(&Q->n_decided, 1);
+    if (t == Q->nactive - 1) {
+        __threadfence();
+        const int go = atomicAdd(&Q->n_continue, 0) > 0 ? 1 : 0;
+        Q->go = go;
+        Q->loops[A.subsystem - 1] += 1;
+        if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, (unsigned)go);
+    }
+}
+
+static int conv_optin(const void *fn, size_t smem, size_t &opted)
+{
+    if (smem > 48 * 1024 && smem > opted) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return 1;
+        opted = smem;
+    }
+    return 0;
+}
+
+static size_t g_conv_ens_opted = 0;
+
+// raise the shared-memory limit of k_conv_ens before any capture of it
+int conv_ens_optin(int Mmax, int ntap_max)
+{
+    const size_t smem = (2 * (size_t)Mmax + (size_t)ntap_max) * sizeof(double);
+    return conv_optin((const void *)k_conv_ens, smem, g_conv_ens_opted);
+}
+
+int launch_conv_ens(const ConvArgs *runs, int nruns, int Mmax, int ncomp, int ntap_max, EnsQueue *Q,
+                    int *sweeps, unsigned long long cond, cudaStream_t s)
+{
+    const size_t smem = (2 * (size_t)Mmax + (size_t)ntap_max) * sizeof(double);
+    if (smem > 48 * 1024 && smem > g_conv_ens_opted) return 1;   // conv_ens_optin first
+    dim3 grid((Mmax + 63) / 64, nruns, ncomp);
+    k_conv_ens<<<grid, 64, smem, s>>>(runs, Q, sweeps, cond);
+    return 0;
 }
 
 int launch_conv(const ConvArgs &a, cudaStream_t s)
@@ -241,11 +313,7 @@ int launch_conv(const ConvArgs &a, cudaStream_t s)
     dim3 grid((a.M + threads - 1) / threads, a.ncomp);
     const size_t smem = (2 * (size_t)a.M + (size_t)a.ntap) * sizeof(double);
     static size_t opted = 0;   // largest dynamic shared memory opted in so far
-    if (smem > 48 * 1024 && smem > opted) {
-        if (cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return 1;
-        opted = smem;
-    }
+    if (conv_optin((const void *)k_conv, smem, opted)) return 1;
     k_conv<<<grid, threads, smem, s>>>(a);
     return 0;
 }
@@ -254,11 +322,22 @@ int launch_conv(const ConvArgs &a, cudaStream_t s)
 // Subsystem I preparation: (G a)_i = (a_i - a_{i-1}) / dx, e^(0) = e^n,
 // ebar = e^n, cleared deposit buffers, reset control block.
 // ---------------------------------------------------------------------------
-__global__ void k_prep1(int M, double dx, const double *ex, double *ek, double *ebar,
-                        const double *ay, const double *az, double *gay, double *gaz,
-                        double *j0, double *j1, DevCtrl *ctrl)
+__device__ __forceinline__ void ctrl_loop_reset(DevCtrl *ctrl)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    ctrl->dmax_bits = 0ull;
+    ctrl->emax_bits = 0ull;
+    ctrl->emag_bits = 0ull;
+    ctrl->dprev_bits = 0x7ff0000000000000ull;
+    ctrl->eprev_bits = 0x7ff0000000000000ull;
+    ctrl->iter = 0;
+    ctrl->converged = 0;
+    ctrl->ticket = 0u;
+}
+
+__device__ __forceinline__ void prep1_at(int i, int M, double dx, const double *ex, double *ek,
+                                         double *ebar, const double *ay, const double *az,
+                                         double *gay, double *gaz, double *j0, double *j1, DevCtrl *ctrl)
+{
     if (i < M) {
         const int im = (i == 0) ? M - 1 : i - 1;
         gay[i] = (ay[i] - ay[im]) / dx;
@@ -268,16 +347,27 @@ __global__ void k_prep1(int M, double dx, const double *ex, double *ek, double *
         j0[i] = 0.0;
         j1[i] = 0.0;
     }
-    if (i == 0) {
-        ctrl->dmax_bits = 0ull;
-        ctrl->emax_bits = 0ull;
-        ctrl->emag_bits = 0ull;
-        ctrl->dprev_bits = 0x7ff0000000000000ull;
-        ctrl->eprev_bits = 0x7ff0000000000000ull;
-        ctrl->iter = 0;
-        ctrl->converged = 0;
-        ctrl->ticket = 0u;
-    }
+    if (i == 0) ctrl_loop_reset(ctrl);
+}
+
+__global__ void k_prep1(int M, double dx, const double *ex, double *ek, double *ebar,
+                        const double *ay, const double *az, double *gay, double *gaz,
+                        double *j0, double *j1, DevCtrl *ctrl)
+{
+    prep1_at(blockIdx.x * blockDim.x + threadIdx.x, M, dx, ex, ek, ebar, ay, az, gay, gaz, j0, j1, ctrl);
+}
+
+__global__ void k_prep1_ens(const RunDesc *runs)
+{
+    const RunDesc &R = runs[blockIdx.y];
+    prep1_at(blockIdx.x * blockDim.x + threadIdx.x, R.M, R.dx, R.ex, R.ek, R.ebar, R.ay, R.az, R.ga_y,
+             R.ga_z, R.j0, R.j1, R.ctrl);
+}
+
+int launch_prep1_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
+{
+    k_prep1_ens<<<dim3((Mmax + 255) / 256, nruns), 256, 0, s>>>(R);
+    return 0;
 }
 
 int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, const double *ay,
@@ -292,12 +382,12 @@ int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, c
 // Subsystem II preparation: b = (M0 - dt^2/4 K) e^n + dt K a^n (banded
 // circulant products), e^(0) = e^n, a^(0) = a^n - dt e^n, cleared deposits.
 // ---------------------------------------------------------------------------
-__global__ void k_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
-                        const double *ey, const double *ez, const double *ay, const double *az,
-                        double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
-                        double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl)
+__device__ __forceinline__ void prep2_at(int i, int M, int K, double dt, const double *rowPm,
+                                         const double *rowK, const double *ey, const double *ez,
+                                         const double *ay, const double *az, double *by, double *bz,
+                                         double *eky, double *ekz, double *aky, double *akz, double *s00,
+                                         double *s01, double *s10, double *s11, DevCtrl *ctrl)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < M) {
         double vy = rowPm[0] * ey[i] + dt * rowK[0] * ay[i];
         double vz = rowPm[0] * ez[i] + dt * rowK[0] * az[i];
@@ -314,16 +404,29 @@ __global__ void k_prep2(int M, int K, double dt, const double *rowPm, const doub
         akz[i] = az[i] - dt * ez[i];
         s00[i] = 0.0; s01[i] = 0.0; s10[i] = 0.0; s11[i] = 0.0;
     }
-    if (i == 0) {
-        ctrl->dmax_bits = 0ull;
-        ctrl->emax_bits = 0ull;
-        ctrl->emag_bits = 0ull;
-        ctrl->dprev_bits = 0x7ff0000000000000ull;
-        ctrl->eprev_bits = 0x7ff0000000000000ull;
-        ctrl->iter = 0;
-        ctrl->converged = 0;
-        ctrl->ticket = 0u;
-    }
+    if (i == 0) ctrl_loop_reset(ctrl);
+}
+
+__global__ void k_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
+                        const double *ey, const double *ez, const double *ay, const double *az,
+                        double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
+                        double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl)
+{
+    prep2_at(blockIdx.x * blockDim.x + threadIdx.x, M, K, dt, rowPm, rowK, ey, ez, ay, az, by, bz, eky,
+             ekz, aky, akz, s00, s01, s10, s11, ctrl);
+}
+
+__global__ void k_prep2_ens(const RunDesc *runs)
+{
+    const RunDesc &R = runs[blockIdx.y];
+    prep2_at(blockIdx.x * blockDim.x + threadIdx.x, R.M, R.K, R.dt, R.rowPm, R.rowK, R.ey, R.ez, R.ay,
+             R.az, R.by, R.bz, R.eky, R.ekz, R.aky, R.akz, R.sy0, R.sz0, R.sy1, R.sz1, R.ctrl);
+}
+
+int launch_prep2_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
+{
+    k_prep2_ens<<<dim3((Mmax + 255) / 256, nruns), 256, 0, s>>>(R);
+    return 0;
 }
 
 int launch_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
@@ -352,6 +455,90 @@ int launch_copy(int M, const double *src0, double *dst0, const double *src1, dou
                 const double *src2, double *dst2, const double *src3, double *dst3, cudaStream_t s)
 {
     k_copy4<<<(M + 255) / 256, 256, 0, s>>>(M, src0, dst0, src1, dst1, src2, dst2, src3, dst3);
+    return 0;
+}
+
+// End of a substep for every run of an ensemble: I: e_x = e^(k); II: e_perp =
+// e^(k), a_perp = a^(k).  Runs stopped by an error keep their fields.
+__global__ void k_copy_ens(const RunDesc *runs, int which)
+{
+    const RunDesc &R = runs[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R.M || (R.ctrl->status & (STATUS_NUMERIC | STATUS_TIMEOUT))) return;
+    if (which == 1) {
+        R.ex[i] = R.ek[i];
+    } else {
+        R.ey[i] = R.eky[i];
+        R.ez[i] = R.ekz[i];
+        R.ay[i] = R.aky[i];
+        R.az[i] = R.akz[i];
+    }
+}
+
+int launch_copy_ens(const RunDesc *R, int nruns, int Mmax, int which, cudaStream_t s)
+{
+    k_copy_ens<<<dim3((Mmax + 255) / 256, nruns), 256, 0, s>>>(R, which);
+    return 0;
+}
+
+// Work list of the next batched sweep: the runs still iterating (not converged,
+// not stopped by an error), each cut into items of item_markers markers;
+// item_start is the exclusive prefix sum of the items per run.
+__global__ void __launch_bounds__(1024) k_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns)
+{
+    __shared__ int s_scan[1024];
+    __shared__ int s_nact[32];
+    const int r = threadIdx.x;
+    int items = 0, act = 0;
+    if (r < nruns) {
+        const DevCtrl *c = runs[r].ctrl;
+        act = (!c->converged && !(c->status & (STATUS_NUMERIC | STATUS_TIMEOUT))) ? 1 : 0;
+        const long long im = Q->item_markers;
+        items = act ? (int)((runs[r].np + im - 1) / im) : 0;
+        Q->active[r] = act;
+    }
+    // inclusive scan (Hillis-Steele) over the block
+    s_scan[r] = items;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int v = r >= o ? s_scan[r - o] : 0;
+        __syncthreads();
+        s_scan[r] += v;
+        __syncthreads();
+    }
+    if (r < nruns) Q->item_start[r + 1] = s_scan[r];
+    const unsigned b = __ballot_sync(0xffffffffu, act != 0);
+    if ((r & 31) == 0) s_nact[r >> 5] = __popc(b);
+    __syncthreads();
+    if (r == 0) {
+        int n = 0;
+        for (int w = 0; w < 32; ++w) n += s_nact[w];
+        Q->item_start[0] = 0;
+        Q->nitems = s_scan[nruns - 1];
+        Q->nactive = n;
+        Q->next = 0;
+        Q->n_decided = 0;
+        Q->n_continue = 0;
+        Q->go = 0;
+    }
+}
+
+__global__ void k_ens_status(const EnsRun *runs, int nruns, int *status)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nruns) status[r] = runs[r].ctrl->status;
+}
+
+int launch_ens_status(const EnsRun *runs, int nruns, int *status, cudaStream_t s)
+{
+    k_ens_status<<<(nruns + 255) / 256, 256, 0, s>>>(runs, nruns, status);
+    return 0;
+}
+
+int launch_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns, cudaStream_t s)
+{
+    if (nruns < 1 || nruns > kEnsMaxRuns) return 1;
+    k_ens_plan<<<1, 1024, 0, s>>>(Q, runs, nruns);
     return 0;
 }
 

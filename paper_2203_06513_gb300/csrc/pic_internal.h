@@ -117,6 +117,58 @@ struct ConvArgs {
 };
 
 int launch_conv(const ConvArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------- batched ensemble
+// Many independent runs advance together: one launch of each kernel covers every
+// run.  The particle sweeps are persistent kernels that claim work items (a run
+// and a range of item_markers of its markers) from a queue built before each
+// sweep from the runs still iterating; grid-side kernels take one block row per run.
+constexpr int kEnsMaxRuns = 1024;
+
+struct EnsQueue {
+    int next;                // claim counter of the current sweep
+    int nitems;              // items of the current sweep
+    int nactive;             // runs in the current sweep
+    int n_decided;           // runs that took their convergence decision in this sweep
+    int n_continue;          // ... and go on
+    int go;                  // 1: some run goes on after this sweep
+    int item_markers;        // markers per item (a multiple of the tile size)
+    int nblocks;             // sweep blocks that claim items (the rest leave at once)
+    int loops[2];            // sweeps of the loops of subsystems I and II (all runs together)
+    int item_start[kEnsMaxRuns + 1];
+    int active[kEnsMaxRuns];
+};
+
+struct EnsRun {
+    long long np;
+    DevCtrl *ctrl;
+};
+
+// per-run pointers of the grid-side kernels
+struct RunDesc {
+    int M, K, fp32;
+    long long np;
+    double dx, dt;
+    PartPtrs P;
+    double *ex, *ek, *ebar, *ay, *az, *ga_y, *ga_z, *j0, *j1;
+    const double *rowPm, *rowK;
+    double *ey, *ez, *by, *bz, *eky, *ekz, *aky, *akz, *sy0, *sz0, *sy1, *sz1;
+    DevCtrl *ctrl;
+};
+
+int launch_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns, cudaStream_t s);
+int launch_ens_status(const EnsRun *runs, int nruns, int *status, cudaStream_t s);
+int conv_ens_optin(int Mmax, int ntap_max);
+int launch_conv_ens(const ConvArgs *runs, int nruns, int Mmax, int ncomp, int ntap_max, EnsQueue *Q,
+                    int *sweeps, unsigned long long cond, cudaStream_t s);
+int launch_prep1_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s);
+int launch_prep2_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s);
+int launch_copy_ens(const RunDesc *R, int nruns, int Mmax, int which, cudaStream_t s);
+int launch_sweep1_ens(int K, int fp32, const Sweep1Args *runs, int nruns, EnsQueue *Q, int grid,
+                      size_t smem, cudaStream_t s);
+int launch_sweep2_ens(int K, int fp32, const Sweep2Args *runs, int nruns, EnsQueue *Q, int grid,
+                      size_t smem, cudaStream_t s);
+int launch_finalize1_ens(int fp32, const RunDesc *R, int nruns, int grid_x, cudaStream_t s);
 int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, const double *ay,
                  const double *az, double *ga_y, double *ga_z, double *j0, double *j1,
                  DevCtrl *ctrl, cudaStream_t s);

@@ -15,7 +15,9 @@
 // tau = dt/dx (fields are staged as e dx and a_j - a_{j-1}), so the discrete
 // work identity (p^(k+1) - p^n) vbar = (Ebar - F)(x^(k+1) - x^n) of Sec. 4.2
 // holds with the same rounded factor on both sides.
+#include <algorithm>
 #include <climits>
+#include <mutex>
 #include <type_traits>
 
 #include "pic_internal.h"
@@ -100,12 +102,14 @@ __device__ __forceinline__ void block_chunk(long long np, long long &beg, long l
     end = beg + chunk < np ? beg + chunk : np;
 }
 
-// Markers stream through shared memory in tiles of kTile (a block's chunk is cut
-// into tiles; tile i goes to stage i % 2).  One thread issues the bulk copies of
-// a tile's arrays (cp.async.bulk, completed on the stage's mbarrier) two tiles
-// ahead of the consumers, so the DRAM latency of the next tile overlaps the
-// arithmetic on the current one.  The marker arrays are allocated with padding,
-// so a tile's byte count may be rounded up to a multiple of 16.
+// Markers stream through shared memory in tiles of kTile (a block's range is cut
+// into tiles; the block's q-th tile overall goes to stage q % 2).  One thread
+// issues the bulk copies of a tile's arrays (cp.async.bulk, completed on the
+// stage's mbarrier) two tiles ahead of the consumers, so the DRAM latency of the
+// next tile overlaps the arithmetic on the current one.  The marker arrays are
+// allocated with padding, so a tile's byte count may be rounded up to a multiple
+// of 16.  A block may process several ranges (batched runs); the tile sequence
+// number q runs on across them, so the stage parities stay consistent.
 constexpr int kTileU = 2;                      // markers per thread per tile
 constexpr int kTile = kSweepThreads * kTileU;  // markers per tile
 
@@ -113,17 +117,29 @@ struct TileBars {
     unsigned long long full[2];
 };
 
+__device__ __forceinline__ void tile_bars_init(TileBars &B)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&B.full[0], 1);
+        mbar_init(&B.full[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
 // Returns false (block-uniform) when a bounded wait gave up; the caller then
 // drains the copies it has in flight (bounded) and leaves.
-__device__ __forceinline__ bool tile_wait(TileBars &B, long long i)
+__device__ __forceinline__ bool tile_wait(TileBars &B, unsigned long long q)
 {
-    const bool ok = mbar_wait(&B.full[i & 1], (unsigned)((i >> 1) & 1));
+    const bool ok = mbar_wait(&B.full[q & 1], (unsigned)((q >> 1) & 1));
     return !__syncthreads_or(!ok);
 }
 
-__device__ __forceinline__ void tile_drain(TileBars &B, long long i, long long ntile)
+// waits (bounded) for the tiles q .. qend-1 still in flight, at most two
+__device__ __forceinline__ void tile_drain(TileBars &B, unsigned long long q, unsigned long long qend)
 {
-    for (long long k = i; k < ntile && k < i + 2; ++k) mbar_wait(&B.full[k & 1], (unsigned)((k >> 1) & 1));
+    for (unsigned long long k = q; k < qend && k < q + 2; ++k)
+        mbar_wait(&B.full[k & 1], (unsigned)((k >> 1) & 1));
 }
 
 // ---------------------------------------------------------------------------
@@ -136,10 +152,12 @@ __device__ __forceinline__ void tile_drain(TileBars &B, long long i, long long n
 //   j_i += w int_{x^n}^{x^n+delta^(k+1)} Lambda^1_i.
 // In cell units with tau = dt/dx: p^(k+1) = p^n + tau (Ebar dx - (A1+A0).D dx/(...)).
 // ---------------------------------------------------------------------------
+// Markers [beg, end) of one run.  q = the block's tile sequence number (in/out).
+// Returns false after a bounded wait gave up (the block must then stop).
 template <int K, typename R>
-__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1(Sweep1Args A)
+__device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg, long long end,
+                                             unsigned char *smem, unsigned long long &q)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
     const int H = A.H;
     const int W = A.M + 2 * H;
     TileBars &Bars = *reinterpret_cast<TileBars *>(smem);
@@ -157,9 +175,8 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
     double *s_red = s_acc + W;
     FieldTile<R> F = carve_tile<R>(reinterpret_cast<unsigned char *>(s_red + 32), W);
 
-    long long beg, end;
-    block_chunk(A.np, beg, end);
     const long long ntile = end > beg ? (end - beg + kTile - 1) / kTile : 0;
+    const unsigned long long q0 = q, qend = q + (unsigned long long)ntile;
     double *jout = A.j;
     bool warm = A.warm != 0;
     if (A.graph) {                          // replayed by a graph: buffers by sweep parity
@@ -168,11 +185,11 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
         warm = warm && it == 0;
     }
     const bool need_delta = !warm;
-    auto issue = [&](long long i) {            // one thread: copies of tile i into stage i % 2
+    auto issue = [&](long long i) {            // one thread: copies of tile i into stage (q0 + i) % 2
         const long long s0 = beg + i * kTile;
         long long n = end - s0 < kTile ? end - s0 : kTile;
         n = (n + 3) & ~3LL;
-        const int b = (int)(i & 1);
+        const int b = (int)((q0 + i) & 1);
         const unsigned bi = (unsigned)(n * sizeof(int32_t)), br = (unsigned)(n * sizeof(R));
         fence_proxy_async();
         mbar_expect_tx(&Bars.full[b], bi + 2 * br + (need_delta ? br : 0u));
@@ -181,12 +198,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
         bulk_g2s(s_p[b], static_cast<const R *>(A.P.p) + s0, br, &Bars.full[b]);
         if (need_delta) bulk_g2s(s_d[b], static_cast<const R *>(A.P.delta) + s0, br, &Bars.full[b]);
     };
-    if (threadIdx.x == 0) {
-        mbar_init(&Bars.full[0], 1);
-        mbar_init(&Bars.full[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
+    __syncthreads();                           // shared memory of a previous range is free
     if (threadIdx.x == 0) {
         if (ntile > 0) issue(0);
         if (ntile > 1) issue(1);
@@ -227,12 +239,12 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
     int wb = INT_MIN;
 
     for (long long i = 0; i < ntile; ++i) {
-        if (!tile_wait(Bars, i)) {
+        if (!tile_wait(Bars, q0 + i)) {
             timeout = true;
-            tile_drain(Bars, i, ntile);
+            tile_drain(Bars, q0 + i, qend);
             break;
         }
-        const int b = (int)(i & 1);
+        const int b = (int)((q0 + i) & 1);
         const long long s0 = beg + i * kTile;
 #pragma unroll 1
         for (int u = 0; u < kTileU; ++u) {
@@ -333,6 +345,19 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
         const double val = s_acc[i];
         if (val != 0.0) atomicAdd(&jout[wrap_cell(i - H, A.M)], val);
     }
+    q = qend;
+    return !timeout;
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1(Sweep1Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    tile_bars_init(*reinterpret_cast<TileBars *>(smem));
+    long long beg, end;
+    block_chunk(A.np, beg, end);
+    unsigned long long q = 0;
+    sweep1_range<K, R>(A, beg, end, smem, q);
 }
 
 size_t sweep1_smem(int M, int H, int fp32)
@@ -424,9 +449,9 @@ int launch_current(const CurrentArgs &a, int grid, int block, size_t smem, cudaS
 // (bulk copies of cell, t, p two tiles ahead) as the subsystem-I sweep.
 // ---------------------------------------------------------------------------
 template <int K, typename R>
-__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2(Sweep2Args A)
+__device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg, long long end,
+                                             unsigned char *smem, unsigned long long &q)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
     const int H = A.H;
     const int W = A.M + 2 * H;
     TileBars &Bars = *reinterpret_cast<TileBars *>(smem);
@@ -444,15 +469,16 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
     using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
     R2 *s_an = reinterpret_cast<R2 *>(s_sz + W);
     R2 *s_ak = s_an + W;
+    // float form: the rounding residues of a^n + a^(k) per node (see below)
+    float2 *s_lo = reinterpret_cast<float2 *>(s_ak + W);
 
-    long long beg, end;
-    block_chunk(A.np, beg, end);
     const long long ntile = end > beg ? (end - beg + kTile - 1) / kTile : 0;
+    const unsigned long long q0 = q, qend = q + (unsigned long long)ntile;
     auto issue = [&](long long i) {
         const long long s0 = beg + i * kTile;
         long long n = end - s0 < kTile ? end - s0 : kTile;
         n = (n + 3) & ~3LL;
-        const int b = (int)(i & 1);
+        const int b = (int)((q0 + i) & 1);
         const unsigned bi = (unsigned)(n * sizeof(int32_t)), br = (unsigned)(n * sizeof(R));
         fence_proxy_async();
         mbar_expect_tx(&Bars.full[b], bi + 2 * br);
@@ -460,12 +486,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
         bulk_g2s(s_t[b], static_cast<const R *>(A.P.t) + s0, br, &Bars.full[b]);
         bulk_g2s(s_p[b], static_cast<const R *>(A.P.p) + s0, br, &Bars.full[b]);
     };
-    if (threadIdx.x == 0) {
-        mbar_init(&Bars.full[0], 1);
-        mbar_init(&Bars.full[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
+    __syncthreads();                           // shared memory of a previous range is free
     if (threadIdx.x == 0) {
         if (ntile > 0) issue(0);
         if (ntile > 1) issue(1);
@@ -474,10 +495,22 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
     const double inv_fact = 1.0 / (double)Fact<K>::v;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
-        s_an[i].x = (R)(A.an_y[g] * inv_fact);
-        s_an[i].y = (R)(A.an_z[g] * inv_fact);
-        s_ak[i].x = (R)(A.ak_y[g] * inv_fact);
-        s_ak[i].y = (R)(A.ak_z[g] * inv_fact);
+        const double ny = A.an_y[g] * inv_fact, nz = A.an_z[g] * inv_fact;
+        const double ky = A.ak_y[g] * inv_fact, kz = A.ak_z[g] * inv_fact;
+        s_an[i].x = (R)ny;
+        s_an[i].y = (R)nz;
+        s_ak[i].x = (R)ky;
+        s_ak[i].y = (R)kz;
+        if constexpr (Real<R>::fp32) {
+            // The float rounding of a coefficient is the same for every marker near
+            // its node, so it does not average out over markers: in the exchange
+            // term (A1 - A0)(A1 + A0)/(g0 + g1) it shows as an energy error of
+            // about 1e-11 per step.  The residues of the sum a^n + a^(k) are kept
+            // and enter the numerator before its one rounding, which leaves only
+            // per-marker rounding (unbiased on average).
+            s_lo[i] = make_float2((float)((ny - (double)s_an[i].x) + (ky - (double)s_ak[i].x)),
+                                  (float)((nz - (double)s_an[i].y) + (kz - (double)s_ak[i].y)));
+        }
         s_sy[i] = 0.0;
         s_sz[i] = 0.0;
     }
@@ -491,12 +524,12 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
     wz.clear();
     int wb = INT_MIN;
     for (long long i = 0; i < ntile; ++i) {
-        if (!tile_wait(Bars, i)) {
+        if (!tile_wait(Bars, q0 + i)) {
             timeout = true;
-            tile_drain(Bars, i, ntile);
+            tile_drain(Bars, q0 + i, qend);
             break;
         }
-        const int b = (int)(i & 1);
+        const int b = (int)((q0 + i) & 1);
         const long long s0 = beg + i * kTile;
 #pragma unroll 1
         for (int u = 0; u < kTileU; ++u) {
@@ -530,8 +563,29 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
             const R pp1 = one + p * p;
             const R g0 = sqrt_(pp1 + A0y * A0y + A0z * A0z);
             const R g1 = sqrt_(pp1 + A1y * A1y + A1z * A1z);
+            R Ly = R(0), Lz = R(0);
+            if constexpr (Real<R>::fp32) {
+#pragma unroll
+                for (int r = 0; r <= K; ++r) {
+                    const float2 l = s_lo[c - r + H];
+                    Ly += l.x * v[r];
+                    Lz += l.y * v[r];
+                }
+            }
             const R cf = fdiv_(one, g0 + g1);
-            const R fy = cf * (A0y + A1y), fz = cf * (A0z + A1z);
+            const R sy = A0y + A1y, sz = A0z + A1z;
+            R fy, fz;
+            if constexpr (Real<R>::fp32) {
+                // f = cf (s + L) rounded once: the residue L is far below half an ulp
+                // of s, so s + L in float would drop it.  The product's own rounding
+                // error (exact by an fma) and cf L are added before the one rounding.
+                const float py = cf * sy, pz = cf * sz;
+                fy = py + (fmaf(cf, sy, -py) + cf * Ly);
+                fz = pz + (fmaf(cf, sz, -pz) + cf * Lz);
+            } else {
+                fy = cf * sy;
+                fz = cf * sz;
+            }
             R vy[K + 1], vz[K + 1];
 #pragma unroll
             for (int r = 0; r <= K; ++r) {
@@ -568,13 +622,26 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
         if (vy != 0.0) atomicAdd(&syo[g], vy);
         if (vz != 0.0) atomicAdd(&szo[g], vz);
     }
+    q = qend;
+    return !timeout;
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2(Sweep2Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    tile_bars_init(*reinterpret_cast<TileBars *>(smem));
+    long long beg, end;
+    block_chunk(A.np, beg, end);
+    unsigned long long q = 0;
+    sweep2_range<K, R>(A, beg, end, smem, q);
 }
 
 size_t sweep2_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
     const size_t stages = 2 * (size_t)kTile * (sizeof(int32_t) + 2 * (fp32 ? sizeof(float) : sizeof(double)));
-    return 128 + stages + 2 * W * sizeof(double) + 2 * W * (fp32 ? sizeof(float2) : sizeof(double2));
+    return 128 + stages + 2 * W * sizeof(double) + (fp32 ? 3 * W * sizeof(float2) : 2 * W * sizeof(double2));
 }
 
 template <typename R>
@@ -731,14 +798,14 @@ int launch_kinetic(const DiagArgs &a, int grid, int block, cudaStream_t s)
 // wrapped periodically), p^{n+1} = p^(k+1); the iterate is reset.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_finalize1(long long np, int M, PartPtrs P)
+__device__ __forceinline__ void finalize1_range(long long np, int M, const PartPtrs &P, long long a0,
+                                                long long stride)
 {
     R *tp = static_cast<R *>(P.t);
     R *pp = static_cast<R *>(P.p);
     R *dp = static_cast<R *>(P.delta);
     const R *pnp = static_cast<const R *>(P.pnew);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < np; a += stride) {
+    for (long long a = a0; a < np; a += stride) {
         const R s = tp[a] + dp[a];
         const R f = floor_(s);
         int c = P.cell[a] + (int)f;
@@ -749,6 +816,13 @@ __global__ void __launch_bounds__(256) k_finalize1(long long np, int M, PartPtrs
         pp[a] = pnp[a];
         dp[a] = R(0);
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_finalize1(long long np, int M, PartPtrs P)
+{
+    finalize1_range<R>(np, M, P, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                       (long long)gridDim.x * blockDim.x);
 }
 
 int launch_finalize1(int fp32, long long np, int M, PartPtrs P, int grid, int block, cudaStream_t s)
@@ -914,11 +988,120 @@ int launch_sort(int fp32, long long np, int M, double tau, PartPtrs src, PartPtr
 // ---------------------------------------------------------------------------
 // Dynamic shared-memory opt-in (per kernel instantiation) and occupancy.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Batched ensemble sweeps: persistent blocks claim work items (run, marker range)
+// until the queue built by the plan kernel is empty.  Item boundaries are
+// multiples of the tile size, so every bulk copy stays 16-byte aligned.  After a
+// bounded wait gave up (the run's status records it) the block stops claiming.
+// ---------------------------------------------------------------------------
+template <typename Args>
+__device__ __forceinline__ bool ens_claim(EnsQueue *Q, const Args *runs, int nruns, int &run,
+                                          long long &beg, long long &end)
+{
+    __shared__ int s_item;
+    __syncthreads();                       // s_item of the previous claim is consumed
+    if (threadIdx.x == 0) s_item = atomicAdd(&Q->next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= Q->nitems) return false;
+    // the run r with item_start[r] <= item < item_start[r + 1]
+    int lo = 0, hi = nruns;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (Q->item_start[mid] <= item) lo = mid; else hi = mid;
+    }
+    run = lo;
+    const long long im = Q->item_markers;
+    beg = (long long)(item - Q->item_start[run]) * im;
+    end = beg + im < runs[run].np ? beg + im : runs[run].np;
+    return true;
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1)
+    k_sweep1_ens(const Sweep1Args *runs, int nruns, EnsQueue *Q)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    if ((int)blockIdx.x >= Q->nblocks) return;
+    tile_bars_init(*reinterpret_cast<TileBars *>(smem));
+    unsigned long long q = 0;
+    int run;
+    long long beg, end;
+    while (ens_claim(Q, runs, nruns, run, beg, end))
+        if (!sweep1_range<K, R>(runs[run], beg, end, smem, q)) break;
+}
+
+template <int K, typename R>
+__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1)
+    k_sweep2_ens(const Sweep2Args *runs, int nruns, EnsQueue *Q)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    if ((int)blockIdx.x >= Q->nblocks) return;
+    tile_bars_init(*reinterpret_cast<TileBars *>(smem));
+    unsigned long long q = 0;
+    int run;
+    long long beg, end;
+    while (ens_claim(Q, runs, nruns, run, beg, end))
+        if (!sweep2_range<K, R>(runs[run], beg, end, smem, q)) break;
+}
+
+template <typename R>
+static int launch_sweep_ens_t(int which, int K, const void *runs, int nruns, EnsQueue *Q, int grid,
+                              size_t smem, cudaStream_t s)
+{
+    const int b = kSweepThreads;
+#define ENS(KK)                                                                                          \
+    case KK:                                                                                             \
+        if (which == 1) k_sweep1_ens<KK, R><<<grid, b, smem, s>>>((const Sweep1Args *)runs, nruns, Q);   \
+        else k_sweep2_ens<KK, R><<<grid, b, smem, s>>>((const Sweep2Args *)runs, nruns, Q);              \
+        break;
+    switch (K) {
+    ENS(2) ENS(3) ENS(4) ENS(5)
+    default: return 1;
+    }
+#undef ENS
+    return 0;
+}
+
+int launch_sweep1_ens(int K, int fp32, const Sweep1Args *runs, int nruns, EnsQueue *Q, int grid,
+                      size_t smem, cudaStream_t s)
+{
+    return fp32 ? launch_sweep_ens_t<float>(1, K, runs, nruns, Q, grid, smem, s)
+                : launch_sweep_ens_t<double>(1, K, runs, nruns, Q, grid, smem, s);
+}
+
+int launch_sweep2_ens(int K, int fp32, const Sweep2Args *runs, int nruns, EnsQueue *Q, int grid,
+                      size_t smem, cudaStream_t s)
+{
+    return fp32 ? launch_sweep_ens_t<float>(2, K, runs, nruns, Q, grid, smem, s)
+                : launch_sweep_ens_t<double>(2, K, runs, nruns, Q, grid, smem, s);
+}
+
+// End of subsystem I for every run (block row = run); runs stopped by an error
+// keep their markers.
+template <typename R>
+__global__ void __launch_bounds__(256) k_finalize1_ens(const RunDesc *runs)
+{
+    const RunDesc &D = runs[blockIdx.y];
+    if (D.ctrl->status & (STATUS_NUMERIC | STATUS_TIMEOUT)) return;
+    finalize1_range<R>(D.np, D.M, D.P, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                       (long long)gridDim.x * blockDim.x);
+}
+
+int launch_finalize1_ens(int fp32, const RunDesc *R, int nruns, int grid_x, cudaStream_t s)
+{
+    if (fp32) k_finalize1_ens<float><<<dim3(grid_x, nruns), 256, 0, s>>>(R);
+    else k_finalize1_ens<double><<<dim3(grid_x, nruns), 256, 0, s>>>(R);
+    return 0;
+}
+
 template <int K, typename R>
 static int set_attrs_kr(size_t s1, size_t s2, size_t s3)
 {
     if (cudaFuncSetAttribute(k_sweep1<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) return 1;
     if (cudaFuncSetAttribute(k_sweep2<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) return 1;
+    if (cudaFuncSetAttribute(k_sweep1_ens<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) return 1;
+    if (cudaFuncSetAttribute(k_sweep2_ens<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) return 1;
     if (cudaFuncSetAttribute(k_current<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3)) return 1;
     if (cudaFuncSetAttribute(k_charge<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3)) return 1;
     return 0;
@@ -947,7 +1130,17 @@ int sweep_blocks_per_sm(int K, int fp32, int which, int block, size_t smem)
 
 }  // namespace pic
 
+// Raises the dynamic shared-memory limits of the marker kernels to at least
+// (s1, s2, s3) bytes; never lowers them, so handles of different grid sizes can
+// coexist in one process.
 int pic_set_smem_attrs(size_t s1, size_t s2, size_t s3)
 {
-    return pic::set_attrs_r<float>(s1, s2, s3) | pic::set_attrs_r<double>(s1, s2, s3);
+    static std::mutex mu;
+    static size_t m1 = 0, m2 = 0, m3 = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    const size_t n1 = std::max(m1, s1), n2 = std::max(m2, s2), n3 = std::max(m3, s3);
+    if (n1 == m1 && n2 == m2 && n3 == m3) return 0;
+    const int rc = pic::set_attrs_r<float>(n1, n2, n3) | pic::set_attrs_r<double>(n1, n2, n3);
+    if (rc == 0) { m1 = n1; m2 = n2; m3 = n3; }
+    return rc;
 }

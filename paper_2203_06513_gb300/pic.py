@@ -152,6 +152,14 @@ class Pic:
         if rc != PIC_OK:
             raise PicError(rc, L.pic_last_error(None).decode())
         self._h = h
+        self._owned = True
+
+    @classmethod
+    def _borrow(cls, lib, handle, cfg: Config) -> "Pic":
+        """A view of a handle owned elsewhere (a run of an Ensemble)."""
+        obj = cls.__new__(cls)
+        obj._lib, obj._h, obj.cfg, obj._owned = lib, handle, cfg, False
+        return obj
 
     # ------------------------------------------------------------------
     def _check(self, rc: int):
@@ -163,7 +171,8 @@ class Pic:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.pic_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self._lib.pic_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -230,6 +239,92 @@ class Pic:
 
 def version() -> str:
     return load().pic_version().decode()
+
+
+class Ensemble:
+    """Independent runs advanced together (see pic_ensemble_* in include/pic.h).
+    cfgs: list of Config; inputs: list of (x, p, ay, az, ey, ez) float64 numpy
+    arrays (ey, ez may be None)."""
+
+    def __init__(self, cfgs, inputs, use_graph: bool = True, stream=None):
+        L = load()
+        self._lib = L
+        vp = ctypes.c_void_p
+        L.pic_ensemble_create.argtypes = [ctypes.POINTER(pic_config), ctypes.POINTER(pic_arrays), ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+        L.pic_ensemble_step.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int32)]
+        L.pic_ensemble_tune.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]
+        L.pic_ensemble_set_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+        L.pic_ensemble_run.argtypes = [vp, ctypes.c_int32]
+        L.pic_ensemble_run.restype = vp
+        L.pic_ensemble_launches.argtypes = [vp]
+        L.pic_ensemble_launches.restype = ctypes.c_int64
+        L.pic_ensemble_destroy.argtypes = [vp]
+        L.pic_ensemble_last_error.argtypes = [vp]
+        L.pic_ensemble_last_error.restype = ctypes.c_char_p
+        n = len(cfgs)
+        assert len(inputs) == n
+        self.cfgs = list(cfgs)
+        self.nruns = n
+        carr = (pic_config * n)(*[c.c() for c in cfgs])
+        self._keep = [tuple(np.ascontiguousarray(a, dtype=np.float64) if a is not None else None for a in inp)
+                      for inp in inputs]
+        aarr = (pic_arrays * n)(*[pic_arrays(_ptr(x), _ptr(p), _dp(), _ptr(ey), _ptr(ez), _ptr(ay), _ptr(az))
+                                  for (x, p, ay, az, ey, ez) in self._keep])
+        h = vp()
+        s = vp(0 if stream is None else int(stream))
+        rc = L.pic_ensemble_create(carr, aarr, n, PIC_MEM_HOST, 1 if use_graph else 0, s, ctypes.byref(h))
+        if rc != PIC_OK:
+            raise PicError(rc, L.pic_last_error(None).decode())
+        self._h = h
+        self._keep = None
+
+    def _check(self, rc: int):
+        if rc != PIC_OK:
+            msg = self._lib.pic_ensemble_last_error(self._h).decode()
+            if rc == PIC_ERR_NOCONVERGE:
+                raise NoConvergence(rc, msg)
+            raise PicError(rc, msg)
+
+    def step(self, nsteps: int = 1, check: bool = True):
+        """Returns (sweeps[nruns, 2], status[nruns]); raises on a run's error if check."""
+        sw = np.zeros((self.nruns, 2), dtype=np.int64)
+        st = np.zeros(self.nruns, dtype=np.int32)
+        rc = self._lib.pic_ensemble_step(self._h, nsteps, sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if check:
+            self._check(rc)
+        return sw, st
+
+    def tune(self, cache_path: str | None = None):
+        ch = (ctypes.c_int32 * 3)()
+        self._check(self._lib.pic_ensemble_tune(self._h, None if cache_path is None else cache_path.encode(), ch))
+        return int(ch[0]), int(ch[1]), bool(ch[2])
+
+    def set_schedule(self, item_markers: int, blocks_per_sm: int):
+        self._check(self._lib.pic_ensemble_set_schedule(self._h, item_markers, blocks_per_sm))
+
+    def run(self, r: int) -> Pic:
+        h = self._lib.pic_ensemble_run(self._h, r)
+        if not h:
+            raise IndexError(r)
+        return Pic._borrow(self._lib, ctypes.c_void_p(h), self.cfgs[r])
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.pic_ensemble_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pic_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 N_MLP_PARAMS = 8898

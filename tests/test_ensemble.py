@@ -1,0 +1,187 @@
+"""Batched ensembles (pic_ensemble_*): many independent runs in one graph launch
+per step.  Each run must reproduce what the method gives for it alone: the FP64
+oracle, and the single-run handle on the same inputs; runs converge (or fail)
+independently; the schedule (item size, blocks per SM) and the loop driver
+(device-ended graph loops or host-driven loops) do not change the results.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2203_06513_gb300 import inputs as I
+from paper_2203_06513_gb300 import pic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def pdist(a, b, L):
+    d = np.mod(a - b + 0.5 * L, L) - 0.5 * L
+    return np.abs(d)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def members(n, base_np=3000, nxs=(32, 64, 16, 128), k=3, **kw):
+    """Runs of uneven sizes: grid sizes cycle through nxs, marker counts are
+    ragged (not multiples of the 1024-marker tile)."""
+    out = []
+    for r in range(n):
+        out.append(I.Workload(f"m{r}", nx=nxs[r % len(nxs)], degree=k, np=base_np + 1237 * r + 17,
+                              seed=50 + r, pump=0.05 + 0.07 * (r % 4), vth=0.05 + 0.03 * (r % 3), **kw))
+    return out
+
+
+def inputs_of(ws):
+    ins = []
+    for w in ws:
+        x, p = I.particles(w)
+        ay, az, ey, ez = I.fields(w)
+        ins.append((x, p, ay, az, ey, ez))
+    return ins
+
+
+def compare(st_a, st_b, L, tol):
+    assert np.max(pdist(st_a["x"], st_b["x"], L)) / L <= tol
+    assert rel(st_a["p"], st_b["p"]) <= tol
+    for k in ("ex", "ey", "ez", "ay", "az"):
+        if np.max(np.abs(st_b[k])) > 0:
+            assert rel(st_a[k], st_b[k]) <= tol, k
+
+
+def test_ensemble_fp64_against_oracle():
+    """Three runs of different grids and sizes, 3 steps, against the oracle of
+    each run: the single-run bar (1e-10 relative in state and fields)."""
+    ws = members(3, base_np=1500, nxs=(32, 16, 64))
+    ins = inputs_of(ws)
+    cfgs = [pic.Config.from_workload(w) for w in ws]
+    ens = pic.Ensemble(cfgs, ins)
+    steps = 3
+    sw, st = ens.step(steps)
+    assert np.all(st == 0)
+    for r, w in enumerate(ws):
+        orc = O.Oracle(w.L, w.nx, w.degree, w.weight, w.dt, w.tol, w.max_iter)
+        x, p, ay, az, ey, ez = ins[r]
+        s = O.initial_state(orc, x, p, ay, az, ey, ez)
+        for _ in range(steps):
+            s = orc.step(s)
+        got = ens.run(r).state_numpy()
+        ref = {"x": s.x, "p": s.p, "ex": s.ex, "ey": s.ey, "ez": s.ez, "ay": s.ay, "az": s.az}
+        compare(got, ref, w.L, 1e-10)
+        E = ens.run(r).energy()
+        assert E["gauss"] < 1e-13
+    assert np.all(sw >= steps)
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", [pic.PIC_FP64, pic.PIC_FP32])
+def test_ensemble_matches_single_runs(precision):
+    """Every run of a 6-run ensemble equals the same run stepped alone, sweep
+    counts included (FP64 to rounding order; FP32 to a few float ulps)."""
+    ws = members(6, base_np=2000)
+    ins = inputs_of(ws)
+    cfgs = [pic.Config.from_workload(w, precision=precision, warm_start=pic.PIC_WARM_EXPLICIT, sort_every=2)
+            for w in ws]
+    ens = pic.Ensemble(cfgs, ins)
+    steps = 4
+    sw, st = ens.step(steps)
+    assert np.all(st == 0)
+    tol = 1e-12 if precision == pic.PIC_FP64 else 1e-5
+    for r, w in enumerate(ws):
+        x, p, ay, az, ey, ez = ins[r]
+        g = pic.Pic(cfgs[r], x, p, ay, az, ey, ez)
+        i1, i2 = g.step(steps)
+        compare(ens.run(r).state_numpy(), g.state_numpy(), w.L, tol)
+        # a decision right at the tolerance may flip with the order of atomics
+        assert abs(sw[r, 0] - i1) <= 1 and abs(sw[r, 1] - i2) <= 1
+        g.close()
+    ens.close()
+
+
+def test_graph_and_host_loop_agree():
+    ws = members(5, base_np=2500)
+    ins = inputs_of(ws)
+    cfgs = [pic.Config.from_workload(w, precision=pic.PIC_FP64) for w in ws]
+    a = pic.Ensemble(cfgs, ins, use_graph=True)
+    b = pic.Ensemble(cfgs, ins, use_graph=False)
+    swa, _ = a.step(3)
+    swb, _ = b.step(3)
+    assert np.max(np.abs(swa - swb)) <= 1
+    for r, w in enumerate(ws):
+        compare(a.run(r).state_numpy(), b.run(r).state_numpy(), w.L, 1e-12)
+    a.close()
+    b.close()
+
+
+def test_schedule_does_not_change_results():
+    ws = members(4, base_np=5000)
+    ins = inputs_of(ws)
+    cfgs = [pic.Config.from_workload(w, precision=pic.PIC_FP64) for w in ws]
+    a = pic.Ensemble(cfgs, ins)
+    b = pic.Ensemble(cfgs, ins)
+    a.set_schedule(1024, 1)
+    b.set_schedule(262144, 1)
+    swa, _ = a.step(2)
+    swb, _ = b.step(2)
+    assert np.max(np.abs(swa - swb)) <= 1
+    for r, w in enumerate(ws):
+        compare(a.run(r).state_numpy(), b.run(r).state_numpy(), w.L, 1e-12)
+    with pytest.raises(pic.PicError):
+        a.set_schedule(1000, 1)
+    a.close()
+    b.close()
+
+
+def test_runs_converge_and_fail_independently():
+    """One run with a one-sweep budget and an unreachable tolerance stops with
+    no-convergence; the others go on and still match their single runs."""
+    ws = members(4, base_np=2000)
+    ins = inputs_of(ws)
+    cfgs = [pic.Config.from_workload(w, precision=pic.PIC_FP64) for w in ws]
+    cfgs[2] = pic.Config.from_workload(ws[2], precision=pic.PIC_FP64, max_iter=1, tol=1e-30)
+    ens = pic.Ensemble(cfgs, ins)
+    sw, st = ens.step(2, check=False)
+    assert st[2] == pic.PIC_ERR_NOCONVERGE
+    assert all(st[r] == 0 for r in (0, 1, 3))
+    assert sw[2, 0] == 2 and sw[2, 1] == 2          # one sweep per loop, every step
+    with pytest.raises(pic.NoConvergence):
+        ens.step(1)
+    for r in (0, 1, 3):
+        x, p, ay, az, ey, ez = ins[r]
+        g = pic.Pic(cfgs[r], x, p, ay, az, ey, ez)
+        g.step(3)
+        compare(ens.run(r).state_numpy(), g.state_numpy(), ws[r].L, 1e-12)
+        g.close()
+    ens.close()
+
+
+def test_tuner_and_cache(tmp_path):
+    ws = members(4, base_np=20000, nxs=(64, 128))
+    ins = inputs_of(ws)
+    cfgs = [pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=pic.PIC_WARM_EXPLICIT) for w in ws]
+    cache = os.path.join(str(tmp_path), "tune.txt")
+    a = pic.Ensemble(cfgs, ins)
+    im, bps, cached = a.tune(cache)
+    assert not cached and im % 1024 == 0 and bps >= 1
+    b = pic.Ensemble(cfgs, ins)
+    im2, bps2, cached2 = b.tune(cache)
+    assert cached2 and (im2, bps2) == (im, bps)
+    # tuning steps are real steps: energy stays conserved
+    for r in range(len(ws)):
+        E = a.run(r).energy()
+        assert np.isfinite(E["total"])
+    a.close()
+    b.close()
+
+
+def test_mixed_degrees_are_rejected():
+    ws = members(2, base_np=500)
+    ins = inputs_of(ws)
+    cfgs = [pic.Config.from_workload(ws[0]), pic.Config.from_workload(I.Workload("d", nx=32, degree=2, np=500))]
+    with pytest.raises(pic.PicError):
+        pic.Ensemble(cfgs, ins)
