@@ -208,7 +208,7 @@ static int upload_schedule(pic_ensemble *e)
 static int loop_body(pic_ensemble *e, int which, cudaStream_t s, unsigned long long cond)
 {
     const int grid = e->num_sms * e->bps_max;
-    ELAUNCH(launch_ens_plan(e->d_q, e->d_er, e->nruns, s), "ensemble plan");
+    ELAUNCH(launch_ens_plan(e->d_q, e->d_er, e->nruns, cond, s), "ensemble plan");
     if (which == 1) {
         ELAUNCH(launch_sweep1_ens(e->K, e->fp32, e->d_a1, e->nruns, e->d_q, grid, e->smem1, s), "ensemble sweep I");
         ELAUNCH(launch_conv_ens(e->d_c1, e->nruns, e->Mmax, 1, e->ntap1, e->d_q, e->d_sweeps, cond, s),

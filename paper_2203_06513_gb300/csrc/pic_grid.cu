@@ -484,7 +484,8 @@ int launch_copy_ens(const RunDesc *R, int nruns, int Mmax, int which, cudaStream
 // Work list of the next batched sweep: the runs still iterating (not converged,
 // not stopped by an error), each cut into items of item_markers markers;
 // item_start is the exclusive prefix sum of the items per run.
-__global__ void __launch_bounds__(1024) k_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns)
+__global__ void __launch_bounds__(1024) k_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns,
+                                                   unsigned long long cond)
 {
     __shared__ int s_scan[1024];
     __shared__ int s_nact[32];
@@ -520,6 +521,9 @@ __global__ void __launch_bounds__(1024) k_ens_plan(EnsQueue *Q, const EnsRun *ru
         Q->n_decided = 0;
         Q->n_continue = 0;
         Q->go = 0;
+        // no run left (every run stopped by an error): no solve will decide, so the
+        // loop is ended here
+        if (n == 0 && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0u);
     }
 }
 
@@ -535,10 +539,10 @@ int launch_ens_status(const EnsRun *runs, int nruns, int *status, cudaStream_t s
     return 0;
 }
 
-int launch_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns, cudaStream_t s)
+int launch_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns, unsigned long long cond, cudaStream_t s)
 {
     if (nruns < 1 || nruns > kEnsMaxRuns) return 1;
-    k_ens_plan<<<1, 1024, 0, s>>>(Q, runs, nruns);
+    k_ens_plan<<<1, 1024, 0, s>>>(Q, runs, nruns, cond);
     return 0;
 }
 

@@ -156,7 +156,7 @@ struct RunDesc {
     DevCtrl *ctrl;
 };
 
-int launch_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns, cudaStream_t s);
+int launch_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns, unsigned long long cond, cudaStream_t s);
 int launch_ens_status(const EnsRun *runs, int nruns, int *status, cudaStream_t s);
 int conv_ens_optin(int Mmax, int ntap_max);
 int launch_conv_ens(const ConvArgs *runs, int nruns, int Mmax, int ncomp, int ntap_max, EnsQueue *Q,
