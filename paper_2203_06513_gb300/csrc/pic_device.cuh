@@ -78,6 +78,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
+// one arrival (release semantics: this thread's earlier shared-memory reads are
+// ordered before the barrier's phase completes)
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
 {
     for (unsigned long long i = 0; i < kMaxWaitTries; ++i) {

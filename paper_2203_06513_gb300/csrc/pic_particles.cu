@@ -102,44 +102,85 @@ __device__ __forceinline__ void block_chunk(long long np, long long &beg, long l
     end = beg + chunk < np ? beg + chunk : np;
 }
 
-// Markers stream through shared memory in tiles of kTile (a block's range is cut
-// into tiles; the block's q-th tile overall goes to stage q % 2).  One thread
-// issues the bulk copies of a tile's arrays (cp.async.bulk, completed on the
-// stage's mbarrier) two tiles ahead of the consumers, so the DRAM latency of the
-// next tile overlaps the arithmetic on the current one.  The marker arrays are
-// allocated with padding, so a tile's byte count may be rounded up to a multiple
-// of 16.  A block may process several ranges (batched runs); the tile sequence
-// number q runs on across them, so the stage parities stay consistent.
-constexpr int kTileU = 2;                      // markers per thread per tile
+// Markers stream through shared memory in tiles of kTile, kStages tiles in flight.
+// The block's q-th tile overall goes to stage q % kStages.  Each stage has a
+// "full" mbarrier (completed by the bulk copies of its arrays, cp.async.bulk)
+// and an "empty" mbarrier (one arrival per warp once the warp has read it).
+// Warps do not synchronise with each other per tile: a warp waits only for its
+// next tile to land, and thread 0 refills a stage once every warp has released
+// it.  A block may process several ranges (batched runs); q runs on across
+// them, so the barrier phases stay consistent.  Every wait is bounded; a wait
+// that gives up sets the block's abort flag, after which no warp consumes or
+// issues more tiles, and the copies still in flight are waited for (bounded)
+// before the block leaves.  The marker arrays are allocated with padding, so a
+// tile's byte count may be rounded up to a multiple of 16.
+constexpr int kTileU = 1;                      // markers per thread per tile
 constexpr int kTile = kSweepThreads * kTileU;  // markers per tile
+constexpr int kStages = 4;
+constexpr int kSweepWarps = kSweepThreads / 32;
 
 struct TileBars {
-    unsigned long long full[2];
+    unsigned long long full[kStages];
+    unsigned long long empty[kStages];
+    int abort;
+    unsigned long long issued;      // tiles issued by this block so far (thread 0)
 };
+static_assert(sizeof(TileBars) <= 128, "tile barriers live in the first 128 bytes");
 
 __device__ __forceinline__ void tile_bars_init(TileBars &B)
 {
     if (threadIdx.x == 0) {
-        mbar_init(&B.full[0], 1);
-        mbar_init(&B.full[1], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&B.full[s], 1);
+            mbar_init(&B.empty[s], kSweepWarps);
+        }
+        B.abort = 0;
+        B.issued = 0;
         fence_mbar_init();
     }
     __syncthreads();
 }
 
-// Returns false (block-uniform) when a bounded wait gave up; the caller then
-// drains the copies it has in flight (bounded) and leaves.
-__device__ __forceinline__ bool tile_wait(TileBars &B, unsigned long long q)
+__device__ __forceinline__ bool tile_aborted(const TileBars &B)
 {
-    const bool ok = mbar_wait(&B.full[q & 1], (unsigned)((q >> 1) & 1));
-    return !__syncthreads_or(!ok);
+    return __shfl_sync(0xffffffffu, *reinterpret_cast<const volatile int *>(&B.abort), 0) != 0;
 }
 
-// waits (bounded) for the tiles q .. qend-1 still in flight, at most two
-__device__ __forceinline__ void tile_drain(TileBars &B, unsigned long long q, unsigned long long qend)
+// Warp: wait (bounded) for tile q; false (warp-uniform) after a timeout or an abort.
+__device__ __forceinline__ bool tile_acquire(TileBars &B, unsigned long long q)
 {
-    for (unsigned long long k = q; k < qend && k < q + 2; ++k)
-        mbar_wait(&B.full[k & 1], (unsigned)((k >> 1) & 1));
+    if (tile_aborted(B)) return false;
+    const bool ok = mbar_wait(&B.full[q % kStages], (unsigned)((q / kStages) & 1));
+    if (__all_sync(0xffffffffu, ok)) return true;
+    if ((threadIdx.x & 31) == 0) atomicExch(&B.abort, 1);
+    return false;
+}
+
+// Warp: done reading tile q.
+__device__ __forceinline__ void tile_release(TileBars &B, unsigned long long q)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&B.empty[q % kStages]);
+}
+
+// Thread 0: may tile q be written into its stage?  Waits (bounded) until every
+// warp released the stage's previous tile q - kStages.
+__device__ __forceinline__ bool tile_stage_free(TileBars &B, unsigned long long q)
+{
+    if (q < (unsigned long long)kStages) return true;
+    if (mbar_wait(&B.empty[q % kStages], (unsigned)(((q / kStages) - 1) & 1))) return true;
+    atomicExch(&B.abort, 1);
+    return false;
+}
+
+// Thread 0, after the block's warps left the range: wait (bounded) for the bulk
+// copies of the last tiles issued, so none is in flight when shared memory is reused
+// or the block exits.
+__device__ __forceinline__ void tile_drain(TileBars &B)
+{
+    const unsigned long long n = B.issued;
+    for (unsigned long long q = n > (unsigned long long)kStages ? n - kStages : 0; q < n; ++q)
+        mbar_wait(&B.full[q % kStages], (unsigned)((q / kStages) & 1));
 }
 
 // ---------------------------------------------------------------------------
@@ -162,15 +203,14 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     const int W = A.M + 2 * H;
     TileBars &Bars = *reinterpret_cast<TileBars *>(smem);
     unsigned char *st = smem + 128;
-    int32_t *s_cell[2];
-    R *s_t[2], *s_p[2], *s_d[2];
-    for (int b = 0; b < 2; ++b) {
-        s_cell[b] = reinterpret_cast<int32_t *>(st);
-        s_t[b] = reinterpret_cast<R *>(st + kTile * sizeof(int32_t));
-        s_p[b] = s_t[b] + kTile;
-        s_d[b] = s_p[b] + kTile;
-        st += kTile * (sizeof(int32_t) + 3 * sizeof(R));
-    }
+    // stage b: cell[kTile], t[kTile], p[kTile], delta[kTile]
+    unsigned char *const stage0 = st;
+    constexpr size_t kStageBytes = kTile * (sizeof(int32_t) + 3 * sizeof(R));
+    auto s_cell = [&](int b) { return reinterpret_cast<int32_t *>(stage0 + b * kStageBytes); };
+    auto s_t = [&](int b) { return reinterpret_cast<R *>(stage0 + b * kStageBytes + kTile * sizeof(int32_t)); };
+    auto s_p = [&](int b) { return s_t(b) + kTile; };
+    auto s_d = [&](int b) { return s_t(b) + 2 * kTile; };
+    st += kStages * kStageBytes;
     double *s_acc = reinterpret_cast<double *>(st);
     double *s_red = s_acc + W;
     FieldTile<R> F = carve_tile<R>(reinterpret_cast<unsigned char *>(s_red + 32), W);
@@ -185,24 +225,24 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
         warm = warm && it == 0;
     }
     const bool need_delta = !warm;
-    auto issue = [&](long long i) {            // one thread: copies of tile i into stage (q0 + i) % 2
+    auto issue = [&](long long i) {            // thread 0: copies of tile i into stage (q0 + i) % kStages
+        if (*reinterpret_cast<volatile int *>(&Bars.abort) || !tile_stage_free(Bars, q0 + i)) return;
         const long long s0 = beg + i * kTile;
         long long n = end - s0 < kTile ? end - s0 : kTile;
         n = (n + 3) & ~3LL;
-        const int b = (int)((q0 + i) & 1);
+        const int b = (int)((q0 + i) % kStages);
         const unsigned bi = (unsigned)(n * sizeof(int32_t)), br = (unsigned)(n * sizeof(R));
         fence_proxy_async();
         mbar_expect_tx(&Bars.full[b], bi + 2 * br + (need_delta ? br : 0u));
-        bulk_g2s(s_cell[b], A.P.cell + s0, bi, &Bars.full[b]);
-        bulk_g2s(s_t[b], static_cast<const R *>(A.P.t) + s0, br, &Bars.full[b]);
-        bulk_g2s(s_p[b], static_cast<const R *>(A.P.p) + s0, br, &Bars.full[b]);
-        if (need_delta) bulk_g2s(s_d[b], static_cast<const R *>(A.P.delta) + s0, br, &Bars.full[b]);
+        bulk_g2s(s_cell(b), A.P.cell + s0, bi, &Bars.full[b]);
+        bulk_g2s(s_t(b), static_cast<const R *>(A.P.t) + s0, br, &Bars.full[b]);
+        bulk_g2s(s_p(b), static_cast<const R *>(A.P.p) + s0, br, &Bars.full[b]);
+        if (need_delta) bulk_g2s(s_d(b), static_cast<const R *>(A.P.delta) + s0, br, &Bars.full[b]);
+        Bars.issued = q0 + i + 1;
     };
     __syncthreads();                           // shared memory of a previous range is free
-    if (threadIdx.x == 0) {
-        if (ntile > 0) issue(0);
-        if (ntile > 1) issue(1);
-    }
+    if (threadIdx.x == 0)
+        for (long long i = 0; i < ntile && i < kStages; ++i) issue(i);
 
     // scaled arithmetic (see piece_means_scaled): the basis is K! N^K, the path
     // means are S1 = S_{K-1} times the means of N^{K-1}; so the staged fields are
@@ -232,26 +272,22 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     const R dlim = (R)A.Dlim;
     const R one = R(1);
     R dmax = R(0);
-    bool bad = false, timeout = false;
+    bool bad = false;
     // window: pieces in cells wb-3 .. wb+3, V1 nodes wb-K-2 .. wb+3
     DepWindow<R, K + 6, K, K + 2, -3, 3> win;
     win.clear();
     int wb = INT_MIN;
 
     for (long long i = 0; i < ntile; ++i) {
-        if (!tile_wait(Bars, q0 + i)) {
-            timeout = true;
-            tile_drain(Bars, q0 + i, qend);
-            break;
-        }
-        const int b = (int)((q0 + i) & 1);
+        if (!tile_acquire(Bars, q0 + i)) break;
+        const int b = (int)((q0 + i) % kStages);
         const long long s0 = beg + i * kTile;
 #pragma unroll 1
         for (int u = 0; u < kTileU; ++u) {
             const int jl = u * kSweepThreads + threadIdx.x;
             const long long a = s0 + jl;
             const bool act = a < end;
-            const int c0 = act ? s_cell[b][jl] : 0;
+            const int c0 = act ? s_cell(b)[jl] : 0;
             const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
             if (lead == INT_MAX) break;                    // whole warp past the chunk end
             if (lead != wb) {
@@ -260,8 +296,8 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             }
             const unsigned amask = __ballot_sync(0xffffffffu, act);
             if (!act) continue;
-            const R t0 = s_t[b][jl];
-            const R pn = s_p[b][jl];
+            const R t0 = s_t(b)[jl];
+            const R pn = s_p(b)[jl];
             R v[K + 1];
             bspline_scaled<K, R>(t0, v);
             R A0y = R(0), A0z = R(0);
@@ -273,7 +309,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
                 A0z += z * v[r];
             }
             const R g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
-            R dold = warm ? fdiv_(tau * pn, g0) : s_d[b][jl];
+            R dold = warm ? fdiv_(tau * pn, g0) : s_d(b)[jl];
             if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
 
             const R s = t0 + dold;
@@ -334,12 +370,17 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             dp[a] = dnew;
             pnp[a] = pnew;
         }
-        __syncthreads();                          // stage b fully consumed
-        if (threadIdx.x == 0 && i + 2 < ntile) issue(i + 2);
+        tile_release(Bars, q0 + i);
+        if (threadIdx.x == 0 && i + kStages < ntile) issue(i + kStages);
     }
     if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
     if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
-    if (timeout && threadIdx.x == 0) atomicOr(&A.ctrl->status, STATUS_TIMEOUT);
+    __syncthreads();
+    const bool timeout = *reinterpret_cast<volatile int *>(&Bars.abort) != 0;
+    if (timeout && threadIdx.x == 0) {
+        atomicOr(&A.ctrl->status, STATUS_TIMEOUT);
+        tile_drain(Bars);
+    }
     block_max_to(&A.ctrl->dmax_bits, (double)dmax, s_red);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const double val = s_acc[i];
@@ -363,7 +404,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
 size_t sweep1_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
-    const size_t stages = 2 * (size_t)kTile * (sizeof(int32_t) + 3 * (fp32 ? sizeof(float) : sizeof(double)));
+    const size_t stages = (size_t)kStages * kTile * (sizeof(int32_t) + 3 * (fp32 ? sizeof(float) : sizeof(double)));
     return 128 + stages + (W + 32) * sizeof(double) +
            (fp32 ? FieldTile<float>::bytes(W) : FieldTile<double>::bytes(W));
 }
@@ -456,14 +497,13 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     const int W = A.M + 2 * H;
     TileBars &Bars = *reinterpret_cast<TileBars *>(smem);
     unsigned char *st = smem + 128;
-    int32_t *s_cell[2];
-    R *s_t[2], *s_p[2];
-    for (int b = 0; b < 2; ++b) {
-        s_cell[b] = reinterpret_cast<int32_t *>(st);
-        s_t[b] = reinterpret_cast<R *>(st + kTile * sizeof(int32_t));
-        s_p[b] = s_t[b] + kTile;
-        st += kTile * (sizeof(int32_t) + 2 * sizeof(R));
-    }
+    // stage b: cell[kTile], t[kTile], p[kTile]
+    unsigned char *const stage0 = st;
+    constexpr size_t kStageBytes = kTile * (sizeof(int32_t) + 2 * sizeof(R));
+    auto s_cell = [&](int b) { return reinterpret_cast<int32_t *>(stage0 + b * kStageBytes); };
+    auto s_t = [&](int b) { return reinterpret_cast<R *>(stage0 + b * kStageBytes + kTile * sizeof(int32_t)); };
+    auto s_p = [&](int b) { return s_t(b) + kTile; };
+    st += kStages * kStageBytes;
     double *s_sy = reinterpret_cast<double *>(st);
     double *s_sz = s_sy + W;
     using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
@@ -474,23 +514,23 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
 
     const long long ntile = end > beg ? (end - beg + kTile - 1) / kTile : 0;
     const unsigned long long q0 = q, qend = q + (unsigned long long)ntile;
-    auto issue = [&](long long i) {
+    auto issue = [&](long long i) {            // thread 0: copies of tile i into stage (q0 + i) % kStages
+        if (*reinterpret_cast<volatile int *>(&Bars.abort) || !tile_stage_free(Bars, q0 + i)) return;
         const long long s0 = beg + i * kTile;
         long long n = end - s0 < kTile ? end - s0 : kTile;
         n = (n + 3) & ~3LL;
-        const int b = (int)((q0 + i) & 1);
+        const int b = (int)((q0 + i) % kStages);
         const unsigned bi = (unsigned)(n * sizeof(int32_t)), br = (unsigned)(n * sizeof(R));
         fence_proxy_async();
         mbar_expect_tx(&Bars.full[b], bi + 2 * br);
-        bulk_g2s(s_cell[b], A.P.cell + s0, bi, &Bars.full[b]);
-        bulk_g2s(s_t[b], static_cast<const R *>(A.P.t) + s0, br, &Bars.full[b]);
-        bulk_g2s(s_p[b], static_cast<const R *>(A.P.p) + s0, br, &Bars.full[b]);
+        bulk_g2s(s_cell(b), A.P.cell + s0, bi, &Bars.full[b]);
+        bulk_g2s(s_t(b), static_cast<const R *>(A.P.t) + s0, br, &Bars.full[b]);
+        bulk_g2s(s_p(b), static_cast<const R *>(A.P.p) + s0, br, &Bars.full[b]);
+        Bars.issued = q0 + i + 1;
     };
     __syncthreads();                           // shared memory of a previous range is free
-    if (threadIdx.x == 0) {
-        if (ntile > 0) issue(0);
-        if (ntile > 1) issue(1);
-    }
+    if (threadIdx.x == 0)
+        for (long long i = 0; i < ntile && i < kStages; ++i) issue(i);
     // scaled basis K! N^K: coefficients staged as a / K!, deposits flushed times w / K!
     const double inv_fact = 1.0 / (double)Fact<K>::v;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -517,26 +557,21 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     __syncthreads();
     const double w = A.w * inv_fact;
     const R one = R(1);
-    bool timeout = false;
     // window: marker cells wb .. wb+3 (wb = the warp's lowest), V0 nodes wb-K .. wb+3
     DepWindow<R, K + 4, K + 1, K, 0, 3> wy, wz;
     wy.clear();
     wz.clear();
     int wb = INT_MIN;
     for (long long i = 0; i < ntile; ++i) {
-        if (!tile_wait(Bars, q0 + i)) {
-            timeout = true;
-            tile_drain(Bars, q0 + i, qend);
-            break;
-        }
-        const int b = (int)((q0 + i) & 1);
+        if (!tile_acquire(Bars, q0 + i)) break;
+        const int b = (int)((q0 + i) % kStages);
         const long long s0 = beg + i * kTile;
 #pragma unroll 1
         for (int u = 0; u < kTileU; ++u) {
             const int jl = u * kSweepThreads + threadIdx.x;
             const long long a = s0 + jl;
             const bool act = a < end;
-            const int c = act ? s_cell[b][jl] : 0;
+            const int c = act ? s_cell(b)[jl] : 0;
             const int lead = __reduce_min_sync(0xffffffffu, act ? c : INT_MAX);
             if (lead == INT_MAX) break;
             if (lead != wb) {
@@ -547,8 +582,8 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
                 wb = lead;
             }
             if (!act) continue;
-            const R t = s_t[b][jl];
-            const R p = s_p[b][jl];
+            const R t = s_t(b)[jl];
+            const R p = s_p(b)[jl];
             R v[K + 1];
             bspline_scaled<K, R>(t, v);
             R A0y = R(0), A0z = R(0), A1y = R(0), A1z = R(0);
@@ -601,14 +636,19 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
                 for (int r = 0; r <= K; ++r) atomicAdd(&s_sz[c - r + H], w * (double)vz[r]);
             }
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && i + 2 < ntile) issue(i + 2);
+        tile_release(Bars, q0 + i);
+        if (threadIdx.x == 0 && i + kStages < ntile) issue(i + kStages);
     }
     if (wb != INT_MIN) {
         wy.flush(s_sy, wb - K + H, w);
         wz.flush(s_sz, wb - K + H, w);
     }
-    if (timeout && threadIdx.x == 0) atomicOr(A.status, STATUS_TIMEOUT);
+    __syncthreads();
+    const bool timeout = *reinterpret_cast<volatile int *>(&Bars.abort) != 0;
+    if (timeout && threadIdx.x == 0) {
+        atomicOr(A.status, STATUS_TIMEOUT);
+        tile_drain(Bars);
+    }
     double *syo = A.s_y, *szo = A.s_z;
     if (A.graph) {                          // replayed by a graph: buffers by sweep parity
         const int it = *reinterpret_cast<volatile const int *>(&A.ctrl->iter);
@@ -640,7 +680,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
 size_t sweep2_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
-    const size_t stages = 2 * (size_t)kTile * (sizeof(int32_t) + 2 * (fp32 ? sizeof(float) : sizeof(double)));
+    const size_t stages = (size_t)kStages * kTile * (sizeof(int32_t) + 2 * (fp32 ? sizeof(float) : sizeof(double)));
     return 128 + stages + 2 * W * sizeof(double) + (fp32 ? 3 * W * sizeof(float2) : 2 * W * sizeof(double2));
 }
 
