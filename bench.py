@@ -185,13 +185,14 @@ def ensemble_inputs(n_runs: int, np_scale: float, seed: int):
     return ws_, ins
 
 
-def ensemble_run(pic, torch, ws_, ins, steps, warmup, stream):
+def ensemble_run(pic, torch, ws_, ins, steps, warmup, stream, use_graph=True):
     """All runs in one ensemble (FP32 form, explicit predictor), schedule picked
-    by the autotuner; device-timed steps, each one graph launch."""
+    by the autotuner; device-timed steps, each one graph launch (or, with
+    use_graph=False, the same kernels with the loops driven from the host)."""
     cfgs = [pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=pic.PIC_WARM_EXPLICIT, sort_every=2)
             for w in ws_]
     t0 = time.perf_counter()
-    ens = pic.Ensemble(cfgs, ins, stream=stream.cuda_stream)
+    ens = pic.Ensemble(cfgs, ins, use_graph=use_graph, stream=stream.cuda_stream)
     t_create = time.perf_counter() - t0
     H0 = [ens.run(r).energy()["total"] for r in range(len(ws_))]
     cache = os.path.join(ROOT, "paper_2203_06513_gb300", "_build", "ensemble_tune.txt")
@@ -218,7 +219,7 @@ def ensemble_run(pic, torch, ws_, ins, steps, warmup, stream):
             "sweeps_per_step_mean": {"I": float(sw[:, 0].mean() / steps), "II": float(sw[:, 1].mean() / steps)},
             "sweeps_per_step_max": {"I": float(sw[:, 0].max() / steps), "II": float(sw[:, 1].max() / steps)},
             "max_rel_energy_err": err, "failed_runs": int((st != 0).sum()),
-            "gpu_launches": int(launches), "create_s": t_create,
+            "gpu_launches": int(launches), "create_s": t_create, "graph": bool(use_graph),
             "workload": "C4: %d runs, nx in {256,512,1024,2048}, Np log-uniform [1e5,4e6], pump U[0.01,0.3], "
                         "vth U[0.02,0.15], k=3, dt=0.05, FP32 form" % len(ws_)}
 
@@ -274,6 +275,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ensemble-runs", type=int, default=256, help="0: skip the batched-ensemble line")
     ap.add_argument("--ensemble-scale", type=float, default=1.0, help="scale of the runs' marker counts")
+    ap.add_argument("--ensemble-host-loop", action="store_true",
+                    help="drive the ensemble's loops from the host (same kernels, no graph; for profiling)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -334,7 +337,8 @@ def main():
     ens = None
     if ens_in is not None:
         del arrays, x, p
-        ens = ensemble_run(pic, torch, ens_in[0], ens_in[1], max(1, min(args.steps, 10)), 1, stream)
+        ens = ensemble_run(pic, torch, ens_in[0], ens_in[1], max(1, min(args.steps, 10)), 1, stream,
+                           use_graph=not args.ensemble_host_loop)
         ens_in = None
         barrier()
 
