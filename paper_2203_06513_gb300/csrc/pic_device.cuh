@@ -6,6 +6,8 @@
 // Lambda^0_j = N^k_j, Lambda^1_j = N^{k-1}_j, supp N^d_j = [x_j, x_{j+d+1})).
 #pragma once
 
+#include <climits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -320,6 +322,21 @@ struct DepWindow {
         if (lane < NS && mine != R(0)) atomicAdd(&s_row[row0 + lane], scale * (double)mine);
     }
 };
+
+// Cell of a marker as its warp's deposit window sees it.  Markers are sorted by
+// cell, but between sorts a marker that crossed the periodic boundary carries
+// cell 0, 1, .. among neighbours at cell M-1 (or the reverse): the warp's lowest
+// cell is then 0, and every marker at the top end would miss the window and take
+// the slow shared-atomic path.  In a warp that holds cells in the upper half of
+// the grid, cells below U are shifted by +M.  Shared arrays staged with a periodic
+// halo of H cells hold cell c at index c + H for -H <= c < M + H, so a kernel whose
+// accesses reach at most `reach` cells above a marker's cell passes
+// U = H - reach: every index stays below M + 2H.  All lanes must call.
+__device__ __forceinline__ int warp_unwrap_cell(int c, bool act, int M, int U)
+{
+    const int hi = __reduce_max_sync(0xffffffffu, act ? c : INT_MIN);
+    return (act && hi >= M / 2 && c < U) ? c + M : c;
+}
 
 // ---------------------------------------------------------------------------
 // Scaled B-spline arithmetic for the sweep kernels.  A rounded reciprocal such

@@ -287,7 +287,8 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             const int jl = u * kSweepThreads + threadIdx.x;
             const long long a = s0 + jl;
             const bool act = a < end;
-            const int c0 = act ? s_cell(b)[jl] : 0;
+            // reach above the cell: the path (Dlim cells)
+            const int c0 = warp_unwrap_cell(act ? s_cell(b)[jl] : 0, act, A.M, H - A.Dlim);
             const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
             if (lead == INT_MAX) break;                    // whole warp past the chunk end
             if (lead != wb) {
@@ -571,7 +572,7 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
             const int jl = u * kSweepThreads + threadIdx.x;
             const long long a = s0 + jl;
             const bool act = a < end;
-            const int c = act ? s_cell(b)[jl] : 0;
+            const int c = warp_unwrap_cell(act ? s_cell(b)[jl] : 0, act, A.M, H);   // no reach above
             const int lead = __reduce_min_sync(0xffffffffu, act ? c : INT_MAX);
             if (lead == INT_MAX) break;
             if (lead != wb) {
@@ -716,14 +717,33 @@ __global__ void __launch_bounds__(256) k_charge(DiagArgs A)
     for (int i = threadIdx.x; i < W; i += blockDim.x) s_acc[i] = 0.0;
     __syncthreads();
     const R *tp = static_cast<const R *>(A.P.t);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
-        const int c = A.P.cell[a];
+    // contiguous chunk per block, so a warp's sorted markers share cells: the warp
+    // accumulates in a register window (cells wb .. wb+3) and flushes it with
+    // shuffles when its lowest cell moves on
+    long long beg, end;
+    block_chunk(A.np, beg, end);
+    DepWindow<double, K + 4, K + 1, K, 0, 3> win;
+    win.clear();
+    int wb = INT_MIN;
+    for (long long a0 = beg; a0 < end; a0 += blockDim.x) {
+        const long long a = a0 + threadIdx.x;
+        const bool act = a < end;
+        const int c = warp_unwrap_cell(act ? A.P.cell[a] : 0, act, A.M, H);   // no reach above
+        const int lead = __reduce_min_sync(0xffffffffu, act ? c : INT_MAX);
+        if (lead == INT_MAX) break;                    // whole warp past the chunk end
+        if (lead != wb) {
+            if (wb != INT_MIN) win.flush(s_acc, wb - K + H, A.w);
+            wb = lead;
+        }
+        if (!act) continue;
         double v[K + 1];
         bspline_vals<K, double>((double)tp[a], v);
+        if (!win.put(c - wb, v)) {
 #pragma unroll
-        for (int r = 0; r <= K; ++r) atomicAdd(&s_acc[c - r + H], A.w * v[r]);
+            for (int r = 0; r <= K; ++r) atomicAdd(&s_acc[c - r + H], A.w * v[r]);
+        }
     }
+    if (wb != INT_MIN) win.flush(s_acc, wb - K + H, A.w);
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const double v = s_acc[i];
