@@ -44,18 +44,52 @@ METRIC = "particle-steps/s at rel. energy err ≤1e-10: FP32+learned vs plain FP
 UNIT = "particle-steps/s"
 WORKLOAD = "C2"
 WEIGHTS = os.path.join(ROOT, "paper_2203_06513_gb300", "data", "warm_mlp.npz")
-# algorithmic bytes per marker per subsystem-I sweep: read cell, offset, p, delta;
-# write delta, p_new (float form 6 x 4 B; double form 4 + 5 x 8 B)
+# Roofline units of the hot kernels (float form, one marker):
+#   k_sweep1: read cell, offset, p, delta; write delta, p_new: 6 x 4 B = 24 B
+#   k_sweep2: read cell, offset, p: 12 B
+#   k_warm_mlp: 2 x (6x64 + 64x64 + 64x64 + 64x2) = 17,408 flop (bf16 tensor cores)
 BYTES_SWEEP1 = {1: 24, 0: 44}
+BYTES_SWEEP2 = 12
+FLOP_MLP = 2 * (6 * 64 + 64 * 64 + 64 * 64 + 64 * 2)
+# DRAM bytes (read + write) per marker from ncu captures of the current kernels on
+# 2e7 markers of the C2 grid (--set full, one launch each); per launch = x N_p.
+NCU_DRAM_PER_MARKER = {"k_sweep1<3,float>": 22.34, "k_sweep2<3,float>": 12.21, "k_warm_mlp<3,float>": None}
 
 
 def peaks():
+    """(HBM GB/s, bf16 TFLOP/s sustained, kind): measured on this machine, else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 1700.0, "fallback"
+
+
+def kernel_rooflines(tr, np_, hbm, tflops, kind):
+    """Per hot kernel of the timed form: achieved against its roof, from the library's
+    CUDA-event timing of each launch."""
+    out = []
+    for name, ms, n, unit_amount, bound in (
+            ("k_sweep1<3,float>", tr["sweep1_ms"], tr["sweep1_launches"], BYTES_SWEEP1[1], "hbm"),
+            ("k_sweep2<3,float>", tr["sweep2_ms"], tr["sweep2_launches"], BYTES_SWEEP2, "hbm"),
+            ("k_warm_mlp<3,float>", tr["warm_ms"], tr["warm_launches"], FLOP_MLP, "tensor")):
+        if n <= 0:
+            continue
+        launch_ms = ms / n
+        if bound == "hbm":
+            achieved = unit_amount * np_ / (launch_ms / 1e3) / 1e9
+            peak, unit = hbm, "GB/s"
+        else:
+            achieved = unit_amount * np_ / (launch_ms / 1e3) / 1e12
+            peak, unit = tflops, "TFLOP/s"
+        per_marker = NCU_DRAM_PER_MARKER.get(name)
+        out.append({"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "peak_kind": kind,
+                    "traffic": None if per_marker is None else per_marker * np_,
+                    "algorithmic_per_launch": unit_amount * np_, "launch_ms": launch_ms,
+                    "launches": n, "share_ms": ms})
+    return out
 
 
 class ClockSampler:
@@ -351,9 +385,9 @@ def main():
     v_expl = total_np * args.steps / (ms_expl / 1e3)
     v64 = total_np * k64 / (ms64 / 1e3)
     tr = r_head["timing"]
-    hbm, peak_kind = peaks()
-    launch_ms = tr["sweep1_ms"] / max(1, tr["sweep1_launches"])
-    achieved = BYTES_SWEEP1[1] * w.np / (launch_ms / 1e3) / 1e9
+    hbm, tflops, peak_kind = peaks()
+    kernels = kernel_rooflines(tr, w.np, hbm, tflops, peak_kind)
+    dominant = max(kernels, key=lambda k: k["share_ms"])
     if rank == 0:
         cpu = None
         if not args.no_cpu:
@@ -384,10 +418,10 @@ def main():
                      "rel_energy_err": r64["rel_energy_err"], "gauss_residual": r64["gauss"],
                      "sweeps_per_step": sweeps(r64, k64),
                      "speedup_fp32_learned_over_fp64": value / v64},
-            "roofline": {"kernel": "k_sweep1<3,float>", "bound": "hbm", "achieved": achieved,
-                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                         "traffic": None, "bytes_per_marker": BYTES_SWEEP1[1], "launch_ms": launch_ms},
-            "kernel_ms": {"sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"], "solve": tr["solve_ms"]},
+            "roofline": dominant,
+            "kernels": kernels,
+            "kernel_ms": {"sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"], "solve": tr["solve_ms"],
+                          "warm_start": tr["warm_ms"]},
             "gpu_launches": tr["launches"],
             "clocks": clk,
             "cpu_baseline": cpu,

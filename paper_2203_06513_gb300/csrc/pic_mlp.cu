@@ -14,9 +14,10 @@
 // b2, W3, b3, W4 (2x64), b4 -- 8898 numbers.
 //
 // Inference runs on the tensor cores: bf16 operands, fp32 accumulation, with
-// mma.sync m16n8k16 (a warp computes 16 markers per tile; the fp32 accumulator
-// fragment of one layer is re-packed in registers as the bf16 A fragment of the
-// next).  Training (forward + backward + Adam) runs in fp32 on the CUDA cores.
+// mma.sync m16n8k16 (a warp computes 32 markers as two 16-row tiles that share
+// every weight fragment; the fp32 accumulator fragment of one layer passes
+// through the GELU in packed bf16 and becomes the bf16 A fragment of the next, in
+// registers).  Training (forward + backward + Adam) runs in fp32 on the CUDA cores.
 #include <cuda_bf16.h>
 
 #include <climits>
@@ -49,14 +50,6 @@ struct MlpTC {
     float norm[kNorm];
 };
 
-__device__ __forceinline__ float gelu_fast(float z)
-{
-    float t;
-    const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-    return 0.5f * z * (1.f + t);
-}
-
 __device__ __forceinline__ float gelu_exact(float z)
 {
     return 0.5f * z * (1.f + tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z)));
@@ -76,6 +69,36 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     uint32_t u;
     memcpy(&u, &v, 4);
     return u;
+}
+
+// GELU (tanh form) of two pre-activations, evaluated in packed bf16 arithmetic on
+// their bf16 roundings and returned packed: the result is a bf16 activation of
+// the next layer either way, and one tanh.approx.bf16x2 serves both values.
+__device__ __forceinline__ uint32_t gelu_bf16x2(float z0, float z1)
+{
+    const __nv_bfloat162 z = __floats2bfloat162_rn(z0, z1);
+    const __nv_bfloat162 c0 = __float2bfloat162_rn(0.7978845608028654f);
+    const __nv_bfloat162 c1 = __float2bfloat162_rn(0.7978845608028654f * 0.044715f);
+    const __nv_bfloat162 half = __float2bfloat162_rn(0.5f);
+    const __nv_bfloat162 u = __hmul2(z, __hfma2(__hmul2(z, z), c1, c0));   // c0 z + c1 z^3
+    uint32_t ui, ti;
+    memcpy(&ui, &u, 4);
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(ti) : "r"(ui));
+    __nv_bfloat162 th;
+    memcpy(&th, &ti, 4);
+    const __nv_bfloat162 out = __hmul2(z, __hfma2(th, half, half));         // z (1 + tanh u) / 2
+    uint32_t o;
+    memcpy(&o, &out, 4);
+    return o;
+}
+
+// four 8x8 bf16 matrices from shared memory; lane l supplies the row address of
+// matrix l / 8, row l % 8
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
@@ -112,74 +135,106 @@ __device__ void stage_tc(MlpTC &S, const float *params, const float *norm)
     if (threadIdx.x < kNorm) S.norm[threadIdx.x] = norm[threadIdx.x];
 }
 
-// One hidden layer: D (16 x 64, 8 n-tiles) = act(A (16 x 16*KT) W^T + b), then
-// re-packed as the bf16 A fragments of the next layer (4 k-tiles).
+// One hidden layer for the warp's two 16-row tiles: D (16 x 64 each) =
+// act(A (16 x 16*KT) W^T + b), re-packed as the bf16 A fragments of the next
+// layer (4 k-tiles).  W is [n][k] row-major in shared memory; each ldmatrix.x4
+// brings the B fragments of two n-tiles at one k-tile, used by both row tiles.
 template <int KT>
-__device__ __forceinline__ void hidden_layer(const uint32_t (&a)[KT][4], const __nv_bfloat16 *W, int stride,
-                                             const float *b, uint32_t (&out)[4][4])
+__device__ __forceinline__ void hidden_layer2(const uint32_t (&a)[2][KT][4], const __nv_bfloat16 *W, int stride,
+                                              const float *b, uint32_t (&out)[2][4][4])
 {
-    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    float d[8][4];
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    const int mi = lane >> 3, rr = lane & 7;
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float b0 = b[8 * nt + 2 * q], b1 = b[8 * nt + 2 * q + 1];
-        d[nt][0] = b0; d[nt][1] = b1; d[nt][2] = b0; d[nt][3] = b1;
+    for (int np2 = 0; np2 < 4; ++np2) {           // n-tiles 2 np2, 2 np2 + 1
+        float d[2][2][4];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float b0 = b[16 * np2 + 8 * s + 2 * q], b1 = b[16 * np2 + 8 * s + 2 * q + 1];
+#pragma unroll
+            for (int tile = 0; tile < 2; ++tile) {
+                d[tile][s][0] = b0; d[tile][s][1] = b1; d[tile][s][2] = b0; d[tile][s][3] = b1;
+            }
+        }
 #pragma unroll
         for (int kt = 0; kt < KT; ++kt) {
-            const __nv_bfloat16 *row = W + (8 * nt + g) * stride + 16 * kt + 2 * q;
-            const uint32_t b_lo = *reinterpret_cast<const uint32_t *>(row);
-            const uint32_t b_hi = *reinterpret_cast<const uint32_t *>(row + 8);
-            mma_bf16(d[nt], a[kt], b_lo, b_hi);
-        }
-    }
+            uint32_t bf[4];
+            // matrices: (n-tile 2np2, k lo), (2np2, k hi), (2np2+1, k lo), (2np2+1, k hi)
+            ldsm_x4(bf, W + (16 * np2 + 8 * (mi >> 1) + rr) * stride + 16 * kt + 8 * (mi & 1));
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-        out[kt][0] = pack_bf16(gelu_fast(d[2 * kt][0]), gelu_fast(d[2 * kt][1]));
-        out[kt][1] = pack_bf16(gelu_fast(d[2 * kt][2]), gelu_fast(d[2 * kt][3]));
-        out[kt][2] = pack_bf16(gelu_fast(d[2 * kt + 1][0]), gelu_fast(d[2 * kt + 1][1]));
-        out[kt][3] = pack_bf16(gelu_fast(d[2 * kt + 1][2]), gelu_fast(d[2 * kt + 1][3]));
+            for (int tile = 0; tile < 2; ++tile) {
+                mma_bf16(d[tile][0], a[tile][kt], bf[0], bf[1]);
+                mma_bf16(d[tile][1], a[tile][kt], bf[2], bf[3]);
+            }
+        }
+#pragma unroll
+        for (int tile = 0; tile < 2; ++tile) {
+            out[tile][np2][0] = gelu_bf16x2(d[tile][0][0], d[tile][0][1]);
+            out[tile][np2][1] = gelu_bf16x2(d[tile][0][2], d[tile][0][3]);
+            out[tile][np2][2] = gelu_bf16x2(d[tile][1][0], d[tile][1][1]);
+            out[tile][np2][3] = gelu_bf16x2(d[tile][1][2], d[tile][1][3]);
+        }
     }
 }
 
-// 16 markers through the network.  X: 16 rows of 16 bf16 (normalised features,
-// zero padded) at row stride xs.  On return lanes with q == 0 hold the outputs
-// of rows g (y[0], y[1]) and g + 8 (y[2], y[3]).
-__device__ __forceinline__ void mlp_tile16(const MlpTC &S, const __nv_bfloat16 *X, int xs, float (&y)[4])
+// 32 markers (two 16-row tiles) through the network.  X: 32 rows of 16 bf16
+// (normalised features, zero padded) at row stride xs.  On return lanes with
+// q == 0 hold, for tile t, the outputs of rows g (y[t][0..1]) and g + 8 (y[t][2..3]).
+__device__ __forceinline__ void mlp_tile32(const MlpTC &S, const __nv_bfloat16 *X, int xs, float (&y)[2][4])
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    uint32_t a0[1][4];
-    a0[0][0] = *reinterpret_cast<const uint32_t *>(X + g * xs + 2 * q);
-    a0[0][1] = *reinterpret_cast<const uint32_t *>(X + (g + 8) * xs + 2 * q);
-    a0[0][2] = *reinterpret_cast<const uint32_t *>(X + g * xs + 2 * q + 8);
-    a0[0][3] = *reinterpret_cast<const uint32_t *>(X + (g + 8) * xs + 2 * q + 8);
-    uint32_t h1[4][4], h2[4][4], h3[4][4];
-    hidden_layer<1>(a0, S.W1, kS1, S.b1, h1);
-    hidden_layer<4>(h1, S.W2, kS, S.b2, h2);
-    hidden_layer<4>(h2, S.W3, kS, S.b3, h3);
-    float d[4];
-    d[0] = S.b4[2 * q]; d[1] = S.b4[2 * q + 1]; d[2] = d[0]; d[3] = d[1];
+    uint32_t a0[2][1][4];
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-        const __nv_bfloat16 *row = S.W4 + g * kS + 16 * kt + 2 * q;
-        mma_bf16(d, h3[kt], *reinterpret_cast<const uint32_t *>(row), *reinterpret_cast<const uint32_t *>(row + 8));
+    for (int tile = 0; tile < 2; ++tile) {
+        const __nv_bfloat16 *Xt = X + tile * 16 * xs;
+        a0[tile][0][0] = *reinterpret_cast<const uint32_t *>(Xt + g * xs + 2 * q);
+        a0[tile][0][1] = *reinterpret_cast<const uint32_t *>(Xt + (g + 8) * xs + 2 * q);
+        a0[tile][0][2] = *reinterpret_cast<const uint32_t *>(Xt + g * xs + 2 * q + 8);
+        a0[tile][0][3] = *reinterpret_cast<const uint32_t *>(Xt + (g + 8) * xs + 2 * q + 8);
     }
-    y[0] = d[0]; y[1] = d[1]; y[2] = d[2]; y[3] = d[3];
+    uint32_t h1[2][4][4], h2[2][4][4];
+    hidden_layer2<1>(a0, S.W1, kS1, S.b1, h1);
+    hidden_layer2<4>(h1, S.W2, kS, S.b2, h2);
+    hidden_layer2<4>(h2, S.W3, kS, S.b3, h1);
+#pragma unroll
+    for (int tile = 0; tile < 2; ++tile) {
+        float d[4];
+        d[0] = S.b4[2 * q]; d[1] = S.b4[2 * q + 1]; d[2] = d[0]; d[3] = d[1];
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const __nv_bfloat16 *row = S.W4 + g * kS + 16 * kt + 2 * q;
+            mma_bf16(d, h1[tile][kt], *reinterpret_cast<const uint32_t *>(row),
+                     *reinterpret_cast<const uint32_t *>(row + 8));
+        }
+        y[tile][0] = d[0]; y[tile][1] = d[1]; y[tile][2] = d[2]; y[tile][3] = d[3];
+    }
 }
 
 // Per-warp staging of 32 markers' features and outputs.
-constexpr int kXS = 24;   // bf16 row stride of the feature tile (16 used)
+constexpr int kXS = 24;   // bf16 row stride of the feature tile (16 used, 16-byte aligned rows)
 struct WarpTile {
     __nv_bfloat16 X[32 * kXS];
     float Y[32][2];
 };
 
-// Features of one marker into row r of the warp tile, normalised.
+// Zero the padding columns of the warp tile once; rows then take only their
+// six features.
+__device__ __forceinline__ void clear_tile(WarpTile &T)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t *w = reinterpret_cast<uint32_t *>(T.X);
+    for (int i = lane; i < 32 * kXS / 2; i += 32) w[i] = 0u;
+    __syncwarp();
+}
+
+// Features of one marker into row r of the warp tile, normalised (columns 0..5).
 __device__ __forceinline__ void put_features(WarpTile &T, const float *norm, int r, const float f[kIn])
 {
-    __nv_bfloat16 *row = T.X + r * kXS;
+    uint32_t *row = reinterpret_cast<uint32_t *>(T.X + r * kXS);
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-        row[i] = __float2bfloat16(i < kIn ? (f[i] - norm[i]) * norm[kIn + i] : 0.f);
+    for (int i = 0; i < kIn / 2; ++i)
+        row[i] = pack_bf16((f[2 * i] - norm[2 * i]) * norm[kIn + 2 * i],
+                           (f[2 * i + 1] - norm[2 * i + 1]) * norm[kIn + 2 * i + 1]);
 }
 
 // Run the warp's 32 rows (two 16-row tiles) and leave the scaled outputs in T.Y.
@@ -187,15 +242,15 @@ __device__ __forceinline__ void run_warp_tile(const MlpTC &S, WarpTile &T)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
     __syncwarp();
+    float y[2][4];
+    mlp_tile32(S, T.X, kXS, y);
+    if (q == 0) {
 #pragma unroll
-    for (int tile = 0; tile < 2; ++tile) {
-        float y[4];
-        mlp_tile16(S, T.X + tile * 16 * kXS, kXS, y);
-        if (q == 0) {
-            T.Y[tile * 16 + g][0] = y[0] * S.norm[2 * kIn];
-            T.Y[tile * 16 + g][1] = y[1] * S.norm[2 * kIn + 1];
-            T.Y[tile * 16 + g + 8][0] = y[2] * S.norm[2 * kIn];
-            T.Y[tile * 16 + g + 8][1] = y[3] * S.norm[2 * kIn + 1];
+        for (int tile = 0; tile < 2; ++tile) {
+            T.Y[tile * 16 + g][0] = y[tile][0] * S.norm[2 * kIn];
+            T.Y[tile * 16 + g][1] = y[tile][1] * S.norm[2 * kIn + 1];
+            T.Y[tile * 16 + g + 8][0] = y[tile][2] * S.norm[2 * kIn];
+            T.Y[tile * 16 + g + 8][1] = y[tile][3] * S.norm[2 * kIn + 1];
         }
     }
     __syncwarp();
@@ -204,7 +259,7 @@ __device__ __forceinline__ void run_warp_tile(const MlpTC &S, WarpTile &T)
 // ---------------------------------------------------------------------------
 // Standalone inference: X (B x 6 raw features, fp32) -> Y (B x 2 scaled outputs).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mlp_infer(const float *params, const float *norm, const float *X,
+__global__ void __launch_bounds__(256, 2) k_mlp_infer(const float *params, const float *norm, const float *X,
                                                    long long B, float *Y)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -213,6 +268,7 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float *params, const fl
     stage_tc(S, params, norm);
     __syncthreads();
     WarpTile &T = tiles[threadIdx.x >> 5];
+    clear_tile(T);
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < B; base += stride) {
@@ -235,7 +291,7 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float *params, const fl
 // with the features gathered at x^n from e_x^n and a^n (staged in shared memory).
 // ---------------------------------------------------------------------------
 template <int K, typename R>
-__global__ void __launch_bounds__(256) k_warm_mlp(WarmArgs A)
+__global__ void __launch_bounds__(256, 2) k_warm_mlp(WarmArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     MlpTC &S = *reinterpret_cast<MlpTC *>(smem);
@@ -254,6 +310,7 @@ __global__ void __launch_bounds__(256) k_warm_mlp(WarmArgs A)
     }
     __syncthreads();
     WarpTile &T = tiles[threadIdx.x >> 5];
+    clear_tile(T);
     const int lane = threadIdx.x & 31;
     const R *tp = static_cast<const R *>(A.P.t);
     const R *pp = static_cast<const R *>(A.P.p);
