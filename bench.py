@@ -329,7 +329,7 @@ def main():
     if args.np:
         kw["np"] = int(args.np)
     w = I.workload(WORKLOAD, **kw)
-    x, p = I.particles(w)
+    x, p = I.particles(w, workers=max(1, min(16, os.cpu_count() or 1)))
     ay, az, ey, ez = I.fields(w)
     arrays = (x, p, ay, az, ey, ez)
     stream = torch.cuda.Stream()

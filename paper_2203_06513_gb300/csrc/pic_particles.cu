@@ -49,23 +49,24 @@ template <> struct FieldTile<float> {
     }
     static size_t bytes(size_t W) { return W * (sizeof(float2) + sizeof(float4)); }
 };
+// Double form: the differences a_j - a_{j-1} are formed from the staged
+// coefficients when read (the same double values a staged copy would hold), which
+// keeps the tile within shared memory for M = 4096, k = 5.
 template <> struct FieldTile<double> {
     double2 *a;     // (a_y, a_z)
-    double2 *g;     // (a_y,j - a_y,j-1, a_z,j - a_z,j-1)
     double *e;      // ebar dx
     __device__ __forceinline__ void aa(int i, double &y, double &z) const { const double2 v = a[i]; y = v.x; z = v.y; }
     __device__ __forceinline__ void eg(int i, double &ev, double &gy, double &gz) const
     {
-        const double2 v = g[i];
-        ev = e[i]; gy = v.x; gz = v.y;
+        const double2 v = a[i], w = a[i - 1];
+        ev = e[i]; gy = v.x - w.x; gz = v.y - w.y;
     }
-    __device__ __forceinline__ void store(int i, double ay, double az, double ev, double gy, double gz)
+    __device__ __forceinline__ void store(int i, double ay, double az, double ev, double, double)
     {
         a[i] = make_double2(ay, az);
-        g[i] = make_double2(gy, gz);
         e[i] = ev;
     }
-    static size_t bytes(size_t W) { return W * (2 * sizeof(double2) + sizeof(double)); }
+    static size_t bytes(size_t W) { return W * (sizeof(double2) + sizeof(double)); }
 };
 
 template <typename R>
@@ -83,8 +84,7 @@ __device__ __forceinline__ FieldTile<double> carve_tile<double>(unsigned char *p
 {
     FieldTile<double> t;
     t.a = reinterpret_cast<double2 *>(p);
-    t.g = t.a + W;
-    t.e = reinterpret_cast<double *>(t.g + W);
+    t.e = reinterpret_cast<double *>(t.a + W);
     return t;
 }
 
@@ -102,8 +102,8 @@ __device__ __forceinline__ void block_chunk(long long np, long long &beg, long l
     end = beg + chunk < np ? beg + chunk : np;
 }
 
-// Markers stream through shared memory in tiles of kTile, kStages tiles in flight.
-// The block's q-th tile overall goes to stage q % kStages.  Each stage has a
+// Markers stream through shared memory in tiles of kTile, NS tiles in flight.
+// The block's q-th tile overall goes to stage q % NS.  Each stage has a
 // "full" mbarrier (completed by the bulk copies of its arrays, cp.async.bulk)
 // and an "empty" mbarrier (one arrival per warp once the warp has read it).
 // Warps do not synchronise with each other per tile: a warp waits only for its
@@ -116,12 +116,16 @@ __device__ __forceinline__ void block_chunk(long long np, long long &beg, long l
 // tile's byte count may be rounded up to a multiple of 16.
 constexpr int kTileU = 1;                      // markers per thread per tile
 constexpr int kTile = kSweepThreads * kTileU;  // markers per tile
-constexpr int kStages = 4;
+constexpr int kMaxStages = 4;
 constexpr int kSweepWarps = kSweepThreads / 32;
+// stages in flight: 4 in float, 2 in double (whose tiles are twice as large and
+// whose field staging needs the room at M = 4096)
+template <typename R> struct Stages { static constexpr int n = Real<R>::fp32 ? 4 : 2; };
+inline int stage_count(int fp32) { return fp32 ? 4 : 2; }
 
 struct TileBars {
-    unsigned long long full[kStages];
-    unsigned long long empty[kStages];
+    unsigned long long full[kMaxStages];
+    unsigned long long empty[kMaxStages];
     int abort;
     unsigned long long issued;      // tiles issued by this block so far (thread 0)
 };
@@ -130,7 +134,7 @@ static_assert(sizeof(TileBars) <= 128, "tile barriers live in the first 128 byte
 __device__ __forceinline__ void tile_bars_init(TileBars &B)
 {
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kMaxStages; ++s) {
             mbar_init(&B.full[s], 1);
             mbar_init(&B.empty[s], kSweepWarps);
         }
@@ -147,28 +151,31 @@ __device__ __forceinline__ bool tile_aborted(const TileBars &B)
 }
 
 // Warp: wait (bounded) for tile q; false (warp-uniform) after a timeout or an abort.
+template <int NS>
 __device__ __forceinline__ bool tile_acquire(TileBars &B, unsigned long long q)
 {
     if (tile_aborted(B)) return false;
-    const bool ok = mbar_wait(&B.full[q % kStages], (unsigned)((q / kStages) & 1));
+    const bool ok = mbar_wait(&B.full[q % NS], (unsigned)((q / NS) & 1));
     if (__all_sync(0xffffffffu, ok)) return true;
     if ((threadIdx.x & 31) == 0) atomicExch(&B.abort, 1);
     return false;
 }
 
 // Warp: done reading tile q.
+template <int NS>
 __device__ __forceinline__ void tile_release(TileBars &B, unsigned long long q)
 {
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&B.empty[q % kStages]);
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&B.empty[q % NS]);
 }
 
 // Thread 0: may tile q be written into its stage?  Waits (bounded) until every
-// warp released the stage's previous tile q - kStages.
+// warp released the stage's previous tile q - NS.
+template <int NS>
 __device__ __forceinline__ bool tile_stage_free(TileBars &B, unsigned long long q)
 {
-    if (q < (unsigned long long)kStages) return true;
-    if (mbar_wait(&B.empty[q % kStages], (unsigned)(((q / kStages) - 1) & 1))) return true;
+    if (q < (unsigned long long)NS) return true;
+    if (mbar_wait(&B.empty[q % NS], (unsigned)(((q / NS) - 1) & 1))) return true;
     atomicExch(&B.abort, 1);
     return false;
 }
@@ -176,11 +183,12 @@ __device__ __forceinline__ bool tile_stage_free(TileBars &B, unsigned long long 
 // Thread 0, after the block's warps left the range: wait (bounded) for the bulk
 // copies of the last tiles issued, so none is in flight when shared memory is reused
 // or the block exits.
+template <int NS>
 __device__ __forceinline__ void tile_drain(TileBars &B)
 {
     const unsigned long long n = B.issued;
-    for (unsigned long long q = n > (unsigned long long)kStages ? n - kStages : 0; q < n; ++q)
-        mbar_wait(&B.full[q % kStages], (unsigned)((q / kStages) & 1));
+    for (unsigned long long q = n > (unsigned long long)NS ? n - NS : 0; q < n; ++q)
+        mbar_wait(&B.full[q % NS], (unsigned)((q / NS) & 1));
 }
 
 // ---------------------------------------------------------------------------
@@ -199,6 +207,7 @@ template <int K, typename R>
 __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg, long long end,
                                              unsigned char *smem, unsigned long long &q)
 {
+    constexpr int NS = Stages<R>::n;
     const int H = A.H;
     const int W = A.M + 2 * H;
     TileBars &Bars = *reinterpret_cast<TileBars *>(smem);
@@ -210,7 +219,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     auto s_t = [&](int b) { return reinterpret_cast<R *>(stage0 + b * kStageBytes + kTile * sizeof(int32_t)); };
     auto s_p = [&](int b) { return s_t(b) + kTile; };
     auto s_d = [&](int b) { return s_t(b) + 2 * kTile; };
-    st += kStages * kStageBytes;
+    st += NS * kStageBytes;
     double *s_acc = reinterpret_cast<double *>(st);
     double *s_red = s_acc + W;
     FieldTile<R> F = carve_tile<R>(reinterpret_cast<unsigned char *>(s_red + 32), W);
@@ -225,12 +234,12 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
         warm = warm && it == 0;
     }
     const bool need_delta = !warm;
-    auto issue = [&](long long i) {            // thread 0: copies of tile i into stage (q0 + i) % kStages
-        if (*reinterpret_cast<volatile int *>(&Bars.abort) || !tile_stage_free(Bars, q0 + i)) return;
+    auto issue = [&](long long i) {            // thread 0: copies of tile i into stage (q0 + i) % NS
+        if (*reinterpret_cast<volatile int *>(&Bars.abort) || !tile_stage_free<NS>(Bars, q0 + i)) return;
         const long long s0 = beg + i * kTile;
         long long n = end - s0 < kTile ? end - s0 : kTile;
         n = (n + 3) & ~3LL;
-        const int b = (int)((q0 + i) % kStages);
+        const int b = (int)((q0 + i) % NS);
         const unsigned bi = (unsigned)(n * sizeof(int32_t)), br = (unsigned)(n * sizeof(R));
         fence_proxy_async();
         mbar_expect_tx(&Bars.full[b], bi + 2 * br + (need_delta ? br : 0u));
@@ -242,7 +251,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     };
     __syncthreads();                           // shared memory of a previous range is free
     if (threadIdx.x == 0)
-        for (long long i = 0; i < ntile && i < kStages; ++i) issue(i);
+        for (long long i = 0; i < ntile && i < NS; ++i) issue(i);
 
     // scaled arithmetic (see piece_means_scaled): the basis is K! N^K, the path
     // means are S1 = S_{K-1} times the means of N^{K-1}; so the staged fields are
@@ -279,8 +288,8 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     int wb = INT_MIN;
 
     for (long long i = 0; i < ntile; ++i) {
-        if (!tile_acquire(Bars, q0 + i)) break;
-        const int b = (int)((q0 + i) % kStages);
+        if (!tile_acquire<NS>(Bars, q0 + i)) break;
+        const int b = (int)((q0 + i) % NS);
         const long long s0 = beg + i * kTile;
 #pragma unroll 1
         for (int u = 0; u < kTileU; ++u) {
@@ -371,8 +380,8 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             dp[a] = dnew;
             pnp[a] = pnew;
         }
-        tile_release(Bars, q0 + i);
-        if (threadIdx.x == 0 && i + kStages < ntile) issue(i + kStages);
+        tile_release<NS>(Bars, q0 + i);
+        if (threadIdx.x == 0 && i + NS < ntile) issue(i + NS);
     }
     if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
     if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
@@ -380,7 +389,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     const bool timeout = *reinterpret_cast<volatile int *>(&Bars.abort) != 0;
     if (timeout && threadIdx.x == 0) {
         atomicOr(&A.ctrl->status, STATUS_TIMEOUT);
-        tile_drain(Bars);
+        tile_drain<NS>(Bars);
     }
     block_max_to(&A.ctrl->dmax_bits, (double)dmax, s_red);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -405,7 +414,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
 size_t sweep1_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
-    const size_t stages = (size_t)kStages * kTile * (sizeof(int32_t) + 3 * (fp32 ? sizeof(float) : sizeof(double)));
+    const size_t stages = (size_t)stage_count(fp32) * kTile * (sizeof(int32_t) + 3 * (fp32 ? sizeof(float) : sizeof(double)));
     return 128 + stages + (W + 32) * sizeof(double) +
            (fp32 ? FieldTile<float>::bytes(W) : FieldTile<double>::bytes(W));
 }
@@ -494,6 +503,7 @@ template <int K, typename R>
 __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg, long long end,
                                              unsigned char *smem, unsigned long long &q)
 {
+    constexpr int NS = Stages<R>::n;
     const int H = A.H;
     const int W = A.M + 2 * H;
     TileBars &Bars = *reinterpret_cast<TileBars *>(smem);
@@ -504,7 +514,7 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     auto s_cell = [&](int b) { return reinterpret_cast<int32_t *>(stage0 + b * kStageBytes); };
     auto s_t = [&](int b) { return reinterpret_cast<R *>(stage0 + b * kStageBytes + kTile * sizeof(int32_t)); };
     auto s_p = [&](int b) { return s_t(b) + kTile; };
-    st += kStages * kStageBytes;
+    st += NS * kStageBytes;
     double *s_sy = reinterpret_cast<double *>(st);
     double *s_sz = s_sy + W;
     using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
@@ -515,12 +525,12 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
 
     const long long ntile = end > beg ? (end - beg + kTile - 1) / kTile : 0;
     const unsigned long long q0 = q, qend = q + (unsigned long long)ntile;
-    auto issue = [&](long long i) {            // thread 0: copies of tile i into stage (q0 + i) % kStages
-        if (*reinterpret_cast<volatile int *>(&Bars.abort) || !tile_stage_free(Bars, q0 + i)) return;
+    auto issue = [&](long long i) {            // thread 0: copies of tile i into stage (q0 + i) % NS
+        if (*reinterpret_cast<volatile int *>(&Bars.abort) || !tile_stage_free<NS>(Bars, q0 + i)) return;
         const long long s0 = beg + i * kTile;
         long long n = end - s0 < kTile ? end - s0 : kTile;
         n = (n + 3) & ~3LL;
-        const int b = (int)((q0 + i) % kStages);
+        const int b = (int)((q0 + i) % NS);
         const unsigned bi = (unsigned)(n * sizeof(int32_t)), br = (unsigned)(n * sizeof(R));
         fence_proxy_async();
         mbar_expect_tx(&Bars.full[b], bi + 2 * br);
@@ -531,7 +541,7 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     };
     __syncthreads();                           // shared memory of a previous range is free
     if (threadIdx.x == 0)
-        for (long long i = 0; i < ntile && i < kStages; ++i) issue(i);
+        for (long long i = 0; i < ntile && i < NS; ++i) issue(i);
     // scaled basis K! N^K: coefficients staged as a / K!, deposits flushed times w / K!
     const double inv_fact = 1.0 / (double)Fact<K>::v;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -564,8 +574,8 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     wz.clear();
     int wb = INT_MIN;
     for (long long i = 0; i < ntile; ++i) {
-        if (!tile_acquire(Bars, q0 + i)) break;
-        const int b = (int)((q0 + i) % kStages);
+        if (!tile_acquire<NS>(Bars, q0 + i)) break;
+        const int b = (int)((q0 + i) % NS);
         const long long s0 = beg + i * kTile;
 #pragma unroll 1
         for (int u = 0; u < kTileU; ++u) {
@@ -637,8 +647,8 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
                 for (int r = 0; r <= K; ++r) atomicAdd(&s_sz[c - r + H], w * (double)vz[r]);
             }
         }
-        tile_release(Bars, q0 + i);
-        if (threadIdx.x == 0 && i + kStages < ntile) issue(i + kStages);
+        tile_release<NS>(Bars, q0 + i);
+        if (threadIdx.x == 0 && i + NS < ntile) issue(i + NS);
     }
     if (wb != INT_MIN) {
         wy.flush(s_sy, wb - K + H, w);
@@ -648,7 +658,7 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     const bool timeout = *reinterpret_cast<volatile int *>(&Bars.abort) != 0;
     if (timeout && threadIdx.x == 0) {
         atomicOr(A.status, STATUS_TIMEOUT);
-        tile_drain(Bars);
+        tile_drain<NS>(Bars);
     }
     double *syo = A.s_y, *szo = A.s_z;
     if (A.graph) {                          // replayed by a graph: buffers by sweep parity
@@ -681,7 +691,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
 size_t sweep2_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
-    const size_t stages = (size_t)kStages * kTile * (sizeof(int32_t) + 2 * (fp32 ? sizeof(float) : sizeof(double)));
+    const size_t stages = (size_t)stage_count(fp32) * kTile * (sizeof(int32_t) + 2 * (fp32 ? sizeof(float) : sizeof(double)));
     return 128 + stages + 2 * W * sizeof(double) + (fp32 ? 3 * W * sizeof(float2) : 2 * W * sizeof(double2));
 }
 

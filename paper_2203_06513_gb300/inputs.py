@@ -111,18 +111,40 @@ def _inverse_cdf(u: np.ndarray, L: float, eps: float, kappa: float) -> np.ndarra
     return x
 
 
-def particles(w: Workload, np_override: int | None = None, chunk: int = 1 << 24):
-    """(x, p) as float64 arrays, seeded by w.seed.  Generated in chunks so that
-    1e8-marker workloads stay within a few GB of host memory."""
+# markers per independently seeded chunk of the generator
+CHUNK = 1 << 22
+
+
+def _chunk(job):
+    seed, c, n, L, eps, kappa, vth = job
+    rng = np.random.default_rng(np.random.SeedSequence([seed, c]))
+    u = rng.random(n)
+    return _inverse_cdf(u, L, eps, kappa), rng.normal(0.0, vth, n)
+
+
+def particles(w: Workload, np_override: int | None = None, workers: int = 1):
+    """(x, p) as float64 arrays.  Chunk c (CHUNK markers) is drawn from its own
+    seed (w.seed, c), so the arrays do not depend on how many processes draw
+    them; workers > 1 uses a pool of spawned processes (safe after CUDA start)."""
     n = w.np if np_override is None else int(np_override)
-    rng = np.random.default_rng(w.seed)
     x = np.empty(n, dtype=np.float64)
     p = np.empty(n, dtype=np.float64)
-    for s in range(0, n, chunk):
-        e = min(n, s + chunk)
-        u = rng.random(e - s)
-        x[s:e] = _inverse_cdf(u, w.L, w.eps, w.kappa)
-        p[s:e] = rng.normal(0.0, w.vth, e - s)
+    starts = list(range(0, n, CHUNK))
+    jobs = [(w.seed, c, min(CHUNK, n - s), w.L, w.eps, w.kappa, w.vth) for c, s in enumerate(starts)]
+    if workers > 1 and len(jobs) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=min(workers, len(jobs)),
+                                    mp_context=mp.get_context("spawn")) as ex:
+            results = ex.map(_chunk, jobs)
+            for s, (xc, pc) in zip(starts, results):
+                x[s:s + xc.size] = xc
+                p[s:s + pc.size] = pc
+    else:
+        for s, job in zip(starts, jobs):
+            xc, pc = _chunk(job)
+            x[s:s + xc.size] = xc
+            p[s:s + pc.size] = pc
     return x, p
 
 
