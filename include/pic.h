@@ -80,7 +80,11 @@ typedef struct pic_handle pic_handle;
 
 typedef struct {
     double  L;           /* domain length (periodic [0, L))                        */
-    int32_t nx;          /* M: number of cells = dim V0 = dim V1, 8 <= M <= 8192    */
+    int32_t nx;          /* M: number of cells = dim V0 = dim V1, 8 <= M <= 8192;
+                            the sweeps stage the whole periodic grid in shared
+                            memory, so pic_init also rejects (PIC_ERR_INVALID)
+                            grids whose staging exceeds it: about M + 2(k + dt/dx)
+                            <= 4600 cells in the FP32 form, 4200 in FP64 (k = 5)  */
     int32_t degree;      /* k: degree of V0 (V1 has k-1), 2 <= k <= 5               */
     int64_t np;          /* N_p >= 1                                                */
     double  weight;      /* w: equal marker weight (L/N_p neutralises the background) */

@@ -428,8 +428,9 @@ static int substep1(pic_handle *h, int *iters)
         wa.P = cur_parts(h);
         wa.ex = h->ex; wa.ay = h->ay; wa.az = h->az;
         wa.params = mlp_params(h->mlp); wa.norm = mlp_norm(h->mlp);
+        wa.status = &h->ctrl->status;
         if ((rc = timed_begin(h))) return rc;
-        if (launch_warm_mlp(wa, h->num_sms * 2, h->stream))
+        if (launch_warm_mlp(wa, h->num_sms, h->stream))
             return fail(h, PIC_ERR_CUDA, "warm-start network: launch setup failed");
         CKL_N("launch_warm_mlp");
         if ((rc = timed_end(h, &h->t_warm, &h->n_warm))) return rc;

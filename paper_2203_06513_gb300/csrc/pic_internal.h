@@ -193,6 +193,7 @@ struct WarmArgs {
     PartPtrs P;
     const double *ex, *ay, *az;
     const float *params, *norm;
+    int *status;        // error bits (STATUS_TIMEOUT)
 };
 int launch_warm_mlp(const WarmArgs &a, int grid, cudaStream_t s);
 

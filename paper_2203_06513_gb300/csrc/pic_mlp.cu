@@ -13,11 +13,10 @@
 // Parameters: one float vector W1 (64x6, row-major [out][in]), b1, W2 (64x64),
 // b2, W3, b3, W4 (2x64), b4 -- 8898 numbers.
 //
-// Inference runs on the tensor cores: bf16 operands, fp32 accumulation, with
-// mma.sync m16n8k16 (a warp computes 32 markers as two 16-row tiles that share
-// every weight fragment; the fp32 accumulator fragment of one layer passes
-// through the GELU in packed bf16 and becomes the bf16 A fragment of the next, in
-// registers).  Training (forward + backward + Adam) runs in fp32 on the CUDA cores.
+// Inference runs on the 5th-generation tensor cores (tcgen05.mma, bf16 operands
+// in shared memory, fp32 accumulators in tensor memory), 128 markers per tile;
+// the GELU runs in packed bf16 on each thread's accumulator row.  Training
+// (forward + backward + Adam) runs in fp32 on the CUDA cores.
 #include <cuda_bf16.h>
 
 #include <climits>
@@ -37,18 +36,6 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
               kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kOut * kHid;
 static_assert(kOffB4 + kOut == kNParams, "parameter packing");
 constexpr int kNorm = 2 * kIn + kOut;     // shift[6], scale[6], out_scale[2]
-
-// shared-memory image of the network for the tensor-core path (bf16 rows padded
-// so that the 8 rows a B fragment touches fall in distinct banks)
-constexpr int kS1 = 24, kS = 72;
-struct MlpTC {
-    __nv_bfloat16 W1[kHid * kS1];
-    __nv_bfloat16 W2[kHid * kS];
-    __nv_bfloat16 W3[kHid * kS];
-    __nv_bfloat16 W4[8 * kS];
-    float b1[kHid], b2[kHid], b3[kHid], b4[8];
-    float norm[kNorm];
-};
 
 __device__ __forceinline__ float gelu_exact(float z)
 {
@@ -92,198 +79,313 @@ __device__ __forceinline__ uint32_t gelu_bf16x2(float z0, float z1)
     return o;
 }
 
-// four 8x8 bf16 matrices from shared memory; lane l supplies the row address of
-// matrix l / 8, row l % 8
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
+// ---------------------------------------------------------------------------
+// Tensor-core inference with tcgen05 (5th-generation tensor cores, accumulators
+// in tensor memory).  One block of 1024 threads per SM runs 8 independent chains,
+// one per warpgroup; a chain takes 128 markers at a time, one row per thread.  Per
+// layer the chain writes its rows' bf16 activations to shared memory in the
+// canonical K-major layout (8-row x 16-byte core matrices), one of its threads
+// issues the layer's tcgen05.mma instructions (M = 128, N = 64, K = 16 each) and
+// commits them to the chain's mbarrier, every thread of the chain waits (bounded),
+// loads its row of the fp32 accumulator from the chain's 64 tensor-memory columns
+// and applies the GELU.  While one chain waits for the tensor
+// cores, the other seven run their epilogues.  Weights are staged once per block,
+// in the same layout, and shared by the chains.
+// ---------------------------------------------------------------------------
+constexpr int kRows = 128;                       // markers per tile (UMMA M) = threads per chain
+constexpr int kChains = 8;                       // warpgroups per block
+constexpr int kMlpThreads = kRows * kChains;     // 1024
+constexpr int kTmemCols = 512;                   // chain g: columns 64 g .. 64 g + 63
+constexpr int kOutN = 16;                        // output layer padded to the smallest N for M = 128
+
+// byte offset of element (r, k) in a K-major no-swizzle operand with K columns:
+// core matrix (r/8, k/8) at (r/8) * (K/8) * 128 + (k/8) * 128, row r%8 at 16 (r%8)
+__host__ __device__ constexpr int kmaj_off(int r, int k, int K)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
+    return (r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Stage the network from fp32 parameters (global) into the shared image.
-__device__ void stage_tc(MlpTC &S, const float *params, const float *norm)
-{
-    for (int i = threadIdx.x; i < kHid * kS1; i += blockDim.x) {
-        const int n = i / kS1, k = i % kS1;
-        S.W1[i] = __float2bfloat16(k < kIn ? params[kOffW1 + n * kIn + k] : 0.f);
-    }
-    for (int i = threadIdx.x; i < kHid * kS; i += blockDim.x) {
-        const int n = i / kS, k = i % kS;
-        S.W2[i] = __float2bfloat16(k < kHid ? params[kOffW2 + n * kHid + k] : 0.f);
-        S.W3[i] = __float2bfloat16(k < kHid ? params[kOffW3 + n * kHid + k] : 0.f);
-    }
-    for (int i = threadIdx.x; i < 8 * kS; i += blockDim.x) {
-        const int n = i / kS, k = i % kS;
-        S.W4[i] = __float2bfloat16(n < kOut && k < kHid ? params[kOffW4 + n * kHid + k] : 0.f);
-    }
-    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
-        S.b1[i] = params[kOffB1 + i];
-        S.b2[i] = params[kOffB2 + i];
-        S.b3[i] = params[kOffB3 + i];
-    }
-    if (threadIdx.x < 8) S.b4[threadIdx.x] = threadIdx.x < kOut ? params[kOffB4 + threadIdx.x] : 0.f;
-    if (threadIdx.x < kNorm) S.norm[threadIdx.x] = norm[threadIdx.x];
-}
-
-// One hidden layer for the warp's two 16-row tiles: D (16 x 64 each) =
-// act(A (16 x 16*KT) W^T + b), re-packed as the bf16 A fragments of the next
-// layer (4 k-tiles).  W is [n][k] row-major in shared memory; each ldmatrix.x4
-// brings the B fragments of two n-tiles at one k-tile, used by both row tiles.
-template <int KT>
-__device__ __forceinline__ void hidden_layer2(const uint32_t (&a)[2][KT][4], const __nv_bfloat16 *W, int stride,
-                                              const float *b, uint32_t (&out)[2][4][4])
-{
-    const int lane = threadIdx.x & 31, q = lane & 3;
-    const int mi = lane >> 3, rr = lane & 7;
-#pragma unroll
-    for (int np2 = 0; np2 < 4; ++np2) {           // n-tiles 2 np2, 2 np2 + 1
-        float d[2][2][4];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const float b0 = b[16 * np2 + 8 * s + 2 * q], b1 = b[16 * np2 + 8 * s + 2 * q + 1];
-#pragma unroll
-            for (int tile = 0; tile < 2; ++tile) {
-                d[tile][s][0] = b0; d[tile][s][1] = b1; d[tile][s][2] = b0; d[tile][s][3] = b1;
-            }
-        }
-#pragma unroll
-        for (int kt = 0; kt < KT; ++kt) {
-            uint32_t bf[4];
-            // matrices: (n-tile 2np2, k lo), (2np2, k hi), (2np2+1, k lo), (2np2+1, k hi)
-            ldsm_x4(bf, W + (16 * np2 + 8 * (mi >> 1) + rr) * stride + 16 * kt + 8 * (mi & 1));
-#pragma unroll
-            for (int tile = 0; tile < 2; ++tile) {
-                mma_bf16(d[tile][0], a[tile][kt], bf[0], bf[1]);
-                mma_bf16(d[tile][1], a[tile][kt], bf[2], bf[3]);
-            }
-        }
-#pragma unroll
-        for (int tile = 0; tile < 2; ++tile) {
-            out[tile][np2][0] = gelu_bf16x2(d[tile][0][0], d[tile][0][1]);
-            out[tile][np2][1] = gelu_bf16x2(d[tile][0][2], d[tile][0][3]);
-            out[tile][np2][2] = gelu_bf16x2(d[tile][1][0], d[tile][1][1]);
-            out[tile][np2][3] = gelu_bf16x2(d[tile][1][2], d[tile][1][3]);
-        }
-    }
-}
-
-// 32 markers (two 16-row tiles) through the network.  X: 32 rows of 16 bf16
-// (normalised features, zero padded) at row stride xs.  On return lanes with
-// q == 0 hold, for tile t, the outputs of rows g (y[t][0..1]) and g + 8 (y[t][2..3]).
-__device__ __forceinline__ void mlp_tile32(const MlpTC &S, const __nv_bfloat16 *X, int xs, float (&y)[2][4])
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    uint32_t a0[2][1][4];
-#pragma unroll
-    for (int tile = 0; tile < 2; ++tile) {
-        const __nv_bfloat16 *Xt = X + tile * 16 * xs;
-        a0[tile][0][0] = *reinterpret_cast<const uint32_t *>(Xt + g * xs + 2 * q);
-        a0[tile][0][1] = *reinterpret_cast<const uint32_t *>(Xt + (g + 8) * xs + 2 * q);
-        a0[tile][0][2] = *reinterpret_cast<const uint32_t *>(Xt + g * xs + 2 * q + 8);
-        a0[tile][0][3] = *reinterpret_cast<const uint32_t *>(Xt + (g + 8) * xs + 2 * q + 8);
-    }
-    uint32_t h1[2][4][4], h2[2][4][4];
-    hidden_layer2<1>(a0, S.W1, kS1, S.b1, h1);
-    hidden_layer2<4>(h1, S.W2, kS, S.b2, h2);
-    hidden_layer2<4>(h2, S.W3, kS, S.b3, h1);
-#pragma unroll
-    for (int tile = 0; tile < 2; ++tile) {
-        float d[4];
-        d[0] = S.b4[2 * q]; d[1] = S.b4[2 * q + 1]; d[2] = d[0]; d[3] = d[1];
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            const __nv_bfloat16 *row = S.W4 + g * kS + 16 * kt + 2 * q;
-            mma_bf16(d, h1[tile][kt], *reinterpret_cast<const uint32_t *>(row),
-                     *reinterpret_cast<const uint32_t *>(row + 8));
-        }
-        y[tile][0] = d[0]; y[tile][1] = d[1]; y[tile][2] = d[2]; y[tile][3] = d[3];
-    }
-}
-
-// Per-warp staging of 32 markers' features and outputs.
-constexpr int kXS = 24;   // bf16 row stride of the feature tile (16 used, 16-byte aligned rows)
-struct WarpTile {
-    __nv_bfloat16 X[32 * kXS];
-    float Y[32][2];
+struct MlpChain {
+    __nv_bfloat16 A0[kRows * 16];   // features (K = 16, 6 used)
+    __nv_bfloat16 A[kRows * 64];    // hidden activations (reused per layer)
+    unsigned long long bar;         // MMA completion
+    int abort;
+    int pad[5];
 };
 
-// Zero the padding columns of the warp tile once; rows then take only their
-// six features.
-__device__ __forceinline__ void clear_tile(WarpTile &T)
+// The biases of layers 1-3 ride on the tensor cores: layer 1 takes b1 as weight
+// column 6 against a constant feature 1; layers 2 and 3 add one K = 16 step of a
+// shared block whose column 0 is 1 against a bias block whose column 0 is b.
+struct MlpUmma {
+    __nv_bfloat16 W1[64 * 16];      // [n][k], K = 16: 6 weights, b1, zeros
+    __nv_bfloat16 W2[64 * 64];
+    __nv_bfloat16 W3[64 * 64];
+    __nv_bfloat16 W4[kOutN * 64];   // rows 0, 1 used
+    __nv_bfloat16 ONES[kRows * 16]; // column 0 = 1
+    __nv_bfloat16 B2[64 * 16];      // column 0 = b2
+    __nv_bfloat16 B3[64 * 16];      // column 0 = b3
+    MlpChain C[kChains];
+    float b4[2];
+    float norm[kNorm];
+    uint32_t tmem;                  // tensor-memory base address
+};
+
+// shared-memory matrix descriptor (tcgen05): start, leading (K-direction core
+// matrix) and stride (8-row group) byte offsets, version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(const void *p, uint32_t lbo, uint32_t sbo)
 {
-    const int lane = threadIdx.x & 31;
-    uint32_t *w = reinterpret_cast<uint32_t *>(T.X);
-    for (int i = lane; i < 32 * kXS / 2; i += 32) w[i] = 0u;
-    __syncwarp();
+    const uint32_t a = smem_u32(p);
+    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Features of one marker into row r of the warp tile, normalised (columns 0..5).
-__device__ __forceinline__ void put_features(WarpTile &T, const float *norm, int r, const float f[kIn])
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 {
-    uint32_t *row = reinterpret_cast<uint32_t *>(T.X + r * kXS);
-#pragma unroll
-    for (int i = 0; i < kIn / 2; ++i)
-        row[i] = pack_bf16((f[2 * i] - norm[2 * i]) * norm[kIn + 2 * i],
-                           (f[2 * i + 1] - norm[2 * i + 1]) * norm[kIn + 2 * i + 1]);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Run the warp's 32 rows (two 16-row tiles) and leave the scaled outputs in T.Y.
-__device__ __forceinline__ void run_warp_tile(const MlpTC &S, WarpTile &T)
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
-    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    __syncwarp();
-    float y[2][4];
-    mlp_tile32(S, T.X, kXS, y);
-    if (q == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// barrier of one chain (named barrier 1 + g, its 128 threads)
+__device__ __forceinline__ void chain_sync(int g)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kRows) : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's tensor-memory lane, and the wait
+// for them, in one statement (the registers are valid only after the wait)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
-        for (int tile = 0; tile < 2; ++tile) {
-            T.Y[tile * 16 + g][0] = y[tile][0] * S.norm[2 * kIn];
-            T.Y[tile * 16 + g][1] = y[tile][1] * S.norm[2 * kIn + 1];
-            T.Y[tile * 16 + g + 8][0] = y[tile][2] * S.norm[2 * kIn];
-            T.Y[tile * 16 + g + 8][1] = y[tile][3] * S.norm[2 * kIn + 1];
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float (&v)[2])
+{
+    uint32_t r0, r1;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0), "=r"(r1)
+        : "r"(taddr)
+        : "memory");
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
+}
+
+__device__ __forceinline__ void put_bf16(void *base, int off, float v)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<char *>(base) + off) = __float2bfloat16(v);
+}
+
+// Stage the network (fp32 parameters in global memory) into the operand layouts.
+__device__ void stage_umma(MlpUmma &S, const float *params, const float *norm)
+{
+    for (int i = threadIdx.x; i < 64 * 16; i += blockDim.x) {
+        const int n = i >> 4, k = i & 15;
+        put_bf16(S.W1, kmaj_off(n, k, 16),
+                 k < kIn ? params[kOffW1 + n * kIn + k] : (k == kIn ? params[kOffB1 + n] : 0.f));
+        put_bf16(S.B2, kmaj_off(n, k, 16), k == 0 ? params[kOffB2 + n] : 0.f);
+        put_bf16(S.B3, kmaj_off(n, k, 16), k == 0 ? params[kOffB3 + n] : 0.f);
+    }
+    for (int i = threadIdx.x; i < kRows * 16; i += blockDim.x) {
+        const int r = i >> 4, k = i & 15;
+        put_bf16(S.ONES, kmaj_off(r, k, 16), k == 0 ? 1.f : 0.f);
+    }
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int n = i >> 6, k = i & 63;
+        put_bf16(S.W2, kmaj_off(n, k, 64), params[kOffW2 + n * kHid + k]);
+        put_bf16(S.W3, kmaj_off(n, k, 64), params[kOffW3 + n * kHid + k]);
+    }
+    for (int i = threadIdx.x; i < kOutN * 64; i += blockDim.x) {
+        const int n = i >> 6, k = i & 63;
+        put_bf16(S.W4, kmaj_off(n, k, 64), n < kOut ? params[kOffW4 + n * kHid + k] : 0.f);
+    }
+    if (threadIdx.x < kOut) S.b4[threadIdx.x] = params[kOffB4 + threadIdx.x];
+    if (threadIdx.x < kNorm) S.norm[threadIdx.x] = norm[threadIdx.x];
+    // the padding half of every feature row (k = 8..15) stays zero
+    const int g = threadIdx.x / kRows, r = threadIdx.x % kRows;
+    *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(S.C[g].A0) + kmaj_off(r, 8, 16)) = make_uint4(0, 0, 0, 0);
+}
+
+// Block prologue: chain barriers, tensor memory (warp 0 allocates all 512
+// columns: one block per SM), staged weights.
+__device__ __forceinline__ void umma_begin(MlpUmma &S, const float *params, const float *norm)
+{
+    if (threadIdx.x < kChains) {
+        mbar_init(&S.C[threadIdx.x].bar, 1);
+        S.C[threadIdx.x].abort = 0;
+    }
+    if (threadIdx.x == 0) fence_mbar_init();
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    stage_umma(S, params, norm);
+    fence_proxy_async();           // weights and zero padding: visible to the tensor cores
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ __forceinline__ void umma_end(MlpUmma &S)
+{
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(kTmemCols)
+                     : "memory");
+}
+
+// Write this thread's feature row (normalised, bf16) into its chain's tile.
+__device__ __forceinline__ void umma_put_features(MlpUmma &S, int g, int r, const float f[kIn])
+{
+    uint4 v;
+    v.x = pack_bf16((f[0] - S.norm[0]) * S.norm[kIn + 0], (f[1] - S.norm[1]) * S.norm[kIn + 1]);
+    v.y = pack_bf16((f[2] - S.norm[2]) * S.norm[kIn + 2], (f[3] - S.norm[3]) * S.norm[kIn + 3]);
+    v.z = pack_bf16((f[4] - S.norm[4]) * S.norm[kIn + 4], (f[5] - S.norm[5]) * S.norm[kIn + 5]);
+    v.w = pack_bf16(1.f, 0.f);     // feature 6 = 1 (carries b1)
+    *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(S.C[g].A0) + kmaj_off(r, 0, 16)) = v;
+}
+
+// One layer of chain g: issue (the chain's first thread), wait (all of its
+// threads); false after a bounded wait gave up.
+__device__ __forceinline__ bool umma_layer(MlpUmma &S, int g, int r, const __nv_bfloat16 *Aop, int K,
+                                           const __nv_bfloat16 *Bop, const __nv_bfloat16 *bias,
+                                           uint32_t idesc, unsigned &phase)
+{
+    MlpChain &C = S.C[g];
+    fence_proxy_async();           // this thread's activations: visible to the tensor cores
+    tc_fence_before();
+    chain_sync(g);
+    tc_fence_after();
+    if (r == 0) {
+        const uint32_t sbo = (uint32_t)K * 16;    // K/8 core matrices of 128 bytes per 8-row group
+        for (int kt = 0; kt < K / 16; ++kt)
+            umma_bf16(S.tmem + 64u * g, umma_desc(reinterpret_cast<const char *>(Aop) + kt * 256, 128, sbo),
+                      umma_desc(reinterpret_cast<const char *>(Bop) + kt * 256, 128, sbo), idesc, kt > 0);
+        if (bias)      // + ones x bias^T
+            umma_bf16(S.tmem + 64u * g, umma_desc(S.ONES, 128, 256), umma_desc(bias, 128, 256), idesc, 1u);
+        umma_commit(&C.bar);
+    }
+    bool ok = mbar_wait(&C.bar, phase);
+    if (!ok) atomicExch(&C.abort, 1);
+    chain_sync(g);
+    if (*reinterpret_cast<volatile int *>(&C.abort)) {
+        // gave up: give the MMAs in flight one more bounded wait before the block
+        // frees its tensor memory and leaves
+        mbar_wait(&C.bar, phase);
+        ok = false;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    return ok;
+}
+
+// GELU of this thread's accumulator row (the chain's 64 columns, bias included)
+// into its row of the next layer's operand.  Warp w reads tensor-memory lanes
+// 32 (w % 4) .. + 31.
+__device__ __forceinline__ void umma_epilogue(MlpUmma &S, int g, int r)
+{
+    const uint32_t taddr = S.tmem + ((uint32_t)(r & ~31) << 16) + 64u * g;
+    char *row = reinterpret_cast<char *>(S.C[g].A);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tmem_ld32(taddr + 32 * h, v);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {      // 8 columns = one 16-byte chunk of the row
+            uint4 o;
+            const int k0 = 32 * h + 8 * c;
+            o.x = gelu_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+            o.y = gelu_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+            o.z = gelu_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+            o.w = gelu_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+            *reinterpret_cast<uint4 *>(row + kmaj_off(r, k0, 64)) = o;
         }
     }
-    __syncwarp();
+}
+
+// The network on chain g's 128 feature rows.  Returns false after a bounded wait
+// gave up; y = this row's scaled outputs.
+__device__ __forceinline__ bool umma_network(MlpUmma &S, int g, int r, unsigned &phase, float (&y)[2])
+{
+    constexpr uint32_t kHidDesc = idesc_bf16(kRows, kHid), kOutDesc = idesc_bf16(kRows, kOutN);
+    MlpChain &C = S.C[g];
+    if (!umma_layer(S, g, r, C.A0, 16, S.W1, nullptr, kHidDesc, phase)) return false;
+    umma_epilogue(S, g, r);
+    if (!umma_layer(S, g, r, C.A, 64, S.W2, S.B2, kHidDesc, phase)) return false;
+    umma_epilogue(S, g, r);
+    if (!umma_layer(S, g, r, C.A, 64, S.W3, S.B3, kHidDesc, phase)) return false;
+    umma_epilogue(S, g, r);
+    if (!umma_layer(S, g, r, C.A, 64, S.W4, nullptr, kOutDesc, phase)) return false;
+    float o[2];
+    tmem_ld2(S.tmem + ((uint32_t)(r & ~31) << 16) + 64u * g, o);
+    y[0] = (o[0] + S.b4[0]) * S.norm[2 * kIn];
+    y[1] = (o[1] + S.b4[1]) * S.norm[2 * kIn + 1];
+    return true;
 }
 
 // ---------------------------------------------------------------------------
 // Standalone inference: X (B x 6 raw features, fp32) -> Y (B x 2 scaled outputs).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 2) k_mlp_infer(const float *params, const float *norm, const float *X,
-                                                   long long B, float *Y)
+__global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_infer(const float *params, const float *norm,
+                                                             const float *X, long long B, float *Y, int *status)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    MlpTC &S = *reinterpret_cast<MlpTC *>(smem);
-    WarpTile *tiles = reinterpret_cast<WarpTile *>(smem + ((sizeof(MlpTC) + 15) & ~size_t(15)));
-    stage_tc(S, params, norm);
-    __syncthreads();
-    WarpTile &T = tiles[threadIdx.x >> 5];
-    clear_tile(T);
-    const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < B; base += stride) {
-        const long long a = base + lane;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    MlpUmma &S = *reinterpret_cast<MlpUmma *>(smem);
+    umma_begin(S, params, norm);
+    const int g = threadIdx.x / kRows, r = threadIdx.x % kRows;
+    unsigned phase = 0;
+    const long long stride = (long long)gridDim.x * kChains * kRows;
+    for (long long base = ((long long)blockIdx.x * kChains + g) * kRows; base < B; base += stride) {
+        const long long a = base + r;
         float f[kIn];
 #pragma unroll
         for (int i = 0; i < kIn; ++i) f[i] = a < B ? X[a * kIn + i] : S.norm[i];
-        put_features(T, S.norm, lane, f);
-        run_warp_tile(S, T);
-        if (a < B) {
-            Y[2 * a] = T.Y[lane][0];
-            Y[2 * a + 1] = T.Y[lane][1];
+        umma_put_features(S, g, r, f);
+        float y[2];
+        if (!umma_network(S, g, r, phase, y)) {
+            if (r == 0) atomicOr(status, STATUS_TIMEOUT);
+            break;
         }
-        __syncwarp();
+        if (a < B) {
+            Y[2 * a] = y[0];
+            Y[2 * a + 1] = y[1];
+        }
     }
+    umma_end(S);
 }
 
 // ---------------------------------------------------------------------------
@@ -291,35 +393,30 @@ __global__ void __launch_bounds__(256, 2) k_mlp_infer(const float *params, const
 // with the features gathered at x^n from e_x^n and a^n (staged in shared memory).
 // ---------------------------------------------------------------------------
 template <int K, typename R>
-__global__ void __launch_bounds__(256, 2) k_warm_mlp(WarmArgs A)
+__global__ void __launch_bounds__(kMlpThreads, 1) k_warm_mlp(WarmArgs A)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    MlpTC &S = *reinterpret_cast<MlpTC *>(smem);
-    unsigned char *p = smem + ((sizeof(MlpTC) + 15) & ~size_t(15));
-    WarpTile *tiles = reinterpret_cast<WarpTile *>(p);
-    p += sizeof(WarpTile) * (blockDim.x >> 5);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    MlpUmma &S = *reinterpret_cast<MlpUmma *>(smem);
     const int H = K + 1;
     const int W = A.M + 2 * H;
-    float *s_e = reinterpret_cast<float *>(p);
+    float *s_e = reinterpret_cast<float *>(smem + ((sizeof(MlpUmma) + 127) & ~size_t(127)));
     float2 *s_a = reinterpret_cast<float2 *>(s_e + ((W + 1) & ~1));
-    stage_tc(S, A.params, A.norm);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
-        const int g = wrap_cell(i - H, A.M);
-        s_e[i] = (float)A.ex[g];
-        s_a[i] = make_float2((float)A.ay[g], (float)A.az[g]);
+        const int gg = wrap_cell(i - H, A.M);
+        s_e[i] = (float)A.ex[gg];
+        s_a[i] = make_float2((float)A.ay[gg], (float)A.az[gg]);
     }
-    __syncthreads();
-    WarpTile &T = tiles[threadIdx.x >> 5];
-    clear_tile(T);
-    const int lane = threadIdx.x & 31;
+    umma_begin(S, A.params, A.norm);
+    const int g = threadIdx.x / kRows, r = threadIdx.x % kRows;
     const R *tp = static_cast<const R *>(A.P.t);
     const R *pp = static_cast<const R *>(A.P.p);
     R *dp = static_cast<R *>(A.P.delta);
     const float tau = (float)(A.dt / A.dx);
     const float c2 = (float)(A.dt * A.dt / A.dx);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < A.np; base += stride) {
-        const long long a = base + lane;
+    unsigned phase = 0;
+    const long long stride = (long long)gridDim.x * kChains * kRows;
+    for (long long base = ((long long)blockIdx.x * kChains + g) * kRows; base < A.np; base += stride) {
+        const long long a = base + r;
         const bool act = a < A.np;
         float f[kIn], pn = 0.f, g0 = 1.f;
         if (act) {
@@ -331,24 +428,28 @@ __global__ void __launch_bounds__(256, 2) k_warm_mlp(WarmArgs A)
             bspline_vals<K - 1, float>(t, u);
             float Ay = 0.f, Az = 0.f, Ex = 0.f;
 #pragma unroll
-            for (int r = 0; r <= K; ++r) {
-                const float2 av = s_a[c - r + H];
-                Ay += av.x * v[r];
-                Az += av.y * v[r];
+            for (int q = 0; q <= K; ++q) {
+                const float2 av = s_a[c - q + H];
+                Ay += av.x * v[q];
+                Az += av.y * v[q];
             }
 #pragma unroll
-            for (int r = 0; r < K; ++r) Ex += s_e[c - r + H] * u[r];
+            for (int q = 0; q < K; ++q) Ex += s_e[c - q + H] * u[q];
             g0 = sqrtf(1.f + pn * pn + Ay * Ay + Az * Az);
             f[0] = t; f[1] = pn; f[2] = Ex; f[3] = Ay; f[4] = Az; f[5] = (float)A.dt;
         } else {
 #pragma unroll
             for (int i = 0; i < kIn; ++i) f[i] = S.norm[i];
         }
-        put_features(T, S.norm, lane, f);
-        run_warp_tile(S, T);
-        if (act) dp[a] = (R)(tau * pn / g0 + T.Y[lane][0] * c2);
-        __syncwarp();
+        umma_put_features(S, g, r, f);
+        float y[2];
+        if (!umma_network(S, g, r, phase, y)) {
+            if (r == 0) atomicOr(A.status, STATUS_TIMEOUT);
+            break;
+        }
+        if (act) dp[a] = (R)(tau * pn / g0 + y[0] * c2);
     }
+    umma_end(S);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,7 +483,7 @@ __device__ __forceinline__ void dense_fwd(const float *W, const float *b, const 
 __global__ void __launch_bounds__(256) k_mlp_train(const float *params, const float *norm, const float *X,
                                                    const float *Tg, long long B, float *grad, double *loss)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem);
     const long long s0 = (long long)blockIdx.x * kTB;
     const int ns = (int)min((long long)kTB, B - s0);
@@ -482,18 +583,24 @@ __global__ void k_adam(float *params, float *m, float *v, const float *g, int n,
     params[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-size_t mlp_infer_smem(int warps) { return ((sizeof(MlpTC) + 15) & ~size_t(15)) + sizeof(WarpTile) * warps; }
+// Every block allocates all 512 tensor-memory columns of its SM, so only one
+// block may be resident per SM (a second would wait in tcgen05.alloc): the
+// shared-memory request is padded above half of the SM's.
+constexpr size_t kMinUmmaSmem = 120 * 1024;
 
-size_t warm_mlp_smem(int M, int K, int warps)
+size_t mlp_infer_smem() { return sizeof(MlpUmma) > kMinUmmaSmem ? sizeof(MlpUmma) : kMinUmmaSmem; }
+
+size_t warm_mlp_smem(int M, int K)
 {
     const size_t W = (size_t)M + 2 * (size_t)(K + 1);
-    return mlp_infer_smem(warps) + ((W + 1) & ~size_t(1)) * sizeof(float) + W * sizeof(float2);
+    const size_t s = ((sizeof(MlpUmma) + 127) & ~size_t(127)) + ((W + 1) & ~size_t(1)) * sizeof(float) +
+                     W * sizeof(float2);
+    return s > kMinUmmaSmem ? s : kMinUmmaSmem;
 }
 
 int launch_warm_mlp(const WarmArgs &a, int grid, cudaStream_t s)
 {
-    const int block = 256;
-    const size_t smem = warm_mlp_smem(a.M, a.K, block / 32);
+    const size_t smem = warm_mlp_smem(a.M, a.K);
     static size_t opted = 0;
     if (smem > opted) {
         cudaError_t e = cudaSuccess;
@@ -506,8 +613,8 @@ int launch_warm_mlp(const WarmArgs &a, int grid, cudaStream_t s)
     }
 #define LAUNCH(KK)                                                                               \
     case KK:                                                                                     \
-        if (a.fp32) k_warm_mlp<KK, float><<<grid, block, smem, s>>>(a);                          \
-        else k_warm_mlp<KK, double><<<grid, block, smem, s>>>(a);                                \
+        if (a.fp32) k_warm_mlp<KK, float><<<grid, kMlpThreads, smem, s>>>(a);                          \
+        else k_warm_mlp<KK, double><<<grid, kMlpThreads, smem, s>>>(a);                                \
         break;
     switch (a.K) {
         LAUNCH(2) LAUNCH(3) LAUNCH(4) LAUNCH(5)
@@ -526,6 +633,7 @@ struct pic_mlp {
     int num_sms = 0;
     float *params = nullptr, *norm = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     double *loss = nullptr;
+    int *status = nullptr;          // error bits of the inference kernel
     long long t = 0;
 };
 
@@ -550,7 +658,8 @@ extern "C" int pic_mlp_create(const float *params, const float *norm, void *stre
               cudaMalloc((void **)&m->grad, kNParams * sizeof(float)) == cudaSuccess &&
               cudaMalloc((void **)&m->m, kNParams * sizeof(float)) == cudaSuccess &&
               cudaMalloc((void **)&m->v, kNParams * sizeof(float)) == cudaSuccess &&
-              cudaMalloc((void **)&m->loss, sizeof(double)) == cudaSuccess;
+              cudaMalloc((void **)&m->loss, sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&m->status, sizeof(int)) == cudaSuccess;
     if (!ok) {
         pic_mlp_destroy(m);
         return mlp_fail(PIC_ERR_NOMEM, "pic_mlp_create: cudaMalloc failed");
@@ -573,6 +682,7 @@ extern "C" int pic_mlp_destroy(pic_mlp *m)
     if (!m) return PIC_OK;
     cudaStreamSynchronize(m->stream);
     cudaFree(m->params); cudaFree(m->norm); cudaFree(m->grad); cudaFree(m->m); cudaFree(m->v); cudaFree(m->loss);
+    cudaFree(m->status);
     delete m;
     return PIC_OK;
 }
@@ -632,19 +742,24 @@ extern "C" int pic_mlp_infer(pic_mlp *m, const float *X, int64_t B, float *Y)
 {
     if (!m || !X || !Y || B < 0) return mlp_fail(PIC_ERR_INVALID, "pic_mlp_infer: invalid argument");
     if (B == 0) return PIC_OK;
-    const int block = 256;
-    const size_t smem = mlp_infer_smem(block / 32);
+    const size_t smem = mlp_infer_smem();
     static bool opted = false;
     if (!opted) {
         if (cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return mlp_fail(PIC_ERR_CUDA, "pic_mlp_infer: shared-memory opt-in failed");
         opted = true;
     }
-    long long blocks = (B + block - 1) / block;
-    if (blocks > (long long)m->num_sms * 4) blocks = (long long)m->num_sms * 4;
-    k_mlp_infer<<<(unsigned)blocks, block, smem, m->stream>>>(m->params, m->norm, X, B, Y);
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(m->stream) != cudaSuccess)
+    long long blocks = (B + kMlpThreads - 1) / kMlpThreads;
+    if (blocks > (long long)m->num_sms) blocks = (long long)m->num_sms;
+    if (cudaMemsetAsync(m->status, 0, sizeof(int), m->stream) != cudaSuccess)
+        return mlp_fail(PIC_ERR_CUDA, "pic_mlp_infer: status reset failed");
+    k_mlp_infer<<<(unsigned)blocks, kMlpThreads, smem, m->stream>>>(m->params, m->norm, X, B, Y, m->status);
+    int st = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
         return mlp_fail(PIC_ERR_CUDA, "pic_mlp_infer: kernel failed");
+    if (st) return mlp_fail(PIC_ERR_CUDA, "pic_mlp_infer: a bounded wait on the tensor cores gave up");
     return PIC_OK;
 }
 

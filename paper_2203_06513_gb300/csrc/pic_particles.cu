@@ -445,7 +445,7 @@ int launch_sweep1(const Sweep1Args &a, int grid, int block, size_t smem, cudaStr
 template <int K, typename R>
 __global__ void __launch_bounds__(256) k_current(CurrentArgs A)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int H = A.H;
     const int W = A.M + 2 * H;
     double *s_acc = reinterpret_cast<double *>(smem);
@@ -720,7 +720,7 @@ int launch_sweep2(const Sweep2Args &a, int grid, int block, size_t smem, cudaStr
 template <int K, typename R>
 __global__ void __launch_bounds__(256) k_charge(DiagArgs A)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int H = K + 1;
     const int W = A.M + 2 * H;
     double *s_acc = reinterpret_cast<double *>(smem);

@@ -154,6 +154,43 @@ def test_ragged_and_tiny_marker_counts(npart):
     compare_state(g, s, w.L, 1e-12, 1e-11, 1e-11)
 
 
+@pytest.mark.parametrize("precision", [pic.PIC_FP64, pic.PIC_FP32])
+def test_all_markers_in_one_cell(precision):
+    """Degenerate distribution: every marker in one cell (all warps on the same
+    deposit window, heavy same-address accumulation), moving both ways."""
+    w = small(M=32, npart=5003, vth=0.3, pump=0.2)
+    x = 7.0 * w.dx + 0.999 * w.dx * np.random.default_rng(12).random(w.np)
+    p = np.random.default_rng(13).normal(0.0, w.vth, w.np)
+    ay, az, ey, ez = I.fields(w)
+    orc = O.Oracle(w.L, w.nx, w.degree, w.weight, w.dt, w.tol, w.max_iter)
+    s = O.initial_state(orc, x, p, ay, az, ey, ez)
+    g = pic.Pic(pic.Config.from_workload(w, precision=precision, sort_every=1), x, p, ay, az, ey, ez)
+    for _ in range(3):
+        s = orc.step(s)
+    g.step(3)
+    if precision == pic.PIC_FP64:
+        compare_state(g, s, w.L, 1e-12, 1e-11, 1e-11)
+    else:
+        compare_state(g, s, w.L, 1e-6, 1e-5, 1e-5)
+
+
+def test_grid_too_large_for_shared_memory_is_rejected():
+    """nx = 8192 with quintic splines cannot be staged in shared memory: pic_init
+    refuses it with PIC_ERR_INVALID and a message, and the library stays usable."""
+    w = I.Workload("big", nx=8192, degree=5, np=1000)
+    x, p = I.particles(w)
+    ay, az, ey, ez = I.fields(w)
+    with pytest.raises(pic.PicError) as e:
+        pic.Pic(pic.Config.from_workload(w, precision=pic.PIC_FP32), x, p, ay, az, ey, ez)
+    assert e.value.code == pic.PIC_ERR_INVALID and "shared memory" in str(e.value)
+    w2 = small(M=16, npart=100)
+    x2, p2 = I.particles(w2)
+    ay2, az2, ey2, ez2 = I.fields(w2)
+    g = pic.Pic(pic.Config.from_workload(w2), x2, p2, ay2, az2, ey2, ez2)
+    g.step(1)
+    g.close()
+
+
 @pytest.mark.parametrize("M", [16, 128])
 def test_edge_markers_on_knots_at_rest_and_crossing_the_boundary(M):
     """Markers exactly on knots, at rest, and crossing x = 0 and x = L; with
