@@ -61,19 +61,25 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 // GELU (tanh form) of two pre-activations, evaluated in packed bf16 arithmetic on
 // their bf16 roundings and returned packed: the result is a bf16 activation of
 // the next layer either way, and one tanh.approx.bf16x2 serves both values.
-__device__ __forceinline__ uint32_t gelu_bf16x2(float z0, float z1)
+struct GeluConsts {
+    __nv_bfloat162 c0, c1, half;    // sqrt(2/pi), sqrt(2/pi) 0.044715, 1/2
+    __device__ __forceinline__ GeluConsts()
+        : c0(__float2bfloat162_rn(0.7978845608028654f)),
+          c1(__float2bfloat162_rn(0.7978845608028654f * 0.044715f)), half(__float2bfloat162_rn(0.5f))
+    {
+    }
+};
+
+__device__ __forceinline__ uint32_t gelu_bf16x2(float z0, float z1, const GeluConsts &k)
 {
     const __nv_bfloat162 z = __floats2bfloat162_rn(z0, z1);
-    const __nv_bfloat162 c0 = __float2bfloat162_rn(0.7978845608028654f);
-    const __nv_bfloat162 c1 = __float2bfloat162_rn(0.7978845608028654f * 0.044715f);
-    const __nv_bfloat162 half = __float2bfloat162_rn(0.5f);
-    const __nv_bfloat162 u = __hmul2(z, __hfma2(__hmul2(z, z), c1, c0));   // c0 z + c1 z^3
+    const __nv_bfloat162 u = __hmul2(z, __hfma2(__hmul2(z, z), k.c1, k.c0));   // c0 z + c1 z^3
     uint32_t ui, ti;
     memcpy(&ui, &u, 4);
     asm("tanh.approx.bf16x2 %0, %1;" : "=r"(ti) : "r"(ui));
     __nv_bfloat162 th;
     memcpy(&th, &ti, 4);
-    const __nv_bfloat162 out = __hmul2(z, __hfma2(th, half, half));         // z (1 + tanh u) / 2
+    const __nv_bfloat162 out = __hmul2(z, __hfma2(th, k.half, k.half));       // z (1 + tanh u) / 2
     uint32_t o;
     memcpy(&o, &out, 4);
     return o;
@@ -299,8 +305,14 @@ __device__ __forceinline__ bool umma_layer(MlpUmma &S, int g, int r, const __nv_
             umma_bf16(S.tmem + 64u * g, umma_desc(S.ONES, 128, 256), umma_desc(bias, 128, 256), idesc, 1u);
         umma_commit(&C.bar);
     }
-    bool ok = mbar_wait(&C.bar, phase);
-    if (!ok) atomicExch(&C.abort, 1);
+    // warp 0 of the chain waits for the MMAs (bounded); the other warps block at
+    // the chain barrier instead of polling
+    bool ok = true;
+    if (r < 32) {
+        ok = mbar_wait(&C.bar, phase);
+        if (!ok) atomicExch(&C.abort, 1);
+        tc_fence_before();
+    }
     chain_sync(g);
     if (*reinterpret_cast<volatile int *>(&C.abort)) {
         // gave up: give the MMAs in flight one more bounded wait before the block
@@ -320,6 +332,7 @@ __device__ __forceinline__ void umma_epilogue(MlpUmma &S, int g, int r)
 {
     const uint32_t taddr = S.tmem + ((uint32_t)(r & ~31) << 16) + 64u * g;
     char *row = reinterpret_cast<char *>(S.C[g].A);
+    const GeluConsts k;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float v[32];
@@ -328,10 +341,10 @@ __device__ __forceinline__ void umma_epilogue(MlpUmma &S, int g, int r)
         for (int c = 0; c < 4; ++c) {      // 8 columns = one 16-byte chunk of the row
             uint4 o;
             const int k0 = 32 * h + 8 * c;
-            o.x = gelu_bf16x2(v[8 * c + 0], v[8 * c + 1]);
-            o.y = gelu_bf16x2(v[8 * c + 2], v[8 * c + 3]);
-            o.z = gelu_bf16x2(v[8 * c + 4], v[8 * c + 5]);
-            o.w = gelu_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+            o.x = gelu_bf16x2(v[8 * c + 0], v[8 * c + 1], k);
+            o.y = gelu_bf16x2(v[8 * c + 2], v[8 * c + 3], k);
+            o.z = gelu_bf16x2(v[8 * c + 4], v[8 * c + 5], k);
+            o.w = gelu_bf16x2(v[8 * c + 6], v[8 * c + 7], k);
             *reinterpret_cast<uint4 *>(row + kmaj_off(r, k0, 64)) = o;
         }
     }
