@@ -97,6 +97,7 @@ static void release(pic_handle *h)
     for (double *a : arr) f(a);
     f(h->counts);
     f(h->ctrl);
+    f(h->img.a); f(h->img.f); f(h->img.an); f(h->img.ak); f(h->img.lo);
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -265,6 +266,15 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
     for (double **a : grid_arrays)
         if ((rc = dalloc(h, a, M))) return bail(rc);
     if ((rc = dalloc(h, &h->diag, 8))) return bail(rc);
+    if (h->fp32) {
+        if ((rc = dalloc(h, &h->img.a, M)) || (rc = dalloc(h, &h->img.f, M)) || (rc = dalloc(h, &h->img.an, M)) ||
+            (rc = dalloc(h, &h->img.ak, M)) || (rc = dalloc(h, &h->img.lo, M)))
+            return bail(rc);
+        double fact = 1.0;
+        for (int d = 2; d <= c.degree; ++d) fact *= d;
+        h->img.inv_fact = 1.0 / fact;
+        h->img.escale = dx / (double)mean_scale(c.degree - 1);
+    }
     if ((rc = dalloc(h, &h->counts, 2 * M * kVelBins))) return bail(rc);
     if ((rc = dalloc(h, &h->ctrl, 1))) return bail(rc);
     if (cudaMallocHost((void **)&h->h_flag, sizeof(int)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
@@ -406,7 +416,7 @@ static int substep1(pic_handle *h, int *iters)
 {
     int rc;
     launch_prep1(h->M, h->dx, h->ex, h->ek, h->ebar, h->ay, h->az, h->ga_y, h->ga_z, h->jb[0],
-                 h->jb[1], h->ctrl, h->stream);
+                 h->jb[1], h->ctrl, h->img, h->stream);
     CKL_N("launch_prep1");
     Sweep1Args a{};
     a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.np = h->np;
@@ -414,7 +424,9 @@ static int substep1(pic_handle *h, int *iters)
     a.P = cur_parts(h);
     a.ebar = h->ebar; a.ga_y = h->ga_y; a.ga_z = h->ga_z; a.ay = h->ay; a.az = h->az;
     a.ctrl = h->ctrl;
+    a.img = h->img;
     ConvArgs c{};
+    c.img = h->img;
     c.M = h->M; c.d_start = h->tapM1_start; c.ntap = h->tapM1_n; c.mode = CONV_SOLVE1; c.ncomp = 1;
     c.taps = h->d_tapM1;
     c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
@@ -469,7 +481,7 @@ static int substep2(pic_handle *h, int *iters)
     int rc;
     launch_prep2(h->M, h->K, h->cfg.dt, h->d_rowPm, h->d_rowK, h->ey, h->ez, h->ay, h->az, h->by,
                  h->bz, h->eky, h->ekz, h->aky, h->akz, h->sy[0], h->sz[0], h->sy[1], h->sz[1],
-                 h->ctrl, h->stream);
+                 h->ctrl, h->img, h->stream);
     CKL_N("launch_prep2");
     if ((rc = conv_plain(h, h->d_tapP, h->tapP_start, h->tapP_n, h->by, h->r0y, h->bz, h->r0z))) return rc;
     Sweep2Args a{};
@@ -477,7 +489,9 @@ static int substep2(pic_handle *h, int *iters)
     a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.w = h->cfg.weight;
     a.P = cur_parts(h);
     a.an_y = h->ay; a.an_z = h->az; a.ak_y = h->aky; a.ak_z = h->akz;
+    a.img = h->img;
     ConvArgs c{};
+    c.img = h->img;
     c.M = h->M; c.d_start = h->tapP_start; c.ntap = h->tapP_n; c.mode = CONV_SOLVE2; c.ncomp = 2;
     c.taps = h->d_tapP;
     c.en[0] = h->ey; c.en[1] = h->ez; c.ek[0] = h->eky; c.ek[1] = h->ekz;

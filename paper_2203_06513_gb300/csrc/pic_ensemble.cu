@@ -120,6 +120,7 @@ static void build_tables(pic_ensemble *e)
         d.eky = h->eky; d.ekz = h->ekz; d.aky = h->aky; d.akz = h->akz;
         d.sy0 = h->sy[0]; d.sz0 = h->sz[0]; d.sy1 = h->sy[1]; d.sz1 = h->sz[1];
         d.ctrl = h->ctrl;
+        d.img = h->img;
 
         Sweep1Args &a = e->a1[r];
         a = Sweep1Args{};
@@ -132,6 +133,7 @@ static void build_tables(pic_ensemble *e)
         a.warm = h->cfg.warm_start == PIC_WARM_EXPLICIT ? 1 : 0;
         a.graph = 1;
         a.jpair[0] = h->jb[0]; a.jpair[1] = h->jb[1];
+        a.img = h->img;
 
         ConvArgs &c = e->c1[r];
         c = ConvArgs{};
@@ -143,6 +145,7 @@ static void build_tables(pic_ensemble *e)
         c.graph = 1;
         c.pair[0][0] = h->jb[0]; c.pair[0][1] = h->jb[1];
         c.cond_handle = 0;      // the ensemble ends the loop, not the run
+        c.img = h->img;
 
         Sweep2Args &b = e->a2[r];
         b = Sweep2Args{};
@@ -154,6 +157,7 @@ static void build_tables(pic_ensemble *e)
         b.graph = 1; b.ctrl = h->ctrl;
         b.sypair[0] = h->sy[0]; b.sypair[1] = h->sy[1];
         b.szpair[0] = h->sz[0]; b.szpair[1] = h->sz[1];
+        b.img = h->img;
 
         ConvArgs &g = e->c2[r];
         g = ConvArgs{};
@@ -168,6 +172,7 @@ static void build_tables(pic_ensemble *e)
         g.pair[0][0] = h->sy[0]; g.pair[0][1] = h->sy[1];
         g.pair[1][0] = h->sz[0]; g.pair[1][1] = h->sz[1];
         g.cond_handle = 0;
+        g.img = h->img;
 
         ConvArgs &p = e->cp[r];
         p = ConvArgs{};

@@ -33,6 +33,12 @@ static double cardinal_tp(int n, double s)
     return acc / fact;
 }
 
+int mean_scale(int d)
+{
+    static const int S[] = {1, 1, 6, 6, 120};
+    return (d >= 0 && d <= 4) ? S[d] : 0;
+}
+
 void mass_band(int d, double dx, double *band)
 {
     for (int r = 0; r <= d; ++r) band[r] = dx * cardinal_tp(2 * d + 1, (double)(d + 1 + r));
@@ -171,6 +177,29 @@ __device__ void decide(const ConvArgs &A)
         cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond_handle, stop ? 0u : 1u);
 }
 
+// float images of sweep I: a / K! rounded, their differences, ebar dx / S1 rounded
+__device__ __forceinline__ void image1_at(int i, int M, const double *ay, const double *az, double ebar,
+                                          const StageImages &img)
+{
+    const int im = (i == 0) ? M - 1 : i - 1;
+    const float y = (float)(ay[i] * img.inv_fact), ym = (float)(ay[im] * img.inv_fact);
+    const float z = (float)(az[i] * img.inv_fact), zm = (float)(az[im] * img.inv_fact);
+    img.a[i] = make_float2(y, z);
+    img.f[i] = make_float4((float)(ebar * img.escale), y - ym, z - zm, 0.f);
+}
+
+// float images of sweep II for one component c: a^(k) / K! rounded and the residue
+// of the sum a^n / K! + a^(k) / K! after both roundings
+__device__ __forceinline__ void image2_at(int i, int c, double an, double ak, const StageImages &img)
+{
+    const double n = an * img.inv_fact, k = ak * img.inv_fact;
+    const float hn = (float)n, hk = (float)k;
+    const float lo = (float)((n - (double)hn) + (k - (double)hk));
+    float *pk = reinterpret_cast<float *>(&img.ak[i]), *pl = reinterpret_cast<float *>(&img.lo[i]);
+    pk[c] = hk;
+    pl[c] = lo;
+}
+
 // y_i = sum_n taps[n] in[(i - (d_start + n)) mod M], one output per thread,
 // input and taps staged in shared memory (input twice, so no index wraps).
 // Block bx of component comp; returns true in the one block that finished the
@@ -217,6 +246,7 @@ __device__ bool conv_block(const ConvArgs &A, int bx, int comp, double *s_conv, 
             mag = fabs(enew);
             A.ek[0][i] = enew;
             A.aux[0][i] = 0.5 * (en + enew);             // ebar for the next sweep
+            if (A.img.f) reinterpret_cast<float *>(A.img.f)[4 * i] = (float)(0.5 * (en + enew) * A.img.escale);
             zero[i] = 0.0;
         } else {                                         // CONV_SOLVE2
             const double en = A.en[comp][i];
@@ -224,7 +254,9 @@ __device__ bool conv_block(const ConvArgs &A, int bx, int comp, double *s_conv, 
             diff = fabs(enew - A.ek[comp][i]);
             mag = fabs(enew);
             A.ek[comp][i] = enew;
-            A.aux[comp][i] = A.an[comp][i] - 0.5 * A.dt * (en + enew);   // a^(k+1)
+            const double ak = A.an[comp][i] - 0.5 * A.dt * (en + enew);   // a^(k+1)
+            A.aux[comp][i] = ak;
+            if (A.img.ak) image2_at(i, comp, A.an[comp][i], ak, A.img);
             zero[i] = 0.0;
         }
     }
@@ -336,8 +368,10 @@ __device__ __forceinline__ void ctrl_loop_reset(DevCtrl *ctrl)
 
 __device__ __forceinline__ void prep1_at(int i, int M, double dx, const double *ex, double *ek,
                                          double *ebar, const double *ay, const double *az,
-                                         double *gay, double *gaz, double *j0, double *j1, DevCtrl *ctrl)
+                                         double *gay, double *gaz, double *j0, double *j1, DevCtrl *ctrl,
+                                         const StageImages &img)
 {
+    if (i < M && img.a) image1_at(i, M, ay, az, ex[i], img);
     if (i < M) {
         const int im = (i == 0) ? M - 1 : i - 1;
         gay[i] = (ay[i] - ay[im]) / dx;
@@ -352,16 +386,16 @@ __device__ __forceinline__ void prep1_at(int i, int M, double dx, const double *
 
 __global__ void k_prep1(int M, double dx, const double *ex, double *ek, double *ebar,
                         const double *ay, const double *az, double *gay, double *gaz,
-                        double *j0, double *j1, DevCtrl *ctrl)
+                        double *j0, double *j1, DevCtrl *ctrl, StageImages img)
 {
-    prep1_at(blockIdx.x * blockDim.x + threadIdx.x, M, dx, ex, ek, ebar, ay, az, gay, gaz, j0, j1, ctrl);
+    prep1_at(blockIdx.x * blockDim.x + threadIdx.x, M, dx, ex, ek, ebar, ay, az, gay, gaz, j0, j1, ctrl, img);
 }
 
 __global__ void k_prep1_ens(const RunDesc *runs)
 {
     const RunDesc &R = runs[blockIdx.y];
     prep1_at(blockIdx.x * blockDim.x + threadIdx.x, R.M, R.dx, R.ex, R.ek, R.ebar, R.ay, R.az, R.ga_y,
-             R.ga_z, R.j0, R.j1, R.ctrl);
+             R.ga_z, R.j0, R.j1, R.ctrl, R.img);
 }
 
 int launch_prep1_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
@@ -372,9 +406,9 @@ int launch_prep1_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
 
 int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, const double *ay,
                  const double *az, double *ga_y, double *ga_z, double *j0, double *j1,
-                 DevCtrl *ctrl, cudaStream_t s)
+                 DevCtrl *ctrl, const StageImages &img, cudaStream_t s)
 {
-    k_prep1<<<(M + 255) / 256, 256, 0, s>>>(M, dx, ex, ek, ebar, ay, az, ga_y, ga_z, j0, j1, ctrl);
+    k_prep1<<<(M + 255) / 256, 256, 0, s>>>(M, dx, ex, ek, ebar, ay, az, ga_y, ga_z, j0, j1, ctrl, img);
     return 0;
 }
 
@@ -386,8 +420,15 @@ __device__ __forceinline__ void prep2_at(int i, int M, int K, double dt, const d
                                          const double *rowK, const double *ey, const double *ez,
                                          const double *ay, const double *az, double *by, double *bz,
                                          double *eky, double *ekz, double *aky, double *akz, double *s00,
-                                         double *s01, double *s10, double *s11, DevCtrl *ctrl)
+                                         double *s01, double *s10, double *s11, DevCtrl *ctrl,
+                                         const StageImages &img)
 {
+    if (i < M && img.an) {
+        const double y0 = ay[i] - dt * ey[i], z0 = az[i] - dt * ez[i];     // a^(0), as below
+        img.an[i] = make_float2((float)(ay[i] * img.inv_fact), (float)(az[i] * img.inv_fact));
+        image2_at(i, 0, ay[i], y0, img);
+        image2_at(i, 1, az[i], z0, img);
+    }
     if (i < M) {
         double vy = rowPm[0] * ey[i] + dt * rowK[0] * ay[i];
         double vz = rowPm[0] * ez[i] + dt * rowK[0] * az[i];
@@ -410,17 +451,17 @@ __device__ __forceinline__ void prep2_at(int i, int M, int K, double dt, const d
 __global__ void k_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
                         const double *ey, const double *ez, const double *ay, const double *az,
                         double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
-                        double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl)
+                        double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl, StageImages img)
 {
     prep2_at(blockIdx.x * blockDim.x + threadIdx.x, M, K, dt, rowPm, rowK, ey, ez, ay, az, by, bz, eky,
-             ekz, aky, akz, s00, s01, s10, s11, ctrl);
+             ekz, aky, akz, s00, s01, s10, s11, ctrl, img);
 }
 
 __global__ void k_prep2_ens(const RunDesc *runs)
 {
     const RunDesc &R = runs[blockIdx.y];
     prep2_at(blockIdx.x * blockDim.x + threadIdx.x, R.M, R.K, R.dt, R.rowPm, R.rowK, R.ey, R.ez, R.ay,
-             R.az, R.by, R.bz, R.eky, R.ekz, R.aky, R.akz, R.sy0, R.sz0, R.sy1, R.sz1, R.ctrl);
+             R.az, R.by, R.bz, R.eky, R.ekz, R.aky, R.akz, R.sy0, R.sz0, R.sy1, R.sz1, R.ctrl, R.img);
 }
 
 int launch_prep2_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
@@ -432,10 +473,11 @@ int launch_prep2_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
 int launch_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
                  const double *ey, const double *ez, const double *ay, const double *az,
                  double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
-                 double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl, cudaStream_t s)
+                 double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl,
+                 const StageImages &img, cudaStream_t s)
 {
     k_prep2<<<(M + 255) / 256, 256, 0, s>>>(M, K, dt, rowPm, rowK, ey, ez, ay, az, by, bz, eky, ekz,
-                                            aky, akz, s00, s01, s10, s11, ctrl);
+                                            aky, akz, s00, s01, s10, s11, ctrl, img);
     return 0;
 }
 

@@ -9,6 +9,7 @@
 using pic::PartPtrs;
 using pic::DevCtrl;
 using pic::kSweepThreads;
+using pic::StageImages;
 
 struct pic_handle {
     pic_config cfg{};
@@ -39,6 +40,7 @@ struct pic_handle {
     double *d_tapM1 = nullptr, *d_tapP = nullptr;
     int tapM1_start = 0, tapM1_n = 0, tapP_start = 0, tapP_n = 0;
 
+    StageImages img{};              // float staging images (FP32 form)
     DevCtrl *ctrl = nullptr;
     int *h_flag = nullptr;          // pinned: converged flag readback
     DevCtrl *h_ctrl = nullptr;      // pinned: full control block readback

@@ -23,6 +23,20 @@ struct PartPtrs {
     int32_t *id;        // caller index of each stored marker
 };
 
+// Float staging images of the grid fields for the float-form sweeps, built on the
+// grid side (prep kernels once per substep, solve epilogues once per sweep) so that
+// the sweep blocks copy them instead of converting doubles per block range.  All
+// pointers null in the double form.
+struct StageImages {
+    float2 *a;          // sweep I: fl(a_y / K!), fl(a_z / K!)
+    float4 *f;          // sweep I: fl(ebar dx / S1), fl(a_j) - fl(a_{j-1}) for y and z, 0
+    float2 *an;         // sweep II: fl(a^n / K!)
+    float2 *ak;         // sweep II: fl(a^(k) / K!)
+    float2 *lo;         // sweep II: fl((a^n/K! - an) + (a^(k)/K! - ak))
+    double inv_fact;    // 1 / K!
+    double escale;      // dx / S1 (S1: scale of the degree-(K-1) path means)
+};
+
 struct Sweep1Args {
     int M, H, Dlim, K, fp32;
     long long np;
@@ -37,6 +51,7 @@ struct Sweep1Args {
     // iter read from ctrl at kernel start
     int graph;
     double *jpair[2];
+    StageImages img;
 };
 
 struct Sweep2Args {
@@ -51,6 +66,7 @@ struct Sweep2Args {
     int graph;
     const DevCtrl *ctrl;
     double *sypair[2], *szpair[2];
+    StageImages img;
 };
 
 struct CurrentArgs {
@@ -114,6 +130,7 @@ struct ConvArgs {
     int graph;
     double *pair[2][2];
     unsigned long long cond_handle;
+    StageImages img;    // SOLVE1: f.x = ebar image; SOLVE2: ak, lo
 };
 
 int launch_conv(const ConvArgs &a, cudaStream_t s);
@@ -154,6 +171,7 @@ struct RunDesc {
     const double *rowPm, *rowK;
     double *ey, *ez, *by, *bz, *eky, *ekz, *aky, *akz, *sy0, *sz0, *sy1, *sz1;
     DevCtrl *ctrl;
+    StageImages img;
 };
 
 int launch_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns, unsigned long long cond, cudaStream_t s);
@@ -171,11 +189,14 @@ int launch_sweep2_ens(int K, int fp32, const Sweep2Args *runs, int nruns, EnsQue
 int launch_finalize1_ens(int fp32, const RunDesc *R, int nruns, int grid_x, cudaStream_t s);
 int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, const double *ay,
                  const double *az, double *ga_y, double *ga_z, double *j0, double *j1,
-                 DevCtrl *ctrl, cudaStream_t s);
+                 DevCtrl *ctrl, const StageImages &img, cudaStream_t s);
 int launch_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
                  const double *ey, const double *ez, const double *ay, const double *az,
                  double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
-                 double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl, cudaStream_t s);
+                 double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl,
+                 const StageImages &img, cudaStream_t s);
+// scale S of the scaled path means of degree d (the sweeps' piece_means_scaled)
+int mean_scale(int d);
 int launch_copy(int M, const double *src0, double *dst0, const double *src1, double *dst1,
                 const double *src2, double *dst2, const double *src3, double *dst3, cudaStream_t s);
 int launch_poisson_rhs(int M, double dx, const double *rho, double *d, cudaStream_t s);

@@ -47,6 +47,11 @@ template <> struct FieldTile<float> {
         a[i] = make_float2((float)ay, (float)az);
         f[i] = make_float4((float)e, (float)gy, (float)gz, 0.f);
     }
+    __device__ __forceinline__ void copy_image(int i, const StageImages &img, int g)
+    {
+        a[i] = img.a[g];
+        f[i] = img.f[g];
+    }
     static size_t bytes(size_t W) { return W * (sizeof(float2) + sizeof(float4)); }
 };
 // Double form: the differences a_j - a_{j-1} are formed from the staged
@@ -66,6 +71,7 @@ template <> struct FieldTile<double> {
         a[i] = make_double2(ay, az);
         e[i] = ev;
     }
+    __device__ __forceinline__ void copy_image(int, const StageImages &, int) {}
     static size_t bytes(size_t W) { return W * (sizeof(double2) + sizeof(double)); }
 };
 
@@ -260,17 +266,26 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     constexpr int S1 = MeanScale<K - 1>::S;
     constexpr int DK = K / MeanScale<K - 1>::X;
     const double inv_fact = 1.0 / (double)Fact<K>::v;
-    for (int i = threadIdx.x; i < W; i += blockDim.x) {
-        const int g = wrap_cell(i - H, A.M);
-        const int gm = g == 0 ? A.M - 1 : g - 1;
-        // the differences of a are formed from the coefficients as staged (rounded
-        // to R), so that the path mean of dA/dx times (x1 - x0) equals A(x1) - A(x0)
-        // of the staged field: the discrete gradient of the A-term stays exact for
-        // the field the markers see
-        const R ay = (R)(A.ay[g] * inv_fact), aym = (R)(A.ay[gm] * inv_fact);
-        const R az = (R)(A.az[g] * inv_fact), azm = (R)(A.az[gm] * inv_fact);
-        F.store(i, ay, az, A.ebar[g] * A.dx / S1, (double)(ay - aym), (double)(az - azm));
-        s_acc[i] = 0.0;
+    if (Real<R>::fp32 && A.img.a) {
+        // float images built on the grid side (same values as the branch below)
+        for (int i = threadIdx.x; i < W; i += blockDim.x) {
+            const int g = wrap_cell(i - H, A.M);
+            F.copy_image(i, A.img, g);
+            s_acc[i] = 0.0;
+        }
+    } else {
+        for (int i = threadIdx.x; i < W; i += blockDim.x) {
+            const int g = wrap_cell(i - H, A.M);
+            const int gm = g == 0 ? A.M - 1 : g - 1;
+            // the differences of a are formed from the coefficients as staged (rounded
+            // to R), so that the path mean of dA/dx times (x1 - x0) equals A(x1) - A(x0)
+            // of the staged field: the discrete gradient of the A-term stays exact for
+            // the field the markers see
+            const R ay = (R)(A.ay[g] * inv_fact), aym = (R)(A.ay[gm] * inv_fact);
+            const R az = (R)(A.az[g] * inv_fact), azm = (R)(A.az[gm] * inv_fact);
+            F.store(i, ay, az, A.ebar[g] * A.dx / S1, (double)(ay - aym), (double)(az - azm));
+            s_acc[i] = 0.0;
+        }
     }
     __syncthreads();
 
@@ -544,7 +559,20 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
         for (long long i = 0; i < ntile && i < NS; ++i) issue(i);
     // scaled basis K! N^K: coefficients staged as a / K!, deposits flushed times w / K!
     const double inv_fact = 1.0 / (double)Fact<K>::v;
-    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    if constexpr (Real<R>::fp32) {
+        if (A.img.an) {
+            // float images built on the grid side (same values as the branch below)
+            for (int i = threadIdx.x; i < W; i += blockDim.x) {
+                const int g = wrap_cell(i - H, A.M);
+                s_an[i] = A.img.an[g];
+                s_ak[i] = A.img.ak[g];
+                s_lo[i] = A.img.lo[g];
+                s_sy[i] = 0.0;
+                s_sz[i] = 0.0;
+            }
+        }
+    }
+    for (int i = threadIdx.x; i < W && !(Real<R>::fp32 && A.img.an); i += blockDim.x) {
         const int g = wrap_cell(i - H, A.M);
         const double ny = A.an_y[g] * inv_fact, nz = A.an_z[g] * inv_fact;
         const double ky = A.ak_y[g] * inv_fact, kz = A.ak_z[g] * inv_fact;
