@@ -39,6 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2203_06513_gb300 import inputs as I  # noqa: E402
+from paper_2203_06513_gb300 import replicas as R  # noqa: E402
 
 METRIC = "particle-steps/s at rel. energy err ≤1e-10: FP32+learned vs plain FP64"
 UNIT = "particle-steps/s"
@@ -144,13 +145,6 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
-
-
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
 
 
 def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=None):
@@ -312,12 +306,12 @@ def main():
     ap.add_argument("--ensemble-host-loop", action="store_true",
                     help="drive the ensemble's loops from the host (same kernels, no graph; for profiling)")
     args = ap.parse_args()
-    ws, rank, local = dist_env()
+    ws, rank, local = R.dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
     ens_in = None
     if args.ensemble_runs > 0:          # host inputs first: the pool starts before any CUDA call
-        ens_in = ensemble_inputs(args.ensemble_runs, args.ensemble_scale, seed=rank)
+        ens_in = ensemble_inputs(args.ensemble_runs, args.ensemble_scale, seed=R.replica_seed(0, rank))
 
     import torch
     from paper_2203_06513_gb300 import pic
@@ -325,7 +319,7 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    kw = {"seed": rank}
+    kw = {"seed": R.replica_seed(0, rank)}
     if args.np:
         kw["np"] = int(args.np)
     w = I.workload(WORKLOAD, **kw)
@@ -339,16 +333,10 @@ def main():
         mlp = pic.Mlp(d["norm"], d["params"], stream=stream.cuda_stream)
 
     def barrier():
-        torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
+        R.barrier(ws, torch.cuda.synchronize)
 
     def max_over_ranks(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return R.max_over_ranks(v, ws, device="cuda")
 
     head_warm = pic.PIC_WARM_MLP if mlp is not None else pic.PIC_WARM_EXPLICIT
     clocks = ClockSampler(local)
@@ -380,10 +368,9 @@ def main():
     ms_expl = max_over_ranks(r_expl["ms"])
     ms64 = max_over_ranks(r64["ms"])
     e2e_s = max_over_ranks(e2e["s"]) if e2e else None
-    total_np = w.np * ws
-    value = total_np * args.steps / (ms_head / 1e3)
-    v_expl = total_np * args.steps / (ms_expl / 1e3)
-    v64 = total_np * k64 / (ms64 / 1e3)
+    value = R.whole_job_rate(w.np, ws, args.steps, ms_head / 1e3)
+    v_expl = R.whole_job_rate(w.np, ws, args.steps, ms_expl / 1e3)
+    v64 = R.whole_job_rate(w.np, ws, k64, ms64 / 1e3)
     tr = r_head["timing"]
     hbm, tflops, peak_kind = peaks()
     kernels = kernel_rooflines(tr, w.np, hbm, tflops, peak_kind)
@@ -427,7 +414,7 @@ def main():
             "cpu_baseline": cpu,
             "ensemble": ens,
             "e2e": None if e2e is None else {
-                "value": total_np * args.steps / e2e_s, "unit": UNIT,
+                "value": R.whole_job_rate(w.np, ws, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d"] / args.steps,
                 "d2h_bytes_per_step": e2e["d2h"] / args.steps},
         }
