@@ -62,15 +62,17 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 // their bf16 roundings and returned packed: the result is a bf16 activation of
 // the next layer either way, and one tanh.approx.bf16x2 serves both values.
 struct GeluConsts {
-    __nv_bfloat162 c0, c1, half;    // sqrt(2/pi), sqrt(2/pi) 0.044715, 1/2
+    __nv_bfloat162 c0, c1;          // sqrt(2/pi), sqrt(2/pi) 0.044715
     __device__ __forceinline__ GeluConsts()
-        : c0(__float2bfloat162_rn(0.7978845608028654f)),
-          c1(__float2bfloat162_rn(0.7978845608028654f * 0.044715f)), half(__float2bfloat162_rn(0.5f))
+        : c0(__float2bfloat162_rn(0.7978845608028654f)), c1(__float2bfloat162_rn(0.7978845608028654f * 0.044715f))
     {
     }
 };
 
-__device__ __forceinline__ uint32_t gelu_bf16x2(float z0, float z1, const GeluConsts &k)
+// Twice the tanh-form GELU of a pair, z (1 + tanh u): the factor 1/2 is folded
+// into the next layer's weights (staged halved, exact in bf16), which saves one
+// packed multiply a pair.
+__device__ __forceinline__ uint32_t gelu2_bf16x2(float z0, float z1, const GeluConsts &k)
 {
     const __nv_bfloat162 z = __floats2bfloat162_rn(z0, z1);
     const __nv_bfloat162 u = __hmul2(z, __hfma2(__hmul2(z, z), k.c1, k.c0));   // c0 z + c1 z^3
@@ -79,7 +81,7 @@ __device__ __forceinline__ uint32_t gelu_bf16x2(float z0, float z1, const GeluCo
     asm("tanh.approx.bf16x2 %0, %1;" : "=r"(ti) : "r"(ui));
     __nv_bfloat162 th;
     memcpy(&th, &ti, 4);
-    const __nv_bfloat162 out = __hmul2(z, __hfma2(th, k.half, k.half));       // z (1 + tanh u) / 2
+    const __nv_bfloat162 out = __hfma2(z, th, z);                              // z (1 + tanh u)
     uint32_t o;
     memcpy(&o, &out, 4);
     return o;
@@ -226,14 +228,15 @@ __device__ void stage_umma(MlpUmma &S, const float *params, const float *norm)
         const int r = i >> 4, k = i & 15;
         put_bf16(S.ONES, kmaj_off(r, k, 16), k == 0 ? 1.f : 0.f);
     }
+    // the layers after a GELU take its doubled output: their weights are halved
     for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
         const int n = i >> 6, k = i & 63;
-        put_bf16(S.W2, kmaj_off(n, k, 64), params[kOffW2 + n * kHid + k]);
-        put_bf16(S.W3, kmaj_off(n, k, 64), params[kOffW3 + n * kHid + k]);
+        put_bf16(S.W2, kmaj_off(n, k, 64), 0.5f * params[kOffW2 + n * kHid + k]);
+        put_bf16(S.W3, kmaj_off(n, k, 64), 0.5f * params[kOffW3 + n * kHid + k]);
     }
     for (int i = threadIdx.x; i < kOutN * 64; i += blockDim.x) {
         const int n = i >> 6, k = i & 63;
-        put_bf16(S.W4, kmaj_off(n, k, 64), n < kOut ? params[kOffW4 + n * kHid + k] : 0.f);
+        put_bf16(S.W4, kmaj_off(n, k, 64), n < kOut ? 0.5f * params[kOffW4 + n * kHid + k] : 0.f);
     }
     if (threadIdx.x < kOut) S.b4[threadIdx.x] = params[kOffB4 + threadIdx.x];
     if (threadIdx.x < kNorm) S.norm[threadIdx.x] = norm[threadIdx.x];
@@ -325,8 +328,8 @@ __device__ __forceinline__ bool umma_layer(MlpUmma &S, int g, int r, const __nv_
     return ok;
 }
 
-// GELU of this thread's accumulator row (the chain's 64 columns, bias included)
-// into its row of the next layer's operand.  Warp w reads tensor-memory lanes
+// Doubled GELU of this thread's accumulator row (the chain's 64 columns, bias
+// included) into its row of the next layer's operand.  Warp w reads tensor-memory lanes
 // 32 (w % 4) .. + 31.
 __device__ __forceinline__ void umma_epilogue(MlpUmma &S, int g, int r)
 {
@@ -341,10 +344,10 @@ __device__ __forceinline__ void umma_epilogue(MlpUmma &S, int g, int r)
         for (int c = 0; c < 4; ++c) {      // 8 columns = one 16-byte chunk of the row
             uint4 o;
             const int k0 = 32 * h + 8 * c;
-            o.x = gelu_bf16x2(v[8 * c + 0], v[8 * c + 1], k);
-            o.y = gelu_bf16x2(v[8 * c + 2], v[8 * c + 3], k);
-            o.z = gelu_bf16x2(v[8 * c + 4], v[8 * c + 5], k);
-            o.w = gelu_bf16x2(v[8 * c + 6], v[8 * c + 7], k);
+            o.x = gelu2_bf16x2(v[8 * c + 0], v[8 * c + 1], k);
+            o.y = gelu2_bf16x2(v[8 * c + 2], v[8 * c + 3], k);
+            o.z = gelu2_bf16x2(v[8 * c + 4], v[8 * c + 5], k);
+            o.w = gelu2_bf16x2(v[8 * c + 6], v[8 * c + 7], k);
             *reinterpret_cast<uint4 *>(row + kmaj_off(r, k0, 64)) = o;
         }
     }

@@ -1001,15 +1001,20 @@ __device__ __forceinline__ int sort_key(int c, R p, float tau)
     return c * kVelBins + b;
 }
 
+// Both passes give each block a contiguous chunk of the markers.  The markers are
+// nearly sorted (they were sorted a few steps ago), so the blocks running at the
+// same time then touch different keys' counters; in a grid-stride order every
+// block would work on the same few cells at once and serialise on their counters.
 template <typename R>
 __global__ void __launch_bounds__(256) k_hist(long long np, float tau, PartPtrs S, int32_t *counts)
 {
     const R *ps = static_cast<const R *>(S.p);
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long beg, end;
+    block_chunk(np, beg, end);
     const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+    for (long long base = beg; base < end; base += blockDim.x) {
         const long long a = base + threadIdx.x;
-        const bool act = a < np;
+        const bool act = a < end;
         const int key = act ? sort_key(S.cell[a], ps[a], tau) : -1;
         const unsigned grp = __match_any_sync(0xffffffffu, key);
         if (act && lane == __ffs(grp) - 1) atomicAdd(&counts[key], __popc(grp));
@@ -1046,11 +1051,12 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, float tau, PartPt
     R *pd = static_cast<R *>(D.p);
     R *pnd = static_cast<R *>(D.pnew);
     R *dd = static_cast<R *>(D.delta);
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long beg, end;
+    block_chunk(np, beg, end);
     const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+    for (long long base = beg; base < end; base += blockDim.x) {
         const long long a = base + threadIdx.x;
-        const bool act = a < np;
+        const bool act = a < end;
         const int c = act ? S.cell[a] : 0;
         const R p = act ? ps[a] : R(0);
         const int key = act ? sort_key(c, p, tau) : -1;
