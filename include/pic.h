@@ -136,6 +136,10 @@ int pic_gather(pic_handle *h, int32_t field, double *out);
  * global e_x update per sweep; PIC_SUBSYSTEM_II: fixed point for
  * (e_y, e_z, a_y, a_z) with the exact solve of (M0 + dt^2/4 G^T M1 G).
  * *iters (may be NULL) receives the number of particle sweeps.
+ * Starting fields: subsystem I starts from e_x^n; subsystem II from e_y^n,
+ * e_z^n extrapolated in time by the polynomial through the states after the
+ * handle's last (up to three) subsystem-II solves.  The fixed point does not
+ * depend on the start, only the sweep count does.
  * PIC_ERR_NOCONVERGE when max_iter sweeps did not reach the tolerance (the
  * state is then the last iterate). */
 int pic_substep(pic_handle *h, int32_t which, int32_t *iters);

@@ -86,7 +86,7 @@ static void release(pic_handle *h)
 {
     auto f = [](void *p) { if (p) cudaFree(p); };
     for (int b = 0; b < 2; ++b) {
-        f(h->P[b].cell); f(h->P[b].t); f(h->P[b].p); f(h->P[b].id);
+        f(h->Pblk[b]);
         f(h->jb[b]); f(h->sy[b]); f(h->sz[b]);
     }
     f(h->delta); f(h->pnew);
@@ -98,6 +98,7 @@ static void release(pic_handle *h)
     f(h->counts);
     f(h->ctrl);
     f(h->img.a); f(h->img.f); f(h->img.an); f(h->img.ak); f(h->img.lo);
+    for (int m = 0; m < kMaxStartOrder; ++m) { f(h->fh.x[m]); f(h->fh.y[m]); f(h->fh.z[m]); }
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -144,6 +145,21 @@ static int read_ctrl(pic_handle *h)
 
 static int particle_grid(pic_handle *h) { return h->num_sms * 4; }
 
+static size_t a256(size_t bytes) { return (bytes + 255) & ~size_t(255); }
+
+// Two double arrays of N_p entries in marker copy b (free between sorts): x at
+// the block's start, p after it.
+static void stage_doubles(pic_handle *h, int b, double **x, double **p)
+{
+    char *base = h->Pblk[b];
+    if (x) *x = reinterpret_cast<double *>(base);
+    if (p) *p = reinterpret_cast<double *>(base + a256((size_t)h->np * sizeof(double)));
+}
+
+// degree of the time extrapolation that starts each subsystem's fixed point
+constexpr int kStartOrder1 = 0;
+constexpr int kStartOrder2 = 3;
+
 // ------------------------------------------------------------------ sort
 static int sort_markers(pic_handle *h)
 {
@@ -161,6 +177,23 @@ static int sort_markers(pic_handle *h)
 
 int pic::handle_sort(pic_handle *h) { return sort_markers(h); }
 PartPtrs pic::handle_parts(pic_handle *h) { return cur_parts(h); }
+
+pic::RunDesc pic::handle_desc(pic_handle *h)
+{
+    RunDesc d{};
+    d.M = h->M; d.K = h->K; d.fp32 = h->fp32; d.np = h->np; d.dx = h->dx; d.dt = h->cfg.dt;
+    d.P = cur_parts(h);
+    d.ex = h->ex; d.ek = h->ek; d.ebar = h->ebar; d.ay = h->ay; d.az = h->az;
+    d.ga_y = h->ga_y; d.ga_z = h->ga_z; d.j0 = h->jb[0]; d.j1 = h->jb[1];
+    d.rowPm = h->d_rowPm; d.rowK = h->d_rowK;
+    d.ey = h->ey; d.ez = h->ez; d.by = h->by; d.bz = h->bz;
+    d.eky = h->eky; d.ekz = h->ekz; d.aky = h->aky; d.akz = h->akz;
+    d.sy0 = h->sy[0]; d.sz0 = h->sz[0]; d.sy1 = h->sy[1]; d.sz1 = h->sz[1];
+    d.ctrl = h->ctrl;
+    d.img = h->img;
+    d.fh = h->fh;
+    return d;
+}
 
 // ------------------------------------------------------------------ charge + Poisson
 static int deposit_charge(pic_handle *h, double *out)
@@ -249,11 +282,16 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
     // marker arrays are padded by 64 entries: the sweeps' bulk copies round a
     // tile's byte count up to a multiple of 16 and may read up to 3 entries past N_p
     const size_t npa = np + 64;
+    // each copy: cell, t, p, id back to back, every array 256-byte aligned; at least
+    // 16 bytes a marker, room for the staged (x, p) doubles of a host transfer
+    const size_t off_t = a256(npa * sizeof(int32_t)), off_p = off_t + a256(npa * h->rsize);
+    const size_t off_id = off_p + a256(npa * h->rsize), blk = off_id + a256(npa * sizeof(int32_t));
     for (int b = 0; b < 2; ++b) {
-        if ((rc = dalloc(h, &h->P[b].cell, npa))) return bail(rc);
-        if ((rc = dalloc(h, (char **)&h->P[b].t, npa * h->rsize))) return bail(rc);
-        if ((rc = dalloc(h, (char **)&h->P[b].p, npa * h->rsize))) return bail(rc);
-        if ((rc = dalloc(h, &h->P[b].id, npa))) return bail(rc);
+        if ((rc = dalloc(h, &h->Pblk[b], blk))) return bail(rc);
+        h->P[b].cell = reinterpret_cast<int32_t *>(h->Pblk[b]);
+        h->P[b].t = h->Pblk[b] + off_t;
+        h->P[b].p = h->Pblk[b] + off_p;
+        h->P[b].id = reinterpret_cast<int32_t *>(h->Pblk[b] + off_id);
         if ((rc = dalloc(h, &h->jb[b], M))) return bail(rc);
         if ((rc = dalloc(h, &h->sy[b], M))) return bail(rc);
         if ((rc = dalloc(h, &h->sz[b], M))) return bail(rc);
@@ -265,6 +303,20 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
                               &h->r0y, &h->r0z, &h->rho, &h->work};
     for (double **a : grid_arrays)
         if ((rc = dalloc(h, a, M))) return bail(rc);
+    // starting fields: subsystem I from e_x^n (its changes are dominated by marker
+    // noise, which no extrapolation predicts); subsystem II cubic in time (the
+    // transverse fields are smooth waves)
+    h->fh.order1 = kStartOrder1;
+    h->fh.order2 = kStartOrder2;
+    for (int m = 0; m < kMaxStartOrder; ++m) {
+        double **arr[] = {&h->fh.x[m], &h->fh.y[m], &h->fh.z[m]};
+        const int order[] = {h->fh.order1, h->fh.order2, h->fh.order2};
+        for (int c = 0; c < 3; ++c) {
+            if (m >= order[c]) continue;
+            if ((rc = dalloc(h, arr[c], M))) return bail(rc);
+            if (cudaMemsetAsync(*arr[c], 0, sizeof(double) * M, h->stream) != cudaSuccess) return bail(PIC_ERR_CUDA);
+        }
+    }
     if ((rc = dalloc(h, &h->diag, 8))) return bail(rc);
     if (h->fp32) {
         if ((rc = dalloc(h, &h->img.a, M)) || (rc = dalloc(h, &h->img.f, M)) || (rc = dalloc(h, &h->img.an, M)) ||
@@ -345,8 +397,8 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
         double *dx_in = nullptr, *dp_in = nullptr;
         const bool host = mem == PIC_MEM_HOST;
         if (host) {
-            if ((rc = dalloc(h, &dx_in, np))) return bail(rc);
-            if ((rc = dalloc(h, &dp_in, np))) { cudaFree(dx_in); return bail(rc); }
+            // staged in the second marker copy, which the first sort overwrites
+            stage_doubles(h, 1, &dx_in, &dp_in);
             cudaMemcpyAsync(dx_in, in->x, np * sizeof(double), cudaMemcpyHostToDevice, h->stream);
             cudaMemcpyAsync(dp_in, in->p, np * sizeof(double), cudaMemcpyHostToDevice, h->stream);
         }
@@ -363,12 +415,6 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
         launch_load(h->fp32, h->np, h->M, dx, host ? dx_in : in->x, host ? dp_in : in->p, P0,
                     particle_grid(h), 256, h->stream);
         cudaError_t e = cudaGetLastError();
-        cudaError_t e2 = cudaStreamSynchronize(h->stream);
-        if (host) {
-            cudaFree(dx_in);
-            cudaFree(dp_in);
-        }
-        if (e == cudaSuccess) e = e2;
         if (e != cudaSuccess)
             return bail(fail(h, PIC_ERR_CUDA, "input copies / load: %s", cudaGetErrorString(e)));
     }
@@ -415,8 +461,8 @@ static int timed_end(pic_handle *h, double *acc, long long *cnt)
 static int substep1(pic_handle *h, int *iters)
 {
     int rc;
-    launch_prep1(h->M, h->dx, h->ex, h->ek, h->ebar, h->ay, h->az, h->ga_y, h->ga_z, h->jb[0],
-                 h->jb[1], h->ctrl, h->img, h->stream);
+    const RunDesc desc = handle_desc(h);
+    launch_prep1(desc, h->stream);
     CKL_N("launch_prep1");
     Sweep1Args a{};
     a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.np = h->np;
@@ -471,17 +517,16 @@ static int substep1(pic_handle *h, int *iters)
     if ((rc = check_status(h, 1))) return rc;
     launch_finalize1(h->fp32, h->np, h->M, cur_parts(h), particle_grid(h), 256, h->stream);
     CKL_N("launch_finalize1");
-    launch_copy(h->M, h->ek, h->ex, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, h->stream);
-    CKL_N("launch_copy");
+    launch_commit(desc, 1, h->stream);
+    CKL_N("launch_commit");
     return PIC_OK;
 }
 
 static int substep2(pic_handle *h, int *iters)
 {
     int rc;
-    launch_prep2(h->M, h->K, h->cfg.dt, h->d_rowPm, h->d_rowK, h->ey, h->ez, h->ay, h->az, h->by,
-                 h->bz, h->eky, h->ekz, h->aky, h->akz, h->sy[0], h->sz[0], h->sy[1], h->sz[1],
-                 h->ctrl, h->img, h->stream);
+    const RunDesc desc = handle_desc(h);
+    launch_prep2(desc, h->stream);
     CKL_N("launch_prep2");
     if ((rc = conv_plain(h, h->d_tapP, h->tapP_start, h->tapP_n, h->by, h->r0y, h->bz, h->r0z))) return rc;
     Sweep2Args a{};
@@ -523,8 +568,8 @@ static int substep2(pic_handle *h, int *iters)
     if (iters) *iters = it;
     if ((rc = check_status(h, 2))) return rc;
     // a^{n+1} = a^n - dt/2 (e^n + e^{n+1}) is the last a^(k); e^{n+1} the last e^(k)
-    launch_copy(h->M, h->eky, h->ey, h->ekz, h->ez, h->aky, h->ay, h->akz, h->az, h->stream);
-    CKL_N("launch_copy");
+    launch_commit(desc, 2, h->stream);
+    CKL_N("launch_commit");
     return PIC_OK;
 }
 
@@ -599,24 +644,16 @@ extern "C" int pic_get_state(pic_handle *h, const pic_arrays *o, int32_t mem)
     int rc = PIC_OK;
     if (o->x || o->p) {
         double *dx_out = o->x, *dp_out = o->p;
-        double *tx = nullptr, *tp = nullptr;
-        if (host) {
-            if (o->x && (rc = dalloc(h, &tx, np))) return rc;
-            if (o->p && (rc = dalloc(h, &tp, np))) { if (tx) cudaFree(tx); return rc; }
-            dx_out = tx;
-            dp_out = tp;
-        }
+        if (host) stage_doubles(h, 1 - h->cur, o->x ? &dx_out : nullptr, o->p ? &dp_out : nullptr);
         launch_store(h->fp32, h->np, h->dx, cur_parts(h), dx_out, dp_out, particle_grid(h), 256, h->stream);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess && host) {
-            if (o->x) e = cudaMemcpyAsync(o->x, tx, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (o->x) e = cudaMemcpyAsync(o->x, dx_out, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
             if (e == cudaSuccess && o->p)
-                e = cudaMemcpyAsync(o->p, tp, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+                e = cudaMemcpyAsync(o->p, dp_out, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
             cudaError_t e2 = cudaStreamSynchronize(h->stream);
             if (e == cudaSuccess) e = e2;
         }
-        if (tx) cudaFree(tx);
-        if (tp) cudaFree(tp);
         if (e != cudaSuccess) return fail(h, PIC_ERR_CUDA, "get_state: %s", cudaGetErrorString(e));
         ++h->launches;
     }

@@ -28,6 +28,7 @@ struct DevCtrl {
     int converged;                     // 1 once the test passed
     int status;                        // error bits, see STATUS_*
     unsigned int ticket;               // last-block election in multi-block grid kernels
+    int hist1, hist2;                  // field changes stored for the starting fields
     double acc[4];                     // reductions for diagnostics (energy, residual)
 };
 

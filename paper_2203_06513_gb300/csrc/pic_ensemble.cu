@@ -109,18 +109,7 @@ static void build_tables(pic_ensemble *e)
         pic_handle *h = e->runs[r];
         const PartPtrs P = handle_parts(h);
 
-        RunDesc &d = e->desc[r];
-        d = RunDesc{};
-        d.M = h->M; d.K = h->K; d.fp32 = h->fp32; d.np = h->np; d.dx = h->dx; d.dt = h->cfg.dt;
-        d.P = P;
-        d.ex = h->ex; d.ek = h->ek; d.ebar = h->ebar; d.ay = h->ay; d.az = h->az;
-        d.ga_y = h->ga_y; d.ga_z = h->ga_z; d.j0 = h->jb[0]; d.j1 = h->jb[1];
-        d.rowPm = h->d_rowPm; d.rowK = h->d_rowK;
-        d.ey = h->ey; d.ez = h->ez; d.by = h->by; d.bz = h->bz;
-        d.eky = h->eky; d.ekz = h->ekz; d.aky = h->aky; d.akz = h->akz;
-        d.sy0 = h->sy[0]; d.sz0 = h->sz[0]; d.sy1 = h->sy[1]; d.sz1 = h->sz[1];
-        d.ctrl = h->ctrl;
-        d.img = h->img;
+        e->desc[r] = handle_desc(h);
 
         Sweep1Args &a = e->a1[r];
         a = Sweep1Args{};
@@ -235,7 +224,7 @@ static int seg_prep1(pic_ensemble *e, cudaStream_t s)
 static int seg_mid(pic_ensemble *e, cudaStream_t s)
 {
     ELAUNCH(launch_finalize1_ens(e->fp32, e->d_desc, e->nruns, e->fin_grid, s), "ensemble finalize I");
-    ELAUNCH(launch_copy_ens(e->d_desc, e->nruns, e->Mmax, 1, s), "ensemble copy I");
+    ELAUNCH(launch_commit_ens(e->d_desc, e->nruns, e->Mmax, 1, s), "ensemble commit I");
     ELAUNCH(launch_prep2_ens(e->d_desc, e->nruns, e->Mmax, s), "ensemble prep II");
     ELAUNCH(launch_conv_ens(e->d_cp, e->nruns, e->Mmax, 2, e->ntap2, e->d_q, e->d_sweeps, 0ull, s),
             "ensemble P solve");
@@ -244,7 +233,7 @@ static int seg_mid(pic_ensemble *e, cudaStream_t s)
 
 static int seg_end(pic_ensemble *e, cudaStream_t s)
 {
-    ELAUNCH(launch_copy_ens(e->d_desc, e->nruns, e->Mmax, 2, s), "ensemble copy II");
+    ELAUNCH(launch_commit_ens(e->d_desc, e->nruns, e->Mmax, 2, s), "ensemble commit II");
     return PIC_OK;
 }
 

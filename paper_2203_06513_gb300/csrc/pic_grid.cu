@@ -350,10 +350,8 @@ int launch_conv(const ConvArgs &a, cudaStream_t s)
     return 0;
 }
 
-// ---------------------------------------------------------------------------
-// Subsystem I preparation: (G a)_i = (a_i - a_{i-1}) / dx, e^(0) = e^n,
-// ebar = e^n, cleared deposit buffers, reset control block.
-// ---------------------------------------------------------------------------
+// Control block at the start of a fixed-point loop (the error bits and the field
+// history counts stay).
 __device__ __forceinline__ void ctrl_loop_reset(DevCtrl *ctrl)
 {
     ctrl->dmax_bits = 0ull;
@@ -366,36 +364,49 @@ __device__ __forceinline__ void ctrl_loop_reset(DevCtrl *ctrl)
     ctrl->ticket = 0u;
 }
 
-__device__ __forceinline__ void prep1_at(int i, int M, double dx, const double *ex, double *ek,
-                                         double *ebar, const double *ay, const double *az,
-                                         double *gay, double *gaz, double *j0, double *j1, DevCtrl *ctrl,
-                                         const StageImages &img)
+// Starting field of a fixed-point iteration.  The fixed point does not depend on
+// it, only the number of sweeps to reach it does: e^n extrapolated in time by the
+// polynomial through the last q + 1 states, q = min(stored changes, order):
+// e^n, e^n + d0, e^n + 2 d0 - d1, e^n + 3 d0 - 3 d1 + d2.
+__device__ __forceinline__ double start_field(double e, double *const d[kMaxStartOrder], int i, int q)
 {
-    if (i < M && img.a) image1_at(i, M, ay, az, ex[i], img);
-    if (i < M) {
-        const int im = (i == 0) ? M - 1 : i - 1;
-        gay[i] = (ay[i] - ay[im]) / dx;
-        gaz[i] = (az[i] - az[im]) / dx;
-        ek[i] = ex[i];
-        ebar[i] = ex[i];
-        j0[i] = 0.0;
-        j1[i] = 0.0;
+    switch (q) {
+    case 0: return e;
+    case 1: return e + d[0][i];
+    case 2: return e + (2.0 * d[0][i] - d[1][i]);
+    default: return e + (3.0 * (d[0][i] - d[1][i]) + d[2][i]);
     }
-    if (i == 0) ctrl_loop_reset(ctrl);
 }
 
-__global__ void k_prep1(int M, double dx, const double *ex, double *ek, double *ebar,
-                        const double *ay, const double *az, double *gay, double *gaz,
-                        double *j0, double *j1, DevCtrl *ctrl, StageImages img)
+// ---------------------------------------------------------------------------
+// Subsystem I preparation: e^(0), ebar^(0) = (e^n + e^(0)) / 2, the gradients
+// (G a)_i = (a_i - a_{i-1}) / dx, cleared deposits, the float images, the
+// control block reset for the loop.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void prep1_at(int i, const RunDesc &R)
 {
-    prep1_at(blockIdx.x * blockDim.x + threadIdx.x, M, dx, ex, ek, ebar, ay, az, gay, gaz, j0, j1, ctrl, img);
+    const int M = R.M;
+    const int q = min(R.ctrl->hist1, R.fh.order1);    // hist1: written only by the commit kernel
+    if (i < M) {
+        const double e0 = start_field(R.ex[i], R.fh.x, i, q);
+        const double eb = 0.5 * (R.ex[i] + e0);
+        if (R.img.a) image1_at(i, M, R.ay, R.az, eb, R.img);
+        const int im = (i == 0) ? M - 1 : i - 1;
+        R.ga_y[i] = (R.ay[i] - R.ay[im]) / R.dx;
+        R.ga_z[i] = (R.az[i] - R.az[im]) / R.dx;
+        R.ek[i] = e0;
+        R.ebar[i] = eb;
+        R.j0[i] = 0.0;
+        R.j1[i] = 0.0;
+    }
+    if (i == 0) ctrl_loop_reset(R.ctrl);
 }
+
+__global__ void k_prep1(RunDesc R) { prep1_at(blockIdx.x * blockDim.x + threadIdx.x, R); }
 
 __global__ void k_prep1_ens(const RunDesc *runs)
 {
-    const RunDesc &R = runs[blockIdx.y];
-    prep1_at(blockIdx.x * blockDim.x + threadIdx.x, R.M, R.dx, R.ex, R.ek, R.ebar, R.ay, R.az, R.ga_y,
-             R.ga_z, R.j0, R.j1, R.ctrl, R.img);
+    prep1_at(blockIdx.x * blockDim.x + threadIdx.x, runs[blockIdx.y]);
 }
 
 int launch_prep1_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
@@ -404,64 +415,55 @@ int launch_prep1_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
     return 0;
 }
 
-int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, const double *ay,
-                 const double *az, double *ga_y, double *ga_z, double *j0, double *j1,
-                 DevCtrl *ctrl, const StageImages &img, cudaStream_t s)
+int launch_prep1(const RunDesc &R, cudaStream_t s)
 {
-    k_prep1<<<(M + 255) / 256, 256, 0, s>>>(M, dx, ex, ek, ebar, ay, az, ga_y, ga_z, j0, j1, ctrl, img);
+    k_prep1<<<(R.M + 255) / 256, 256, 0, s>>>(R);
     return 0;
 }
 
 // ---------------------------------------------------------------------------
 // Subsystem II preparation: b = (M0 - dt^2/4 K) e^n + dt K a^n (banded
-// circulant products), e^(0) = e^n, a^(0) = a^n - dt e^n, cleared deposits.
+// circulant products), e^(0), a^(0) = a^n - dt/2 (e^n + e^(0)), cleared
+// deposits, the float images, the control block reset for the loop.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void prep2_at(int i, int M, int K, double dt, const double *rowPm,
-                                         const double *rowK, const double *ey, const double *ez,
-                                         const double *ay, const double *az, double *by, double *bz,
-                                         double *eky, double *ekz, double *aky, double *akz, double *s00,
-                                         double *s01, double *s10, double *s11, DevCtrl *ctrl,
-                                         const StageImages &img)
+__device__ __forceinline__ void prep2_at(int i, const RunDesc &R)
 {
-    if (i < M && img.an) {
-        const double y0 = ay[i] - dt * ey[i], z0 = az[i] - dt * ez[i];     // a^(0), as below
-        img.an[i] = make_float2((float)(ay[i] * img.inv_fact), (float)(az[i] * img.inv_fact));
-        image2_at(i, 0, ay[i], y0, img);
-        image2_at(i, 1, az[i], z0, img);
-    }
+    const int M = R.M, K = R.K;
+    const double dt = R.dt;
+    const int q = min(R.ctrl->hist2, R.fh.order2);    // hist2: written only by the commit kernel
     if (i < M) {
-        double vy = rowPm[0] * ey[i] + dt * rowK[0] * ay[i];
-        double vz = rowPm[0] * ez[i] + dt * rowK[0] * az[i];
+        const double *ey = R.ey, *ez = R.ez, *ay = R.ay, *az = R.az;
+        const double ey0 = start_field(ey[i], R.fh.y, i, q);
+        const double ez0 = start_field(ez[i], R.fh.z, i, q);
+        const double ay0 = ay[i] - 0.5 * dt * (ey[i] + ey0), az0 = az[i] - 0.5 * dt * (ez[i] + ez0);
+        if (R.img.an) {
+            R.img.an[i] = make_float2((float)(ay[i] * R.img.inv_fact), (float)(az[i] * R.img.inv_fact));
+            image2_at(i, 0, ay[i], ay0, R.img);
+            image2_at(i, 1, az[i], az0, R.img);
+        }
+        double vy = R.rowPm[0] * ey[i] + dt * R.rowK[0] * ay[i];
+        double vz = R.rowPm[0] * ez[i] + dt * R.rowK[0] * az[i];
         for (int d = 1; d <= K; ++d) {
             const int ip = (i + d) % M, im = (i - d + M) % M;
-            vy += rowPm[d] * (ey[ip] + ey[im]) + dt * rowK[d] * (ay[ip] + ay[im]);
-            vz += rowPm[d] * (ez[ip] + ez[im]) + dt * rowK[d] * (az[ip] + az[im]);
+            vy += R.rowPm[d] * (ey[ip] + ey[im]) + dt * R.rowK[d] * (ay[ip] + ay[im]);
+            vz += R.rowPm[d] * (ez[ip] + ez[im]) + dt * R.rowK[d] * (az[ip] + az[im]);
         }
-        by[i] = vy;
-        bz[i] = vz;
-        eky[i] = ey[i];
-        ekz[i] = ez[i];
-        aky[i] = ay[i] - dt * ey[i];
-        akz[i] = az[i] - dt * ez[i];
-        s00[i] = 0.0; s01[i] = 0.0; s10[i] = 0.0; s11[i] = 0.0;
+        R.by[i] = vy;
+        R.bz[i] = vz;
+        R.eky[i] = ey0;
+        R.ekz[i] = ez0;
+        R.aky[i] = ay0;
+        R.akz[i] = az0;
+        R.sy0[i] = 0.0; R.sz0[i] = 0.0; R.sy1[i] = 0.0; R.sz1[i] = 0.0;
     }
-    if (i == 0) ctrl_loop_reset(ctrl);
+    if (i == 0) ctrl_loop_reset(R.ctrl);
 }
 
-__global__ void k_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
-                        const double *ey, const double *ez, const double *ay, const double *az,
-                        double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
-                        double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl, StageImages img)
-{
-    prep2_at(blockIdx.x * blockDim.x + threadIdx.x, M, K, dt, rowPm, rowK, ey, ez, ay, az, by, bz, eky,
-             ekz, aky, akz, s00, s01, s10, s11, ctrl, img);
-}
+__global__ void k_prep2(RunDesc R) { prep2_at(blockIdx.x * blockDim.x + threadIdx.x, R); }
 
 __global__ void k_prep2_ens(const RunDesc *runs)
 {
-    const RunDesc &R = runs[blockIdx.y];
-    prep2_at(blockIdx.x * blockDim.x + threadIdx.x, R.M, R.K, R.dt, R.rowPm, R.rowK, R.ey, R.ez, R.ay,
-             R.az, R.by, R.bz, R.eky, R.ekz, R.aky, R.akz, R.sy0, R.sz0, R.sy1, R.sz1, R.ctrl, R.img);
+    prep2_at(blockIdx.x * blockDim.x + threadIdx.x, runs[blockIdx.y]);
 }
 
 int launch_prep2_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
@@ -470,56 +472,63 @@ int launch_prep2_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s)
     return 0;
 }
 
-int launch_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
-                 const double *ey, const double *ez, const double *ay, const double *az,
-                 double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
-                 double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl,
-                 const StageImages &img, cudaStream_t s)
+int launch_prep2(const RunDesc &R, cudaStream_t s)
 {
-    k_prep2<<<(M + 255) / 256, 256, 0, s>>>(M, K, dt, rowPm, rowK, ey, ez, ay, az, by, bz, eky, ekz,
-                                            aky, akz, s00, s01, s10, s11, ctrl, img);
+    k_prep2<<<(R.M + 255) / 256, 256, 0, s>>>(R);
     return 0;
 }
 
-__global__ void k_copy4(int M, const double *s0, double *d0, const double *s1, double *d1,
-                        const double *s2, double *d2, const double *s3, double *d3)
+// e^{n+1} = e^(k) replaces e^n; its change enters the history (d[2] = d[1],
+// d[1] = d[0], d[0] = e^{n+1} - e^n), as deep as the extrapolation order needs.
+__device__ __forceinline__ void commit_field(int i, const double *ek, double *e, double *const d[kMaxStartOrder],
+                                             int order)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M) {
-        if (s0) d0[i] = s0[i];
-        if (s1) d1[i] = s1[i];
-        if (s2) d2[i] = s2[i];
-        if (s3) d3[i] = s3[i];
+    const double v = ek[i];
+    for (int m = order - 1; m > 0; --m) d[m][i] = d[m - 1][i];
+    if (order > 0) d[0][i] = v - e[i];
+    e[i] = v;
+}
+
+// End of a substep: I: e_x = e^(k); II: e_perp = e^(k), a_perp = a^(k).  Thread
+// 0 counts the stored changes (up to kMaxStartOrder) for the next preparation.
+__device__ __forceinline__ void commit_at(int i, const RunDesc &R, int which)
+{
+    if (i < R.M) {
+        if (which == 1) {
+            commit_field(i, R.ek, R.ex, R.fh.x, R.fh.order1);
+        } else {
+            commit_field(i, R.eky, R.ey, R.fh.y, R.fh.order2);
+            commit_field(i, R.ekz, R.ez, R.fh.z, R.fh.order2);
+            R.ay[i] = R.aky[i];
+            R.az[i] = R.akz[i];
+        }
+    }
+    if (i == 0) {
+        int *h = which == 1 ? &R.ctrl->hist1 : &R.ctrl->hist2;
+        if (*h < kMaxStartOrder) *h += 1;
     }
 }
 
-int launch_copy(int M, const double *src0, double *dst0, const double *src1, double *dst1,
-                const double *src2, double *dst2, const double *src3, double *dst3, cudaStream_t s)
+__global__ void k_commit(RunDesc R, int which) { commit_at(blockIdx.x * blockDim.x + threadIdx.x, R, which); }
+
+int launch_commit(const RunDesc &R, int which, cudaStream_t s)
 {
-    k_copy4<<<(M + 255) / 256, 256, 0, s>>>(M, src0, dst0, src1, dst1, src2, dst2, src3, dst3);
+    k_commit<<<(R.M + 255) / 256, 256, 0, s>>>(R, which);
     return 0;
 }
 
-// End of a substep for every run of an ensemble: I: e_x = e^(k); II: e_perp =
-// e^(k), a_perp = a^(k).  Runs stopped by an error keep their fields.
-__global__ void k_copy_ens(const RunDesc *runs, int which)
+// The same for every run of an ensemble.  Runs stopped by an error keep their
+// fields and history.
+__global__ void k_commit_ens(const RunDesc *runs, int which)
 {
     const RunDesc &R = runs[blockIdx.y];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= R.M || (R.ctrl->status & (STATUS_NUMERIC | STATUS_TIMEOUT))) return;
-    if (which == 1) {
-        R.ex[i] = R.ek[i];
-    } else {
-        R.ey[i] = R.eky[i];
-        R.ez[i] = R.ekz[i];
-        R.ay[i] = R.aky[i];
-        R.az[i] = R.akz[i];
-    }
+    if (R.ctrl->status & (STATUS_NUMERIC | STATUS_TIMEOUT)) return;
+    commit_at(blockIdx.x * blockDim.x + threadIdx.x, R, which);
 }
 
-int launch_copy_ens(const RunDesc *R, int nruns, int Mmax, int which, cudaStream_t s)
+int launch_commit_ens(const RunDesc *R, int nruns, int Mmax, int which, cudaStream_t s)
 {
-    k_copy_ens<<<dim3((Mmax + 255) / 256, nruns), 256, 0, s>>>(R, which);
+    k_commit_ens<<<dim3((Mmax + 255) / 256, nruns), 256, 0, s>>>(R, which);
     return 0;
 }
 
@@ -682,6 +691,8 @@ __global__ void k_ctrl_reset(DevCtrl *c)
     c->converged = 0;
     c->status = 0;
     c->ticket = 0u;
+    c->hist1 = 0;
+    c->hist2 = 0;
     c->acc[0] = c->acc[1] = c->acc[2] = c->acc[3] = 0.0;
 }
 

@@ -23,6 +23,9 @@ struct pic_handle {
 
     // marker state: two copies of (cell, t, p, id) for the counting sort
     PartPtrs P[2]{};
+    // one device block per copy holds its four arrays; between sorts the copy not
+    // in use (P[1 - cur]) is free, and the host transfers stage doubles in it
+    char *Pblk[2] = {nullptr, nullptr};
     int cur = 0;
     void *delta = nullptr, *pnew = nullptr;
 
@@ -41,6 +44,7 @@ struct pic_handle {
     int tapM1_start = 0, tapM1_n = 0, tapP_start = 0, tapP_n = 0;
 
     StageImages img{};              // float staging images (FP32 form)
+    pic::FieldHist fh{};            // field changes of the last solves (starting fields)
     DevCtrl *ctrl = nullptr;
     int *h_flag = nullptr;          // pinned: converged flag readback
     DevCtrl *h_ctrl = nullptr;      // pinned: full control block readback
@@ -65,4 +69,6 @@ namespace pic {
 // marker sort of one handle (swaps its current buffer); its current marker arrays
 int handle_sort(pic_handle *h);
 PartPtrs handle_parts(pic_handle *h);
+// the grid-side pointers of one handle (preparation and commit kernels)
+RunDesc handle_desc(pic_handle *h);
 }  // namespace pic

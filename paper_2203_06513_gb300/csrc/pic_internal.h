@@ -162,6 +162,16 @@ struct EnsRun {
 };
 
 // per-run pointers of the grid-side kernels
+// Field changes of the last solves of each subsystem (x: subsystem I's e_x; y, z:
+// subsystem II's e_y, e_z): d[0] = e^n - e^{n-1}, d[1] = e^{n-1} - e^{n-2}, ...
+// order1 / order2: the degree of the time extrapolation that starts each
+// subsystem's iteration (0: e^(0) = e^n), at most kMaxStartOrder.
+constexpr int kMaxStartOrder = 3;
+struct FieldHist {
+    double *x[kMaxStartOrder], *y[kMaxStartOrder], *z[kMaxStartOrder];
+    int order1, order2;
+};
+
 struct RunDesc {
     int M, K, fp32;
     long long np;
@@ -172,6 +182,7 @@ struct RunDesc {
     double *ey, *ez, *by, *bz, *eky, *ekz, *aky, *akz, *sy0, *sz0, *sy1, *sz1;
     DevCtrl *ctrl;
     StageImages img;
+    FieldHist fh;
 };
 
 int launch_ens_plan(EnsQueue *Q, const EnsRun *runs, int nruns, unsigned long long cond, cudaStream_t s);
@@ -181,24 +192,19 @@ int launch_conv_ens(const ConvArgs *runs, int nruns, int Mmax, int ncomp, int nt
                     int *sweeps, unsigned long long cond, cudaStream_t s);
 int launch_prep1_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s);
 int launch_prep2_ens(const RunDesc *R, int nruns, int Mmax, cudaStream_t s);
-int launch_copy_ens(const RunDesc *R, int nruns, int Mmax, int which, cudaStream_t s);
+int launch_commit_ens(const RunDesc *R, int nruns, int Mmax, int which, cudaStream_t s);
 int launch_sweep1_ens(int K, int fp32, const Sweep1Args *runs, int nruns, EnsQueue *Q, int grid,
                       size_t smem, cudaStream_t s);
 int launch_sweep2_ens(int K, int fp32, const Sweep2Args *runs, int nruns, EnsQueue *Q, int grid,
                       size_t smem, cudaStream_t s);
 int launch_finalize1_ens(int fp32, const RunDesc *R, int nruns, int grid_x, cudaStream_t s);
-int launch_prep1(int M, double dx, const double *ex, double *ek, double *ebar, const double *ay,
-                 const double *az, double *ga_y, double *ga_z, double *j0, double *j1,
-                 DevCtrl *ctrl, const StageImages &img, cudaStream_t s);
-int launch_prep2(int M, int K, double dt, const double *rowPm, const double *rowK,
-                 const double *ey, const double *ez, const double *ay, const double *az,
-                 double *by, double *bz, double *eky, double *ekz, double *aky, double *akz,
-                 double *s00, double *s01, double *s10, double *s11, DevCtrl *ctrl,
-                 const StageImages &img, cudaStream_t s);
+int launch_prep1(const RunDesc &R, cudaStream_t s);
+int launch_prep2(const RunDesc &R, cudaStream_t s);
+// end of a substep (which = 1, 2): the converged iterate becomes the state, and
+// its change is recorded for the next starting field
+int launch_commit(const RunDesc &R, int which, cudaStream_t s);
 // scale S of the scaled path means of degree d (the sweeps' piece_means_scaled)
 int mean_scale(int d);
-int launch_copy(int M, const double *src0, double *dst0, const double *src1, double *dst1,
-                const double *src2, double *dst2, const double *src3, double *dst3, cudaStream_t s);
 int launch_poisson_rhs(int M, double dx, const double *rho, double *d, cudaStream_t s);
 int launch_energy_grid(int M, int K, double dx, const double *rowM0, const double *rowM1,
                        const double *rowK, const double *ex, const double *ey, const double *ez,

@@ -97,10 +97,12 @@ def test_ensemble_matches_single_runs(precision):
         g = pic.Pic(cfgs[r], x, p, ay, az, ey, ez)
         i1, i2 = g.step(steps)
         compare(ens.run(r).state_numpy(), g.state_numpy(), w.L, tol)
-        # a decision right at the tolerance may flip with the order of atomics (in
-        # float, at the noise floor of the increments: up to once per step)
-        slack = 1 if precision == pic.PIC_FP64 else steps
-        assert abs(sw[r, 0] - i1) <= slack and abs(sw[r, 1] - i2) <= slack
+        # a decision right at the tolerance may flip with the order of atomics.  In
+        # float, runs this small stop at the noise floor of the increments, where
+        # the stagnation test waits for an increment that no longer shrinks, and
+        # which sweep shows one depends on the rounding: up to two sweeps a step.
+        slack = 1 if precision == pic.PIC_FP64 else 2 * steps
+        assert abs(sw[r, 0] - i1) <= slack and abs(sw[r, 1] - i2) <= slack, (r, sw[r], i1, i2)
         g.close()
     ens.close()
 
