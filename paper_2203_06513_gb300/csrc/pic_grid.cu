@@ -6,7 +6,9 @@
 // Solves apply the exact inverse as a circulant convolution: the inverse of a
 // banded SPD circulant has a first row that decays geometrically, so it is
 // truncated where its entries fall below 1e-17 of the largest (or kept whole).
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "pic_internal.h"
@@ -46,41 +48,48 @@ void mass_band(int d, double dx, double *band)
 
 // First row g of the inverse of the symmetric circulant with band c_0..c_bw:
 // eigenvalues lambda_m = c_0 + 2 sum_d c_d cos(2 pi m d / M), g_d = 1/M sum_m
-// cos(2 pi m d / M) / lambda_m, with one step of iterative refinement.
-void inverse_taps(const double *band, int bw, int M, double cut, double *g, int *d_start,
-                  int *ntap, double *taps)
+// cos(2 pi m d / M) / lambda_m, with one step of iterative refinement.  The
+// cosine table is made exactly symmetric (cs[M - j] = cs[j]), so both transforms
+// are symmetric in their output index bit for bit and only the first half is
+// summed; indices m q mod M advance by addition.
+static void inverse_taps_compute(const double *band, int bw, int M, double cut, double *g, int *d_start,
+                                 int *ntap, double *taps)
 {
     const double twopi = 6.283185307179586476925286766559;
     std::vector<double> cs(M), lam(M), r(M), corr(M);
-    for (int m = 0; m < M; ++m) cs[m] = std::cos(twopi * (double)m / (double)M);
+    for (int m = 0; m <= M / 2; ++m) cs[m] = std::cos(twopi * (double)m / (double)M);
+    for (int m = M / 2 + 1; m < M; ++m) cs[m] = cs[M - m];
     for (int m = 0; m < M; ++m) {
         double l = band[0];
         for (int d = 1; d <= bw; ++d) l += 2.0 * band[d] * cs[(long long)m * d % M];
         lam[m] = 1.0 / l;
     }
+    // y_k = sum_j v_j cs[k j mod M] for k = 0 .. M/2, mirrored; four interleaved
+    // compensated partial sums (independent chains), added at the end
+    auto cos_transform = [&](const std::vector<double> &v, std::vector<double> &y) {
+        for (int k = 0; k <= M / 2; ++k) {
+            double s[4] = {0.0, 0.0, 0.0, 0.0}, comp[4] = {0.0, 0.0, 0.0, 0.0};
+            int idx = 0;
+            for (int j = 0; j < M; ++j) {
+                const int l = j & 3;
+                const double t = v[j] * cs[idx] - comp[l];
+                const double tt = s[l] + t;
+                comp[l] = (tt - s[l]) - t;
+                s[l] = tt;
+                idx += k;
+                if (idx >= M) idx -= M;
+            }
+            y[k] = ((s[0] + s[1]) + (s[2] + s[3])) - ((comp[0] + comp[1]) + (comp[2] + comp[3]));
+        }
+        for (int k = M / 2 + 1; k < M; ++k) y[k] = y[M - k];
+    };
     auto apply_inv = [&](const std::vector<double> &rhs_even, std::vector<double> &out) {
         // rhs is symmetric (even) so its DFT is real: R_m = sum_q rhs_q cos(2 pi m q / M)
         std::vector<double> R(M);
-        for (int m = 0; m < M; ++m) {
-            double s = 0.0, comp = 0.0;
-            for (int q = 0; q < M; ++q) {
-                const double y = rhs_even[q] * cs[(long long)m * q % M] - comp;
-                const double tt = s + y;
-                comp = (tt - s) - y;
-                s = tt;
-            }
-            R[m] = s * lam[m];
-        }
-        for (int d = 0; d < M; ++d) {
-            double s = 0.0, comp = 0.0;
-            for (int m = 0; m < M; ++m) {
-                const double y = R[m] * cs[(long long)m * d % M] - comp;
-                const double tt = s + y;
-                comp = (tt - s) - y;
-                s = tt;
-            }
-            out[d] = s / (double)M;
-        }
+        cos_transform(rhs_even, R);
+        for (int m = 0; m < M; ++m) R[m] *= lam[m];
+        cos_transform(R, out);
+        for (int d = 0; d < M; ++d) out[d] /= (double)M;
     };
     std::vector<double> e0(M, 0.0), gv(M);
     e0[0] = 1.0;
@@ -109,6 +118,38 @@ void inverse_taps(const double *band, int bw, int M, double cut, double *g, int 
         *ntap = M;
         for (int n = 0; n < M; ++n) taps[n] = gv[((lo + n) % M + M) % M];
     }
+}
+
+// The taps of one (band, M, cut) are the same for every handle that asks: a
+// process-wide table of the recent ones spares repeated set-ups the O(M^2) work.
+void inverse_taps(const double *band, int bw, int M, double cut, double *g, int *d_start, int *ntap,
+                  double *taps)
+{
+    struct Entry {
+        std::vector<double> key, g, taps;
+        int d_start, ntap;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> table;
+    std::vector<double> key(band, band + bw + 1);
+    key.push_back((double)M);
+    key.push_back(cut);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry &e : table)
+            if (e.key == key) {
+                std::copy(e.g.begin(), e.g.end(), g);
+                std::copy(e.taps.begin(), e.taps.end(), taps);
+                *d_start = e.d_start;
+                *ntap = e.ntap;
+                return;
+            }
+    }
+    inverse_taps_compute(band, bw, M, cut, g, d_start, ntap, taps);
+    std::lock_guard<std::mutex> lock(mu);
+    if (table.size() >= 64) table.clear();
+    table.push_back(Entry{key, std::vector<double>(g, g + M), std::vector<double>(taps, taps + *ntap), *d_start,
+                          *ntap});
 }
 
 // ---------------------------------------------------------------------------
