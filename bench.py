@@ -54,7 +54,11 @@ BYTES_SWEEP2 = 12
 FLOP_MLP = 2 * (6 * 64 + 64 * 64 + 64 * 64 + 64 * 2)
 # DRAM bytes (read + write) per marker from ncu captures of the current kernels on
 # 2e7 markers of the C2 grid (--set full, one launch each); per launch = x N_p.
-NCU_DRAM_PER_MARKER = {"k_sweep1<3,float>": 22.34, "k_sweep2<3,float>": 12.21, "k_warm_mlp<3,float>": None}
+NCU_DRAM_PER_MARKER = {"k_sweep1<3,float>": 22.34, "k_sweep2<3,float>": 12.21, "k_warm_mlp<3,float>": 15.04}
+# Warp instructions x 32 per marker from the same captures: the kernels are bound by
+# instruction issue, which the "issue" entry compares with the issue-slot peak
+# (SMs x 4 schedulers x 1 warp instruction a cycle x the sampled SM clock).
+NCU_INST_PER_MARKER = {"k_sweep1<3,float>": 608, "k_sweep2<3,float>": 292, "k_warm_mlp<3,float>": 1179}
 
 
 def peaks():
@@ -67,7 +71,7 @@ def peaks():
         return 6800.0, 1700.0, "fallback"
 
 
-def kernel_rooflines(tr, np_, hbm, tflops, kind):
+def kernel_rooflines(tr, np_, hbm, tflops, kind, sms=None, sm_mhz=None):
     """Per hot kernel of the timed form: achieved against its roof, from the library's
     CUDA-event timing of each launch."""
     out = []
@@ -85,11 +89,18 @@ def kernel_rooflines(tr, np_, hbm, tflops, kind):
             achieved = unit_amount * np_ / (launch_ms / 1e3) / 1e12
             peak, unit = tflops, "TFLOP/s"
         per_marker = NCU_DRAM_PER_MARKER.get(name)
-        out.append({"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                    "frac": achieved / peak, "peak_kind": kind,
-                    "traffic": None if per_marker is None else per_marker * np_,
-                    "algorithmic_per_launch": unit_amount * np_, "launch_ms": launch_ms,
-                    "launches": n, "share_ms": ms})
+        entry = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                 "frac": achieved / peak, "peak_kind": kind,
+                 "traffic": None if per_marker is None else per_marker * np_,
+                 "algorithmic_per_launch": unit_amount * np_, "launch_ms": launch_ms,
+                 "launches": n, "share_ms": ms}
+        inst = NCU_INST_PER_MARKER.get(name)
+        if inst and sms and sm_mhz:
+            got = inst / 32.0 * np_ / (launch_ms / 1e3) / 1e9
+            top = sms * 4 * sm_mhz / 1e3
+            entry["issue"] = {"inst_per_marker": inst, "achieved": got, "peak": top, "unit": "G warp-inst/s",
+                              "frac": got / top}
+        out.append(entry)
     return out
 
 
@@ -373,7 +384,9 @@ def main():
     v64 = R.whole_job_rate(w.np, ws, k64, ms64 / 1e3)
     tr = r_head["timing"]
     hbm, tflops, peak_kind = peaks()
-    kernels = kernel_rooflines(tr, w.np, hbm, tflops, peak_kind)
+    sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+    kernels = kernel_rooflines(tr, w.np, hbm, tflops, peak_kind,
+                               torch.cuda.get_device_properties(local).multi_processor_count, sm_mhz)
     dominant = max(kernels, key=lambda k: k["share_ms"])
     if rank == 0:
         cpu = None
