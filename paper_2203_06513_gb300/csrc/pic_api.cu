@@ -101,8 +101,10 @@ static void release(pic_handle *h)
     for (int m = 0; m < kMaxStartOrder; ++m) { f(h->fh.x[m]); f(h->fh.y[m]); f(h->fh.z[m]); }
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
-    if (h->ev0) cudaEventDestroy(h->ev0);
-    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (auto &t : h->timed) { cudaEventDestroy(t.b); cudaEventDestroy(t.e); }
+    for (auto &t : h->spare) { cudaEventDestroy(t.first); cudaEventDestroy(t.second); }
+    h->timed.clear();
+    h->spare.clear();
 }
 
 static PartPtrs cur_parts(pic_handle *h)
@@ -331,8 +333,6 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
     if ((rc = dalloc(h, &h->ctrl, 1))) return bail(rc);
     if (cudaMallocHost((void **)&h->h_flag, sizeof(int)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
     if (cudaMallocHost((void **)&h->h_ctrl, sizeof(DevCtrl)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
-    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
-        return bail(PIC_ERR_CUDA);
 
     // circulant bands: M0 (degree k), M1 (degree k-1), K = G^T M1 G, P = M0 +/- dt^2/4 K
     const int K = h->K;
@@ -440,21 +440,55 @@ static int check_status(pic_handle *h, int which)
     return PIC_OK;
 }
 
+// Timing without host synchronisation: each timed launch gets its own pair of
+// events, recorded on the handle's stream; the pairs are read when the timing
+// is read (or when many are pending) and then reused.
+constexpr size_t kMaxTimedLaunches = 4096;
+static int timing_fold(pic_handle *h);
+
 static int timed_begin(pic_handle *h)
 {
-    if (h->timing) CK(cudaEventRecord(h->ev0, h->stream));
+    if (!h->timing) return PIC_OK;
+    int rc;
+    if (h->timed.size() >= kMaxTimedLaunches && (rc = timing_fold(h))) return rc;
+    if (h->spare.empty()) {
+        cudaEvent_t b = nullptr, e = nullptr;
+        CK(cudaEventCreate(&b));
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaEventDestroy(b);
+            return fail(h, PIC_ERR_CUDA, "cudaEventCreate failed");
+        }
+        h->spare.emplace_back(b, e);
+    }
+    CK(cudaEventRecord(h->spare.back().first, h->stream));
     return PIC_OK;
 }
 
-static int timed_end(pic_handle *h, double *acc, long long *cnt)
+static int timed_end(pic_handle *h, int kind)
 {
     if (!h->timing) return PIC_OK;
-    CK(cudaEventRecord(h->ev1, h->stream));
-    CK(cudaEventSynchronize(h->ev1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    *acc += ms;
-    ++*cnt;
+    auto pr = h->spare.back();
+    h->spare.pop_back();
+    h->timed.push_back({pr.first, pr.second, kind});
+    CK(cudaEventRecord(pr.second, h->stream));
+    return PIC_OK;
+}
+
+// Adds the pending pairs' durations to the totals and returns the pairs to the spares.
+static int timing_fold(pic_handle *h)
+{
+    if (h->timed.empty()) return PIC_OK;
+    CK(cudaEventSynchronize(h->timed.back().e));
+    for (auto &t : h->timed) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, t.b, t.e));
+        double *acc[] = {&h->t_sw1, &h->t_sw2, &h->t_solve, &h->t_warm};
+        long long *cnt[] = {&h->n_sw1, &h->n_sw2, &h->n_solve, &h->n_warm};
+        *acc[t.kind] += ms;
+        ++*cnt[t.kind];
+        h->spare.emplace_back(t.b, t.e);
+    }
+    h->timed.clear();
     return PIC_OK;
 }
 
@@ -491,7 +525,7 @@ static int substep1(pic_handle *h, int *iters)
         if (launch_warm_mlp(wa, h->num_sms, h->stream))
             return fail(h, PIC_ERR_CUDA, "warm-start network: launch setup failed");
         CKL_N("launch_warm_mlp");
-        if ((rc = timed_end(h, &h->t_warm, &h->n_warm))) return rc;
+        if ((rc = timed_end(h, 3))) return rc;
     }
     int it = 0;
     for (;;) {
@@ -501,21 +535,22 @@ static int substep1(pic_handle *h, int *iters)
         if (launch_sweep1(a, h->sweep_grid, h->sweep_block, h->smem1, h->stream))
             return fail(h, PIC_ERR_INVALID, "sweep1: bad degree");
         CKL_N("launch_sweep1");
-        if ((rc = timed_end(h, &h->t_sw1, &h->n_sw1))) return rc;
+        if ((rc = timed_end(h, 0))) return rc;
         h->marker_sweeps += h->np;
         c.in[0] = h->jb[it & 1];
         c.zero[0] = h->jb[(it + 1) & 1];
         if ((rc = timed_begin(h))) return rc;
         if (launch_conv(c, h->stream)) return fail(h, PIC_ERR_CUDA, "k_conv shared-memory opt-in failed");
         CKL_N("launch_conv");
-        if ((rc = timed_end(h, &h->t_solve, &h->n_solve))) return rc;
+        if ((rc = timed_end(h, 2))) return rc;
         ++it;
         if ((rc = read_ctrl(h))) return rc;
         if (h->h_ctrl->converged) break;
     }
     if (iters) *iters = it;
     if ((rc = check_status(h, 1))) return rc;
-    launch_finalize1(h->fp32, h->np, h->M, cur_parts(h), particle_grid(h), 256, h->stream);
+    launch_finalize1(h->fp32, h->np, h->M, cur_parts(h), h->cfg.warm_start == PIC_WARM_NONE, particle_grid(h), 256,
+                     h->stream);
     CKL_N("launch_finalize1");
     launch_commit(desc, 1, h->stream);
     CKL_N("launch_commit");
@@ -552,7 +587,7 @@ static int substep2(pic_handle *h, int *iters)
         if (launch_sweep2(a, h->sweep_grid, h->sweep_block, h->smem2, h->stream))
             return fail(h, PIC_ERR_INVALID, "sweep2: bad degree");
         CKL_N("launch_sweep2");
-        if ((rc = timed_end(h, &h->t_sw2, &h->n_sw2))) return rc;
+        if ((rc = timed_end(h, 1))) return rc;
         c.in[0] = h->sy[it & 1];
         c.in[1] = h->sz[it & 1];
         c.zero[0] = h->sy[(it + 1) & 1];
@@ -560,7 +595,7 @@ static int substep2(pic_handle *h, int *iters)
         if ((rc = timed_begin(h))) return rc;
         if (launch_conv(c, h->stream)) return fail(h, PIC_ERR_CUDA, "k_conv shared-memory opt-in failed");
         CKL_N("launch_conv");
-        if ((rc = timed_end(h, &h->t_solve, &h->n_solve))) return rc;
+        if ((rc = timed_end(h, 2))) return rc;
         ++it;
         if ((rc = read_ctrl(h))) return rc;
         if (h->h_ctrl->converged) break;
@@ -741,6 +776,8 @@ extern "C" int pic_set_warm_mlp(pic_handle *h, pic_mlp *m)
 extern "C" int pic_timing_enable(pic_handle *h, int32_t on)
 {
     if (!h) return PIC_ERR_INVALID;
+    int rc;
+    if ((rc = timing_fold(h))) return rc;      // pairs of an earlier period are dropped below
     h->timing = on ? 1 : 0;
     h->t_sw1 = h->t_sw2 = h->t_solve = h->t_warm = 0.0;
     h->n_warm = 0;
@@ -753,6 +790,8 @@ extern "C" int pic_timing_enable(pic_handle *h, int32_t on)
 extern "C" int pic_timing_read(pic_handle *h, double out[10])
 {
     if (!h || !out) return PIC_ERR_INVALID;
+    int rc;
+    if ((rc = timing_fold(h))) return rc;
     out[0] = h->t_sw1;
     out[1] = (double)h->n_sw1;
     out[2] = h->t_sw2;

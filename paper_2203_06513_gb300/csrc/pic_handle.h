@@ -2,6 +2,8 @@
 #pragma once
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "pic.h"
 #include "pic_internal.h"
@@ -52,9 +54,15 @@ struct pic_handle {
     int sweep_grid = 0, sweep_block = kSweepThreads;
     size_t smem1 = 0, smem2 = 0;
 
-    // timing
+    // timing: event pairs recorded around the timed launches, read back (and the
+    // pairs reused) by pic_timing_read or when kMaxTimedLaunches are pending
     int timing = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    struct Timed {
+        cudaEvent_t b, e;
+        int kind;                   // 0 sweep I, 1 sweep II, 2 solve, 3 warm start
+    };
+    std::vector<Timed> timed;       // pairs in use, in launch order
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
     double t_sw1 = 0, t_sw2 = 0, t_solve = 0;
     long long n_sw1 = 0, n_sw2 = 0, n_solve = 0, launches = 0, marker_sweeps = 0;
 

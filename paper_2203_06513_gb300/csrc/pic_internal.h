@@ -98,7 +98,8 @@ int launch_charge(const DiagArgs &a, int grid, int block, size_t smem, cudaStrea
 size_t charge_smem(int M, int H);
 int launch_gather(const DiagArgs &a, int field_degree, int grid, int block, cudaStream_t s);
 int launch_kinetic(const DiagArgs &a, int grid, int block, cudaStream_t s);
-int launch_finalize1(int fp32, long long np, int M, PartPtrs P, int grid, int block, cudaStream_t s);
+int launch_finalize1(int fp32, long long np, int M, PartPtrs P, bool zero_delta, int grid, int block,
+                     cudaStream_t s);
 int launch_load(int fp32, long long np, int M, double dx, const double *x, const double *p,
                 PartPtrs P, int grid, int block, cudaStream_t s);
 int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, double *p,

@@ -893,11 +893,13 @@ int launch_kinetic(const DiagArgs &a, int grid, int block, cudaStream_t s)
 
 // ---------------------------------------------------------------------------
 // End of subsystem I: x^{n+1} = x^n + delta (re-split into cell and offset,
-// wrapped periodically), p^{n+1} = p^(k+1); the iterate is reset.
+// wrapped periodically), p^{n+1} = p^(k+1).  delta is cleared only where the
+// next iteration starts from it (no warm start): the warm starts overwrite it
+// before any sweep reads it.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void finalize1_range(long long np, int M, const PartPtrs &P, long long a0,
-                                                long long stride)
+                                                long long stride, bool zero_delta)
 {
     R *tp = static_cast<R *>(P.t);
     R *pp = static_cast<R *>(P.p);
@@ -912,21 +914,22 @@ __device__ __forceinline__ void finalize1_range(long long np, int M, const PartP
         P.cell[a] = wrap_cell(c, M);
         tp[a] = t;
         pp[a] = pnp[a];
-        dp[a] = R(0);
+        if (zero_delta) dp[a] = R(0);
     }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_finalize1(long long np, int M, PartPtrs P)
+__global__ void __launch_bounds__(256) k_finalize1(long long np, int M, PartPtrs P, bool zero_delta)
 {
     finalize1_range<R>(np, M, P, (long long)blockIdx.x * blockDim.x + threadIdx.x,
-                       (long long)gridDim.x * blockDim.x);
+                       (long long)gridDim.x * blockDim.x, zero_delta);
 }
 
-int launch_finalize1(int fp32, long long np, int M, PartPtrs P, int grid, int block, cudaStream_t s)
+int launch_finalize1(int fp32, long long np, int M, PartPtrs P, bool zero_delta, int grid, int block,
+                     cudaStream_t s)
 {
-    if (fp32) k_finalize1<float><<<grid, block, 0, s>>>(np, M, P);
-    else k_finalize1<double><<<grid, block, 0, s>>>(np, M, P);
+    if (fp32) k_finalize1<float><<<grid, block, 0, s>>>(np, M, P, zero_delta);
+    else k_finalize1<double><<<grid, block, 0, s>>>(np, M, P, zero_delta);
     return 0;
 }
 
@@ -989,8 +992,10 @@ int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, doubl
 // ---------------------------------------------------------------------------
 // Counting sort of the markers by key = cell * kVelBins + velocity bin, the
 // bin being the expected displacement tau p in whole cells (clamped), so that a
-// warp's markers share cells and piece counts.  Runs between steps (delta = 0,
-// p_new = p).  Atomics are aggregated per warp over equal keys.
+// warp's markers share cells and piece counts.  Runs between steps; delta and
+// p_new are not carried (each step's first sweep or warm start writes them
+// before they are read, and delta is all zero where the iteration starts from
+// it).  Atomics are aggregated per warp over equal keys.
 // counts: 2 * nkeys int32 (histogram, then cursors).
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -1049,8 +1054,6 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, float tau, PartPt
     const R *ps = static_cast<const R *>(S.p);
     R *td = static_cast<R *>(D.t);
     R *pd = static_cast<R *>(D.p);
-    R *pnd = static_cast<R *>(D.pnew);
-    R *dd = static_cast<R *>(D.delta);
     long long beg, end;
     block_chunk(np, beg, end);
     const int lane = threadIdx.x & 31;
@@ -1070,8 +1073,6 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, float tau, PartPt
         D.cell[j] = c;
         td[j] = ts[a];
         pd[j] = p;
-        pnd[j] = p;
-        dd[j] = R(0);
         D.id[j] = S.id[a];
     }
 }
@@ -1189,7 +1190,7 @@ __global__ void __launch_bounds__(256) k_finalize1_ens(const RunDesc *runs)
     const RunDesc &D = runs[blockIdx.y];
     if (D.ctrl->status & (STATUS_NUMERIC | STATUS_TIMEOUT)) return;
     finalize1_range<R>(D.np, D.M, D.P, (long long)blockIdx.x * blockDim.x + threadIdx.x,
-                       (long long)gridDim.x * blockDim.x);
+                       (long long)gridDim.x * blockDim.x, true);
 }
 
 int launch_finalize1_ens(int fp32, const RunDesc *R, int nruns, int grid_x, cudaStream_t s)
