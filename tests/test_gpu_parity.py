@@ -242,3 +242,24 @@ def test_noconvergence_is_reported():
     g = pic.Pic(cfg, x, p, ay, az, ey, ez)
     with pytest.raises(pic.NoConvergence):
         g.substep(pic.PIC_SUBSYSTEM_I)
+
+
+def test_timing_counts_match_sweeps():
+    """Kernel timing (events recorded without host synchronisation, read back by
+    pic_timing_read): one timed launch per sweep and per solve, positive times,
+    and a fresh enable starts from zero."""
+    w = small(M=64, npart=20000, seed=9)
+    for warm in (pic.PIC_WARM_NONE, pic.PIC_WARM_EXPLICIT):
+        _, _, g = setup(w, precision=pic.PIC_FP32, warm_start=warm, sort_every=2)
+        g.step(1)
+        g.timing_enable(True)
+        i1, i2 = g.step(3)
+        t = g.timing_read()
+        assert t["sweep1_launches"] == i1 and t["sweep2_launches"] == i2
+        assert t["solve_launches"] == i1 + i2
+        assert t["sweep1_ms"] > 0 and t["sweep2_ms"] > 0 and t["solve_ms"] > 0
+        assert t["marker_sweeps1"] == i1 * w.np
+        g.timing_enable(True)
+        t = g.timing_read()
+        assert t["sweep1_launches"] == 0 and t["sweep1_ms"] == 0
+        g.close()
