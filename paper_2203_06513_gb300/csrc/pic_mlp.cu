@@ -385,11 +385,19 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_infer(const float *param
     const int g = threadIdx.x / kRows, r = threadIdx.x % kRows;
     unsigned phase = 0;
     const long long stride = (long long)gridDim.x * kChains * kRows;
-    for (long long base = ((long long)blockIdx.x * kChains + g) * kRows; base < B; base += stride) {
+    // the next tile's inputs are loaded while the network runs on this one
+    float nx[kIn];
+    const long long base0 = ((long long)blockIdx.x * kChains + g) * kRows;
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) nx[i] = base0 + r < B ? X[(base0 + r) * kIn + i] : 0.f;
+    for (long long base = base0; base < B; base += stride) {
         const long long a = base + r;
         float f[kIn];
 #pragma unroll
-        for (int i = 0; i < kIn; ++i) f[i] = a < B ? X[a * kIn + i] : S.norm[i];
+        for (int i = 0; i < kIn; ++i) f[i] = a < B ? nx[i] : S.norm[i];
+        const long long an = a + stride;
+#pragma unroll
+        for (int i = 0; i < kIn; ++i) nx[i] = an < B ? X[an * kIn + i] : 0.f;
         umma_put_features(S, g, r, f);
         float y[2];
         if (!umma_network(S, g, r, phase, y)) {
@@ -431,14 +439,28 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_warm_mlp(WarmArgs A)
     const float c2 = (float)(A.dt * A.dt / A.dx);
     unsigned phase = 0;
     const long long stride = (long long)gridDim.x * kChains * kRows;
-    for (long long base = ((long long)blockIdx.x * kChains + g) * kRows; base < A.np; base += stride) {
+    // the next tile's markers are loaded while the network runs on this one
+    const long long base0 = ((long long)blockIdx.x * kChains + g) * kRows;
+    int nc = 0;
+    R nt = R(0), np_ = R(0);
+    if (base0 + r < A.np) {
+        nc = A.P.cell[base0 + r];
+        nt = tp[base0 + r];
+        np_ = pp[base0 + r];
+    }
+    for (long long base = base0; base < A.np; base += stride) {
         const long long a = base + r;
         const bool act = a < A.np;
         float f[kIn], pn = 0.f, g0 = 1.f;
+        const int c = nc;
+        const float t = (float)nt;
+        pn = act ? (float)np_ : 0.f;
+        if (a + stride < A.np) {
+            nc = A.P.cell[a + stride];
+            nt = tp[a + stride];
+            np_ = pp[a + stride];
+        }
         if (act) {
-            const int c = A.P.cell[a];
-            const float t = (float)tp[a];
-            pn = (float)pp[a];
             float v[K + 1], u[K];
             bspline_vals<K, float>(t, v);
             bspline_vals<K - 1, float>(t, u);
