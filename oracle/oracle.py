@@ -20,7 +20,18 @@ linear algebra here (numpy / scipy LAPACK), written as the paper states it:
 * the Lie--Trotter step Phi_II(dt) o Phi_I(dt) (Sec. 5),
 * the discrete Hamiltonian (Eq. discrete_H) and the Gauss-law residual.
 
-Readings of points the paper leaves open are listed in the design doc (S1-S15).
+Where the paper is silent or its printed schemes disagree, this module reads it so:
+the V1 basis is the plain B-spline N^{k-1} with (G v)_j = (v_j - v_{j-1}) / dx; a
+marker in cell c touches Lambda^0_{c-k..c}, a knot belonging to the cell on its
+right; Poisson is G^T M1 e_x = -rho + dx (neutralising background) with sum e_x = 0;
+subsystem I iterates on positions from x^(0) = x^n (or a given warm start) with
+p^(0) = p^n; the difference quotient of A is the exact path mean of dA/dx, so no
+0/0 arises; subsystem II uses Lambda^0 and solves (M0 + dt^2/4 K) exactly each
+sweep; the stray M0^{-1} and the dot in the printed schemes are typos and the
+hbar terms vanish; the Lie--Trotter order is subsystem I first; each loop stops
+when the position and field increments are both at most tol = 1e-13; path
+integrals are split at every crossed knot and integrated by ceil(k/2)-point
+Gauss--Legendre on each piece.
 Parity status: every function here is pinned by tests/test_oracle_*.py.
 """
 from __future__ import annotations

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-FP64 form: the spec bar is a relative 1e-10 in particle state and field
+FP64 form: the parity bar is a relative 1e-10 in particle state and field
 coefficients over the 50 steps of the plain workload; single kernels and single
 substeps are held to 1e-12..1e-13 (both sides solve the same fixed point to
 tol = 1e-13, and differ only in rounding order: atomics, and the kernel's exact
