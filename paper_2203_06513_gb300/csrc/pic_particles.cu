@@ -1057,23 +1057,38 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, float tau, PartPt
     long long beg, end;
     block_chunk(np, beg, end);
     const int lane = threadIdx.x & 31;
-    for (long long base = beg; base < end; base += blockDim.x) {
-        const long long a = base + threadIdx.x;
-        const bool act = a < end;
-        const int c = act ? S.cell[a] : 0;
-        const R p = act ? ps[a] : R(0);
-        const int key = act ? sort_key(c, p, tau) : -1;
-        const unsigned grp = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(grp) - 1;
-        int first = 0;
-        if (act && lane == leader) first = atomicAdd(&cursor[key], __popc(grp));
-        first = __shfl_sync(0xffffffffu, first, leader);
-        if (!act) continue;
-        const long long j = (long long)first + __popc(grp & ((1u << lane) - 1u));
-        D.cell[j] = c;
-        td[j] = ts[a];
-        pd[j] = p;
-        D.id[j] = S.id[a];
+    // kSortU markers a thread per pass: their cursor atomics are independent, so
+    // the warp waits for the returned slots once per pass instead of once a marker
+    constexpr int kSortU = 4;
+    for (long long base = beg; base < end; base += kSortU * (long long)blockDim.x) {
+        int c[kSortU], key[kSortU], first[kSortU];
+        R p[kSortU];
+        unsigned grp[kSortU];
+#pragma unroll
+        for (int u = 0; u < kSortU; ++u) {
+            const long long a = base + u * (long long)blockDim.x + threadIdx.x;
+            const bool act = a < end;
+            c[u] = act ? S.cell[a] : 0;
+            p[u] = act ? ps[a] : R(0);
+            key[u] = act ? sort_key(c[u], p[u], tau) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortU; ++u) {
+            grp[u] = __match_any_sync(0xffffffffu, key[u]);
+            first[u] = 0;
+            if (key[u] >= 0 && lane == __ffs(grp[u]) - 1) first[u] = atomicAdd(&cursor[key[u]], __popc(grp[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < kSortU; ++u) {
+            const long long a = base + u * (long long)blockDim.x + threadIdx.x;
+            const int f = __shfl_sync(0xffffffffu, first[u], __ffs(grp[u]) - 1);
+            if (key[u] < 0) continue;
+            const long long j = (long long)f + __popc(grp[u] & ((1u << lane) - 1u));
+            D.cell[j] = c[u];
+            td[j] = ts[a];
+            pd[j] = p[u];
+            D.id[j] = S.id[a];
+        }
     }
 }
 
