@@ -120,6 +120,7 @@ static void build_tables(pic_ensemble *e)
         a.ctrl = h->ctrl;
         a.j = h->jb[0];
         a.warm = h->cfg.warm_start == PIC_WARM_EXPLICIT ? 1 : 0;
+        a.a0 = h->a0;
         a.graph = 1;
         a.jpair[0] = h->jb[0]; a.jpair[1] = h->jb[1];
         a.img = h->img;

@@ -30,6 +30,7 @@ struct pic_handle {
     char *Pblk[2] = {nullptr, nullptr};
     int cur = 0;
     void *delta = nullptr, *pnew = nullptr;
+    void *a0 = nullptr;             // subsystem-I start-point cache (4 reals a marker; FP64 form)
 
     // grid state (double)
     double *ex = nullptr, *ey = nullptr, *ez = nullptr, *ay = nullptr, *az = nullptr;

@@ -46,12 +46,16 @@ struct Sweep1Args {
     double *j;
     DevCtrl *ctrl;
     int warm;           // 1: delta^(0) = explicit predictor, computed in-kernel (first sweep)
+    int first;          // 1: the first sweep of the loop (writes the start-point cache)
     // graph mode (the launch is replayed by a CUDA graph): the deposit buffer is
-    // jpair[iter & 1] and the explicit warm start applies when iter == 0, with
-    // iter read from ctrl at kernel start
+    // jpair[iter & 1], and the explicit warm start and the first-sweep role apply
+    // when iter == 0, with iter read from ctrl at kernel start
     int graph;
     double *jpair[2];
     StageImages img;
+    // start-point cache, 4 reals a marker (A_y(x^n), A_z(x^n), gamma(p^n, A(x^n)),
+    // unused): written by the loop's first sweep, read by the later ones; NULL: none
+    void *a0;
 };
 
 struct Sweep2Args {

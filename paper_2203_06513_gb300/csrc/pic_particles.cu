@@ -209,6 +209,37 @@ __device__ __forceinline__ void tile_drain(TileBars &B)
 // ---------------------------------------------------------------------------
 // Markers [beg, end) of one run.  q = the block's tile sequence number (in/out).
 // Returns false after a bounded wait gave up (the block must then stop).
+// Start-point cache of subsystem I: (A_y, A_z, gamma, unused) per marker, as one
+// 16-byte (float) or two 16-byte (double) accesses.
+template <typename R>
+__device__ __forceinline__ void start_cache_store(void *base, long long a, R y, R z, R g)
+{
+    if constexpr (Real<R>::fp32) {
+        reinterpret_cast<float4 *>(base)[a] = make_float4(y, z, g, 0.f);
+    } else {
+        double2 *q = reinterpret_cast<double2 *>(base) + 2 * a;
+        q[0] = make_double2(y, z);
+        q[1] = make_double2(g, 0.0);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void start_cache_load(const void *base, long long a, R &y, R &z, R &g)
+{
+    if constexpr (Real<R>::fp32) {
+        const float4 v = reinterpret_cast<const float4 *>(base)[a];
+        y = v.x;
+        z = v.y;
+        g = v.z;
+    } else {
+        const double2 *q = reinterpret_cast<const double2 *>(base) + 2 * a;
+        const double2 u = q[0], w = q[1];
+        y = u.x;
+        z = u.y;
+        g = w.x;
+    }
+}
+
 template <int K, typename R>
 __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg, long long end,
                                              unsigned char *smem, unsigned long long &q)
@@ -234,10 +265,12 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     const unsigned long long q0 = q, qend = q + (unsigned long long)ntile;
     double *jout = A.j;
     bool warm = A.warm != 0;
+    bool first = A.first != 0;
     if (A.graph) {                          // replayed by a graph: buffers by sweep parity
         const int it = *reinterpret_cast<volatile const int *>(&A.ctrl->iter);
         jout = A.jpair[it & 1];
         warm = warm && it == 0;
+        first = it == 0;
     }
     const bool need_delta = !warm;
     auto issue = [&](long long i) {            // thread 0: copies of tile i into stage (q0 + i) % NS
@@ -324,16 +357,27 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             const R t0 = s_t(b)[jl];
             const R pn = s_p(b)[jl];
             R v[K + 1];
-            bspline_scaled<K, R>(t0, v);
-            R A0y = R(0), A0z = R(0);
+            // A(x^n) and gamma(p^n, A(x^n)) do not change during the loop: in the
+            // double form the first sweep stores them and the later ones read them
+            // back (the float form recomputes: there the extra bytes cost more)
+            R A0y = R(0), A0z = R(0), g0;
+            bool cached = false;
+            if constexpr (!Real<R>::fp32) cached = !first && A.a0 != nullptr;
+            if (cached) {
+                start_cache_load<R>(A.a0, a, A0y, A0z, g0);
+            } else {
+                bspline_scaled<K, R>(t0, v);
 #pragma unroll
-            for (int r = 0; r <= K; ++r) {
-                R y, z;
-                F.aa(c0 - r + H, y, z);
-                A0y += y * v[r];
-                A0z += z * v[r];
+                for (int r = 0; r <= K; ++r) {
+                    R y, z;
+                    F.aa(c0 - r + H, y, z);
+                    A0y += y * v[r];
+                    A0z += z * v[r];
+                }
+                g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
+                if constexpr (!Real<R>::fp32)
+                    if (A.a0) start_cache_store<R>(A.a0, a, A0y, A0z, g0);
             }
-            const R g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
             R dold = warm ? fdiv_(tau * pn, g0) : s_d(b)[jl];
             if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
 
