@@ -25,7 +25,12 @@
  *    pinned).  The caller owns every array it passes; the handle never keeps
  *    a caller pointer after a call returns.
  *  - The handle owns its device state and scratch (allocated in pic_init,
- *    freed in pic_destroy).  All work is ordered on the stream given to
+ *    freed in pic_destroy).  They come from a stream-ordered memory pool that
+ *    the library keeps per device: what pic_destroy returns stays reserved in
+ *    that pool for later handles of the process (until the process exits), so
+ *    a repeated pic_init does not map new device memory; other allocators of
+ *    the process are not affected.  The stream must outlive the handle.
+ *    All work is ordered on the stream given to
  *    pic_init (a cudaStream_t passed as void*; NULL = legacy default stream).
  *    Calls return after their results are complete on that stream unless
  *    stated otherwise.  A handle must not be used from two threads at once.

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "pic.h"
@@ -70,21 +71,53 @@ static bool debug_sync()
     return v == 1;
 }
 
+// Device memory of the handles comes from a stream-ordered pool of the library's
+// own, one per device, that keeps what destroyed handles return: a later pic_init
+// in the process (the next run of a job, the runs of an ensemble) takes it back
+// without mapping new memory.  Other allocators of the process are not affected.
+static cudaMemPool_t handle_pool(int device)
+{
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)pools.size() <= device) pools.resize(device + 1, nullptr);
+    if (!pools[device]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = ~0ull;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return nullptr;
+        }
+        pools[device] = pool;
+    }
+    return pools[device];
+}
+
 template <typename T>
 static int dalloc(pic_handle *h, T **p, size_t n)
 {
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    cudaMemPool_t pool = handle_pool(h->device);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync((void **)p, n * sizeof(T), pool, h->stream)
+                         : cudaErrorMemoryAllocation;
     if (e != cudaSuccess) {
         *p = nullptr;
-        return fail(h, PIC_ERR_NOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+        cudaGetLastError();
+        return fail(h, PIC_ERR_NOMEM, "device allocation (%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
     }
     return PIC_OK;
 }
 
+// Returns the handle's device memory to the pool (in stream order, then waits).
 static void release(pic_handle *h)
 {
-    auto f = [](void *p) { if (p) cudaFree(p); };
+    cudaStream_t s = h->stream;
+    auto f = [s](void *p) { if (p) cudaFreeAsync(p, s); };
     for (int b = 0; b < 2; ++b) {
         f(h->Pblk[b]);
         f(h->jb[b]); f(h->sy[b]); f(h->sz[b]);
@@ -99,6 +132,7 @@ static void release(pic_handle *h)
     f(h->ctrl);
     f(h->img.a); f(h->img.f); f(h->img.an); f(h->img.ak); f(h->img.lo);
     for (int m = 0; m < kMaxStartOrder; ++m) { f(h->fh.x[m]); f(h->fh.y[m]); f(h->fh.z[m]); }
+    cudaStreamSynchronize(s);
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto &t : h->timed) { cudaEventDestroy(t.b); cudaEventDestroy(t.e); }
