@@ -1,8 +1,9 @@
 /*
  * pic_oracle.c -- plain FP64 CPU oracle for the particle loops of the
- * energy-conserving PIC scheme (1D reduced relativistic Vlasov--Maxwell,
- * hbar = 0) of Li, "Energy conserving particle-in-cell methods for
- * relativistic Vlasov--Maxwell equations of laser-plasma interaction".
+ * energy-conserving PIC scheme (1D reduced relativistic Vlasov--Maxwell)
+ * of Li, "Energy conserving particle-in-cell methods for relativistic
+ * Vlasov--Maxwell equations of laser-plasma interaction": the hbar = 0
+ * scheme, and the spin terms (hbar != 0) at the end of the file.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
  * calls this file: only tests/, the smoke check and the benchmark's CPU
@@ -339,4 +340,192 @@ void orc_sweep2(int k, long M, double dx, double w, long np,
             s_z[i] += cf * (A0z + A1z) * v[r];
         }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Spin (hbar != 0): the terms of Sec. 4.2 that carry hbar.              */
+/*                                                                      */
+/* The Hamiltonian (Eq. discrete_H) adds                                 */
+/*   hbar sum_a w (s_y,a dA_z/dx(x_a) - s_z,a dA_y/dx(x_a)),             */
+/* with dA_h/dx = sum_i (G a)_i Lambda^1_i (Sec. 3.1).  Its second       */
+/* derivative is the degree-(k-2) spline sum_i (G' G a)_i Lambda^2_i,    */
+/* Lambda^2_i = N^{k-2}_i, (G' v)_i = (v_i - v_{i-1})/dx, by the same    */
+/* derivative relation one degree lower.                                  */
+/* ------------------------------------------------------------------ */
+
+/* Path mean of every degree-d basis function N^d_i along x0 -> x1 (the
+ * path split at every knot, q = ceil((d+1)/2) Gauss--Legendre nodes per
+ * piece: exact for degree d).  mean[] must be zero on entry; the touched
+ * node range is returned in [lo, hi] (unwrapped).                       */
+static void path_mean_deg(int d, long M, double dx, double x0, double x1,
+                          double *mean, long *touched_lo, long *touched_hi)
+{
+    double xi[16], w[16];
+    int nq = (d + 2) / 2;
+    orc_gauss_legendre(nq, xi, w);
+    double u0 = x0 / dx, u1 = x1 / dx;
+    double len = u1 - u0;
+    double dir = (len >= 0.0) ? 1.0 : -1.0;
+    double ua = u0;
+    long lo = 0, hi = 0;
+    int first = 1;
+    for (;;) {
+        double ub;
+        if (dir > 0) { ub = floor(ua) + 1.0; if (ub > u1) ub = u1; }
+        else         { ub = ceil(ua) - 1.0;  if (ub < u1) ub = u1; }
+        if (len == 0.0) ub = u1;
+        double seg_lo = ua < ub ? ua : ub;
+        long c = (long)floor(seg_lo);
+        double frac = (len == 0.0) ? 1.0 : (ub - ua) / len;
+        for (int q = 0; q < nq; ++q) {
+            double uq = ua + (ub - ua) * 0.5 * (1.0 + xi[q]);
+            double v[8];
+            orc_basis(d, uq - (double)c, v);
+            for (int r = 0; r <= d; ++r) mean[wrap_index(c - r, M)] += frac * 0.5 * w[q] * v[r];
+        }
+        if (first) { lo = c - d; hi = c; first = 0; }
+        if (c - d < lo) lo = c - d;
+        if (c > hi) hi = c;
+        if (ub == u1) break;
+        ua = ub;
+    }
+    *touched_lo = lo;
+    *touched_hi = hi;
+}
+
+/* Exposed for tests: path means of the degree-d basis along x0 -> x1. */
+void orc_path_mean_deg(int d, long M, double dx, double x0, double x1, double *mean)
+{
+    long lo, hi;
+    for (long i = 0; i < M; ++i) mean[i] = 0.0;
+    path_mean_deg(d, M, dx, x0, x1, mean, &lo, &hi);
+}
+
+/* Subsystem I sweep with spin: orc_sweep1 plus, in the momentum update,
+ *   - dt hbar ( s_y D2_z - s_z D2_y ),
+ * D2 = (dA/dx(x^(k)) - dA/dx(x^n)) / (x^(k) - x^n) = the path mean of
+ * d^2A/dx^2 = sum_i (G'Ga)_i m2_i, m2 = path means of Lambda^2 (exact, so
+ * no 0/0 arises), the spin held at s^n (Sec. 4.2, subsystem I with the
+ * discrete gradient of the Zeeman term).  gga_y, gga_z: G'G a_y, G'G a_z. */
+void orc_sweep1_spin(int k, long M, double dx, double dt, double w, double hbar, long np,
+                     const double *x, const double *p, const double *sy, const double *sz,
+                     double *delta, double *pk,
+                     const double *ebar, const double *ga_y, const double *ga_z,
+                     const double *gga_y, const double *gga_z,
+                     const double *ay, const double *az,
+                     double *j, double *dmax, double *pmax,
+                     double *mean_scratch, double *mean2_scratch)
+{
+    double dm = 0.0, pm = 0.0;
+    double xi[16], wq[16];
+    orc_gauss_legendre((k + 1) / 2, xi, wq);
+    for (long a = 0; a < np; ++a) {
+        double x0 = x[a];
+        double x1 = x0 + delta[a];
+        double A0y = fe_value(k, ay, M, dx, x0), A0z = fe_value(k, az, M, dx, x0);
+        double A1y = fe_value(k, ay, M, dx, x1), A1z = fe_value(k, az, M, dx, x1);
+
+        long lo, hi;
+        path_mean_1form(k, M, dx, x0, x1, xi, wq, mean_scratch, &lo, &hi);
+        double Ebar = 0.0, Dy = 0.0, Dz = 0.0;
+        for (long jj = lo; jj <= hi && jj - lo < M; ++jj) {
+            long i = wrap_index(jj, M);
+            Ebar += mean_scratch[i] * ebar[i];
+            Dy += mean_scratch[i] * ga_y[i];
+            Dz += mean_scratch[i] * ga_z[i];
+            mean_scratch[i] = 0.0;
+        }
+        double D2y = 0.0, D2z = 0.0;
+        path_mean_deg(k - 2, M, dx, x0, x1, mean2_scratch, &lo, &hi);
+        for (long jj = lo; jj <= hi && jj - lo < M; ++jj) {
+            long i = wrap_index(jj, M);
+            D2y += mean2_scratch[i] * gga_y[i];
+            D2z += mean2_scratch[i] * gga_z[i];
+            mean2_scratch[i] = 0.0;
+        }
+        double pn = p[a];
+        double g1 = sqrt(1.0 + pn * pn + A1y * A1y + A1z * A1z);
+        double g0 = sqrt(1.0 + pn * pn + A0y * A0y + A0z * A0z);
+        double pnew = pn + dt * Ebar - dt * ((A1y + A0y) * Dy + (A1z + A0z) * Dz) / (g1 + g0)
+                      - dt * hbar * (sy[a] * D2z - sz[a] * D2y);
+        double g2 = sqrt(1.0 + pnew * pnew + A1y * A1y + A1z * A1z);
+        double dnew = dt * (pn + pnew) / (g1 + g2);
+
+        path_mean_1form(k, M, dx, x0, x0 + dnew, xi, wq, mean_scratch, &lo, &hi);
+        for (long jj = lo; jj <= hi && jj - lo < M; ++jj) {
+            long i = wrap_index(jj, M);
+            j[i] += w * dnew * mean_scratch[i];
+            mean_scratch[i] = 0.0;
+        }
+
+        double dd = fabs(dnew - delta[a]);
+        double dp = fabs(pnew - pk[a]);
+        if (!(dd <= dm)) dm = dd;
+        if (!(dp <= pm)) pm = dp;
+        delta[a] = dnew;
+        pk[a] = pnew;
+    }
+    *dmax = dm;
+    *pmax = pm;
+}
+
+/* d_i = sum_a w s_a Lambda^1_i(x_a): the Lambda_1(X)^T W S of the spin source
+ * of subsystem II (applied with G^T on the grid side).                  */
+void orc_spin_deposit(int k, long M, double dx, long np, const double *x, double w,
+                      const double *s, double *d)
+{
+    for (long i = 0; i < M; ++i) d[i] = 0.0;
+    for (long a = 0; a < np; ++a) {
+        long c; double t; double v[8];
+        split_u(x[a] / dx, &c, &t);
+        orc_basis(k - 1, t, v);
+        for (int r = 0; r <= k - 1; ++r) d[wrap_index(c - r, M)] += w * s[a] * v[r];
+    }
+}
+
+/* Subsystem III (Sec. 4.2, Eq. spin_rodrigue): with Y = dA_y/dx(x_a),
+ * Z = dA_z/dx(x_a) (V1 gathers of G a_y, G a_z), the spin obeys
+ * ds/dt = r^ s, r^ s = r x s, r = (0, Z, -Y), and the exact step is the
+ * Rodrigues rotation
+ *   s^{n+1} = s + sin(dt|r|)/|r| (r x s) + (1/2) (sin(dt|r|/2)/(|r|/2))^2 r x (r x s). */
+void orc_spin_rotate(int k, long M, double dx, double dt, long np, const double *x,
+                     const double *ga_y, const double *ga_z,
+                     double *sx, double *sy, double *sz)
+{
+    for (long a = 0; a < np; ++a) {
+        double Y = fe_value(k - 1, ga_y, M, dx, x[a]);
+        double Z = fe_value(k - 1, ga_z, M, dx, x[a]);
+        double r0 = 0.0, r1 = Z, r2 = -Y;
+        double nr = sqrt(r1 * r1 + r2 * r2);
+        double s0 = sx[a], s1 = sy[a], s2 = sz[a];
+        /* c1 = r x s, c2 = r x (r x s) */
+        double c1x = r1 * s2 - r2 * s1, c1y = r2 * s0 - r0 * s2, c1z = r0 * s1 - r1 * s0;
+        double c2x = r1 * c1z - r2 * c1y, c2y = r2 * c1x - r0 * c1z, c2z = r0 * c1y - r1 * c1x;
+        double f1, f2;
+        if (nr > 0.0) {
+            f1 = sin(dt * nr) / nr;
+            double h = sin(0.5 * dt * nr) / (0.5 * nr);
+            f2 = 0.5 * h * h;
+        } else {
+            f1 = dt;
+            f2 = 0.5 * dt * dt;
+        }
+        sx[a] = s0 + f1 * c1x + f2 * c2x;
+        sy[a] = s1 + f1 * c1y + f2 * c2y;
+        sz[a] = s2 + f1 * c1z + f2 * c2z;
+    }
+}
+
+/* Zeeman part of the discrete Hamiltonian without hbar:
+ * sum_a w (s_y,a dA_z/dx(x_a) - s_z,a dA_y/dx(x_a)).                   */
+double orc_spin_energy(int k, long M, double dx, long np, const double *x, double w,
+                       const double *sy, const double *sz, const double *ga_y, const double *ga_z)
+{
+    double e = 0.0;
+    for (long a = 0; a < np; ++a) {
+        double Y = fe_value(k - 1, ga_y, M, dx, x[a]);
+        double Z = fe_value(k - 1, ga_z, M, dx, x[a]);
+        e += w * (sy[a] * Z - sz[a] * Y);
+    }
+    return e;
 }
