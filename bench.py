@@ -11,6 +11,10 @@ dt = 0.05.  Forms measured on the same seeded markers:
   * plain FP64 (all double, no warm start).
 A step is one full Lie--Trotter step (subsystem I then II, all fixed-point
 sweeps).  Markers (>= 2.4 GB) exceed the 129 MB L2: no flush between steps.
+Besides the timed steps the line reports the energy and Gauss-law drift of the
+two FP32 forms over the workload's 1,000 steps, the Gauss residual of the three
+deposit accumulations of the FP32 form, and the batched-ensemble workload.  The
+energy and convergence figures come last in the line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -21,7 +25,8 @@ from __future__ import annotations
 
 import os
 
-# the CPU baseline (oracle) is timed single-threaded, BLAS included
+# the oracle's grid algebra runs single-threaded (BLAS included); its marker loops
+# run on one thread or, for the all-core figure, on slices in parallel threads
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -45,11 +50,14 @@ METRIC = "particle-steps/s at rel. energy err ≤1e-10: FP32+learned vs plain FP
 UNIT = "particle-steps/s"
 WORKLOAD = "C2"
 WEIGHTS = os.path.join(ROOT, "paper_2203_06513_gb300", "data", "warm_mlp.npz")
-# Roofline units of the hot kernels (float form, one marker):
-#   k_sweep1: read cell, offset, p, delta; write delta, p_new: 6 x 4 B = 24 B
+# Roofline units of the hot kernels (float form, one marker), as the method must
+# move them (a Picard sweep re-reads every marker because e_x couples them all):
+#   k_sweep1: read x^n (cell + offset, 8 B), p^n (4 B), x^(k) (8 B); write
+#             x^(k+1) (8 B): 28 B (the kernel stores x^(k) as a 4-byte
+#             displacement and writes p^(k+1) every sweep: 24 B moved)
 #   k_sweep2: read cell, offset, p: 12 B
 #   k_warm_mlp: 2 x (6x64 + 64x64 + 64x64 + 64x2) = 17,408 flop (bf16 tensor cores)
-BYTES_SWEEP1 = {1: 24, 0: 44}
+BYTES_SWEEP1 = {1: 28, 0: 44}
 BYTES_SWEEP2 = 12
 FLOP_MLP = 2 * (6 * 64 + 64 * 64 + 64 * 64 + 64 * 2)
 # DRAM bytes (read + write) per marker from ncu captures of the current kernels on
@@ -158,10 +166,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=None):
+def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=None, deposit=0):
     """Advance one replica from host arrays; CUDA-event timing of `steps` steps."""
     x, p, ay, az, ey, ez = arrays
-    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2)
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2, deposit=deposit)
     g = pic.Pic(cfg, x, p, ay, az, ey, ez, stream=stream.cuda_stream)
     if mlp is not None:
         mlp.attach(g)
@@ -181,6 +189,35 @@ def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=
     g.close()
     return {"ms": ms, "iters": it, "iters_warm": it_warm, "timing": tr, "H0": H0, "H": E["total"],
             "gauss": E["gauss"], "rel_energy_err": abs(E["total"] - H0) / abs(H0)}
+
+
+def drift_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None, every=100):
+    """The workload over its configured length: relative energy error and Gauss
+    residual sampled every `every` steps (untimed)."""
+    x, p, ay, az, ey, ez = arrays
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2)
+    g = pic.Pic(cfg, x, p, ay, az, ey, ez, stream=stream.cuda_stream)
+    if mlp is not None:
+        mlp.attach(g)
+    H0 = g.energy()["total"]
+    errs, gauss, sw = [], [], [0, 0]
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        n = min(every, steps - done)
+        i1, i2 = g.step(n)
+        sw[0] += i1
+        sw[1] += i2
+        done += n
+        E = g.energy()
+        errs.append(abs(E["total"] - H0) / abs(H0))
+        gauss.append(E["gauss"])
+    wall = time.perf_counter() - t0
+    g.close()
+    return {"steps": steps, "sample_every": every, "max_rel_energy_err": max(errs),
+            "final_rel_energy_err": errs[-1], "max_gauss_residual": max(gauss),
+            "energy_ok": max(errs) <= 1e-10, "sweeps_per_step": {"I": sw[0] / steps, "II": sw[1] / steps},
+            "wall_s": wall}
 
 
 def e2e_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None):
@@ -248,11 +285,17 @@ def ensemble_run(pic, torch, ws_, ins, steps, warmup, stream, use_graph=True):
     ms = e0.elapsed_time(e1)
     launches = ens.launches - l0
     H = [ens.run(r).energy()["total"] for r in range(len(ws_))]
-    err = max(abs(a - b) / abs(b) for a, b in zip(H, H0))
+    errs = np.array([abs(a - b) / abs(b) for a, b in zip(H, H0)])
+    err = float(errs.max())
     nps = np.array([w.np for w in ws_], dtype=np.float64)
     ens.close()
     total = float(nps.sum())
+    ok = errs <= 1e-10
     return {"value": total * steps / (ms / 1e3), "unit": UNIT, "runs": len(ws_), "total_np": int(total),
+            "value_runs_at_bar": float(nps[ok].sum()) * steps / (ms / 1e3),
+            "runs_above_bar": int((~ok).sum()),
+            "min_np_above_bar": int(nps[~ok].min()) if (~ok).any() else None,
+            "median_rel_energy_err": float(np.median(errs)),
             "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
             "schedule": {"item_markers": im, "blocks_per_sm": bps, "from_cache": cached},
             "sweeps_per_step_mean": {"I": float(sw[:, 0].mean() / steps), "II": float(sw[:, 1].mean() / steps)},
@@ -263,14 +306,15 @@ def ensemble_run(pic, torch, ws_, ins, steps, warmup, stream, use_graph=True):
                         "vth U[0.02,0.15], k=3, dt=0.05, FP32 form" % len(ws_)}
 
 
-def oracle_sample(n_sample: int, steps: int, warmup: int):
-    """The FP64 CPU oracle on n_sample markers of the workload's grid."""
+def oracle_sample(n_sample: int, steps: int, warmup: int, threads: int = 1):
+    """The FP64 CPU oracle on n_sample markers of the workload's grid; its marker
+    loops on `threads` host threads."""
     from oracle import oracle as O
     w = I.workload(WORKLOAD)
     ws_ = I.workload(WORKLOAD, np=n_sample)
     x, p = I.particles(ws_)
     ay, az, ey, ez = I.fields(ws_)
-    orc = O.Oracle(w.L, w.nx, w.degree, ws_.weight, w.dt, w.tol, w.max_iter)
+    orc = O.Oracle(w.L, w.nx, w.degree, ws_.weight, w.dt, w.tol, w.max_iter, threads=threads)
     s = O.initial_state(orc, x, p, ay, az, ey, ez)
     for _ in range(warmup):
         s = orc.step(s)
@@ -280,26 +324,42 @@ def oracle_sample(n_sample: int, steps: int, warmup: int):
     return n_sample * steps / (time.perf_counter() - t0)
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def reference_arm(args, ws, rank):
     """The reference arm: the oracle (plain FP64 CPU program of the same scheme) on
-    a bounded sample of the workload (same grid, fewer markers), host cores."""
+    a bounded sample of the workload (same grid, fewer markers), all host cores,
+    the same --steps and --warmup as the GPU arm."""
     if rank != 0:
         return 0
-    n_sample = int(os.environ.get("PIC_REF_SAMPLE", "100000"))
-    steps = max(1, min(args.steps, 2))
-    warmup = max(0, min(args.warmup, 1))
-    v = oracle_sample(n_sample, steps, warmup)
+    n_sample = int(os.environ.get("PIC_REF_SAMPLE", "40000"))
+    steps, warmup = args.steps, args.warmup
+    cores = host_cores()
+    v = oracle_sample(n_sample, steps, warmup, threads=cores)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * n_sample / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "C2: L=4pi, M=2048, k=3, dt=0.05, pump 0.2, vth 0.1 "
                                    "(oracle on a marker sample)", "sample_np": n_sample},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n_sample} markers on the M=2048 grid, {steps} steps"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_sample} markers on the M=2048 grid, {warmup} + {steps} steps, "
+                                       f"marker loops on {cores} threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _compact_kernel(k: dict) -> dict:
+    out = {key: k[key] for key in ("kernel", "bound", "frac", "achieved", "unit", "launch_ms", "launches")}
+    if "issue" in k:
+        out["issue_frac"] = k["issue"]["frac"]
+    return out
 
 
 def main():
@@ -312,6 +372,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--drift-steps", type=int, default=1000,
+                    help="steps of the untimed energy/Gauss drift runs of the FP32 forms (0: skip)")
+    ap.add_argument("--deposit-variants", type=int, default=5,
+                    help="steps of the FP32 runs that compare the deposit accumulations (0: skip)")
     ap.add_argument("--ensemble-runs", type=int, default=256, help="0: skip the batched-ensemble line")
     ap.add_argument("--ensemble-scale", type=float, default=1.0, help="scale of the runs' marker counts")
     ap.add_argument("--ensemble-host-loop", action="store_true",
@@ -367,6 +431,25 @@ def main():
     e2e = None if args.no_e2e else e2e_run(pic, torch, w, arrays, pic.PIC_FP32, head_warm, args.steps,
                                            stream, mlp)
     barrier()
+    drift = None
+    if args.drift_steps > 0:
+        drift = {"learned" if mlp is not None else "explicit_head":
+                 drift_run(pic, torch, w, arrays, pic.PIC_FP32, head_warm, args.drift_steps, stream, mlp)}
+        drift["explicit"] = drift_run(pic, torch, w, arrays, pic.PIC_FP32, pic.PIC_WARM_EXPLICIT,
+                                      args.drift_steps, stream)
+        barrier()
+    dep = None
+    if args.deposit_variants > 0:
+        dep = {}
+        for name, code in (("float", pic.PIC_ACC_FLOAT), ("compensated", pic.PIC_ACC_COMPENSATED),
+                           ("double", pic.PIC_ACC_DOUBLE)):
+            r = run_form(pic, torch, w, arrays, pic.PIC_FP32, pic.PIC_WARM_EXPLICIT, args.deposit_variants, 0,
+                         stream, deposit=code)
+            dep[name] = {"gauss_residual": r["gauss"], "rel_energy_err": r["rel_energy_err"],
+                         "sweep1_launch_ms": r["timing"]["sweep1_ms"] / max(1, r["timing"]["sweep1_launches"]),
+                         "sweep2_launch_ms": r["timing"]["sweep2_ms"] / max(1, r["timing"]["sweep2_launches"]),
+                         "ms_per_step": r["ms"] / args.deposit_variants}
+        barrier()
     ens = None
     if ens_in is not None:
         del arrays, x, p
@@ -391,13 +474,20 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu:
-            n_cpu = int(os.environ.get("PIC_CPU_SAMPLE", "2000000"))
-            cpu = {"value": oracle_sample(n_cpu, 1, 0), "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{n_cpu} markers on the M=2048 grid, 1 step (single thread)"}
+            n_cpu = int(os.environ.get("PIC_CPU_SAMPLE", "1000000"))
+            cores = host_cores()
+            v1 = oracle_sample(n_cpu, 1, 0, threads=1)
+            vall = oracle_sample(n_cpu, 1, 0, threads=cores)
+            cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{n_cpu} markers on the M=2048 grid, 1 step, marker loops on one thread",
+                   "all_cores": {"value": vall, "cores": cores,
+                                 "sample": f"the same sample, marker loops on {cores} threads"}}
 
         def sweeps(r, k):
             return {"I": r["iters"][0] / k, "II": r["iters"][1] / k}
 
+        # order: contract keys, measurement context, bulky detail, then the energy
+        # and convergence figures last (a reader of the line's tail sees them)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_head / args.steps, "higher_is_better": True,
@@ -408,28 +498,32 @@ def main():
                        "warm_start": "learned (MLP)" if mlp is not None else "explicit (no weights file)",
                        "l2": "inputs larger than L2 (markers %.1f GB)" % (w.np * 24 / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "rel_energy_err": r_head["rel_energy_err"], "energy_ok": r_head["rel_energy_err"] <= 1e-10,
-            "gauss_residual": r_head["gauss"], "sweeps_per_step": sweeps(r_head, args.steps),
-            "warm_start_ms": tr.get("warm_ms"),
-            "fp32_explicit": {"value": v_expl, "unit": UNIT, "ms_per_step": ms_expl / args.steps,
-                              "rel_energy_err": r_expl["rel_energy_err"],
-                              "sweeps_per_step": sweeps(r_expl, args.steps)},
-            "fp64": {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
-                     "rel_energy_err": r64["rel_energy_err"], "gauss_residual": r64["gauss"],
-                     "sweeps_per_step": sweeps(r64, k64),
-                     "speedup_fp32_learned_over_fp64": value / v64},
-            "roofline": dominant,
-            "kernels": kernels,
-            "kernel_ms": {"sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"], "solve": tr["solve_ms"],
-                          "warm_start": tr["warm_ms"]},
             "gpu_launches": tr["launches"],
+            "roofline": dominant,
             "clocks": clk,
             "cpu_baseline": cpu,
-            "ensemble": ens,
             "e2e": None if e2e is None else {
                 "value": R.whole_job_rate(w.np, ws, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d"] / args.steps,
                 "d2h_bytes_per_step": e2e["d2h"] / args.steps},
+            "kernels": [_compact_kernel(k) for k in kernels],
+            "kernel_ms": {"sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"], "solve": tr["solve_ms"],
+                          "warm_start": tr["warm_ms"]},
+            "ensemble": ens,
+            "deposit_accumulation": dep,
+            "fp64": {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+                     "rel_energy_err": r64["rel_energy_err"], "gauss_residual": r64["gauss"],
+                     "sweeps_per_step": sweeps(r64, k64),
+                     "speedup_fp32_learned_over_fp64": value / v64},
+            "fp32_explicit": {"value": v_expl, "unit": UNIT, "ms_per_step": ms_expl / args.steps,
+                              "rel_energy_err": r_expl["rel_energy_err"],
+                              "sweeps_per_step": sweeps(r_expl, args.steps)},
+            "drift": drift,
+            "warm_start_ms": tr.get("warm_ms"),
+            "sweeps_per_step": sweeps(r_head, args.steps),
+            "gauss_residual": r_head["gauss"],
+            "rel_energy_err": r_head["rel_energy_err"],
+            "energy_ok": r_head["rel_energy_err"] <= 1e-10,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

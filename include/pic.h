@@ -3,7 +3,7 @@
  * particle side of the energy-conserving PIC scheme of Y. Li,
  * "Energy conserving particle-in-cell methods for relativistic
  * Vlasov--Maxwell equations of laser-plasma interaction" (arXiv:2203.06513),
- * one dimension, hbar = 0 (no spin).
+ * one dimension, with or without spin (hbar).
  *
  * The discrete system (Sec. 3.1): M uniform periodic cells of width
  * dx = L/M; E_x in the degree-(k-1) spline space V1, E_y, E_z, A_y, A_z in
@@ -76,10 +76,24 @@ extern "C" {
 #define PIC_FIELD_EZ        2
 #define PIC_FIELD_AY        3   /* A_y,h(x_a), V0                           */
 #define PIC_FIELD_AZ        4
+#define PIC_FIELD_EX_PATHAVG 5  /* path mean of E_x,h along x_a -> x_a + d_a (see pic_gather) */
+
+/* deposit accumulation (pic_config.deposit): how the sweeps of the FP32 form
+ * sum the float contributions of the markers a lane holds before they reach the
+ * double grid row.  The FP64 form always accumulates in double. */
+#define PIC_ACC_DEFAULT      0  /* FP32: PIC_ACC_COMPENSATED                                  */
+#define PIC_ACC_FLOAT        1  /* FP32, k = 3 or 5: plain float lane sums, float warp sums    */
+#define PIC_ACC_COMPENSATED  2  /* FP32: compensated float pair per lane (two-sum), double warp sums */
+#define PIC_ACC_DOUBLE       3  /* FP32, k = 3 or 5: double lane sums of the float contributions */
+
+/* time splitting of pic_step (pic_config.splitting) */
+#define PIC_SPLIT_LIE        0  /* Phi_II(dt) o Phi_I(dt), the paper's Lie--Trotter step (Sec. 5) */
+#define PIC_SPLIT_STRANG     1  /* Phi_I(dt/2) o Phi_II(dt) o Phi_I(dt/2) (symmetric, second order) */
 
 /* pic_substep selectors */
 #define PIC_SUBSYSTEM_I     1
 #define PIC_SUBSYSTEM_II    2
+#define PIC_SUBSYSTEM_III   3   /* spin rotation (hbar != 0 only) */
 
 typedef struct pic_handle pic_handle;
 
@@ -100,9 +114,13 @@ typedef struct {
     int32_t precision;   /* PIC_FP64 or PIC_FP32                                    */
     int32_t warm_start;  /* PIC_WARM_*                                              */
     int32_t sort_every;  /* re-sort markers by cell every this many steps (0: only at init) */
+    int32_t deposit;     /* PIC_ACC_* (FP32 form; 0 = default)                      */
+    int32_t splitting;   /* PIC_SPLIT_LIE or PIC_SPLIT_STRANG                       */
+    double  hbar;        /* normalised Planck constant; nonzero turns the spin on
+                            (FP64 form, Lie--Trotter steps, no learned warm start) */
 } pic_config;
 
-/* FP64 arrays of the discrete state u = (X, P, e_x, e_y, e_z, a_y, a_z), Sec. 3.1.
+/* FP64 arrays of the discrete state u = (X, P, S, e_x, e_y, e_z, a_y, a_z), Sec. 3.1.
  * Any member may be NULL where a call says it is ignored. */
 typedef struct {
     double *x;           /* N_p positions in [0, L)        */
@@ -110,15 +128,44 @@ typedef struct {
     double *ex;          /* M coefficients in V1           */
     double *ey, *ez;     /* M coefficients in V0           */
     double *ay, *az;     /* M coefficients in V0           */
+    double *sx, *sy, *sz;/* N_p spin components (read and written only when hbar != 0) */
 } pic_arrays;
 
 /* Create a handle and load the initial state (Sec. 3.1).  Reads x, p, ey, ez,
- * ay, az from `in` (mem space `mem`); in->ex is ignored: e_x is computed from
+ * ay, az (and sx, sy, sz when hbar != 0) from `in` (mem space `mem`); in->ex is
+ * ignored: e_x is computed from
  * the discrete Poisson equation G^T M1 e_x = -Lambda_0(X)^T W 1 + dx 1 with
  * sum_j e_x,j = 0 (Remark 2 of Sec. 4.2, with the neutralising background).
  * Markers are sorted by cell.  On success *out owns the handle. */
 int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem,
              void *stream, pic_handle **out);
+
+/* ---------------------------------------------------------------------
+ * One plasma split over several processes by markers (one GPU each): the
+ * markers are independent given the fields, and the fields couple them only
+ * through sums over markers (Sec. 4.2).  Each process creates its handle
+ * with pic_init_split on its own markers (cfg->np = the local count, weight =
+ * the global L / N_p) and the same initial fields; every later call is made on
+ * every process in the same order.  The library then passes every sum over
+ * markers that the fields need -- the charge of the discrete Poisson equation,
+ * each sweep's current (subsystem I) and susceptibility (subsystem II) deposit,
+ * the spin source, the kinetic, Zeeman and Gauss sums of pic_energy -- and the
+ * fixed-point test's largest marker increment with the error bits through
+ * reduce(ctx, op, buf, n, stream): buf is a device array of n doubles ordered on
+ * `stream` (the handle's); the callback must replace it, in stream order, by the
+ * elementwise sum (op = PIC_REDUCE_SUM) or max (PIC_REDUCE_MAX) over all
+ * processes -- an all-reduce such as ncclAllReduce on that stream -- and return
+ * 0 (nonzero: the call fails with PIC_ERR_CUDA).  Every process then solves the
+ * same grid equations and takes the same decisions.  pic_deposit and pic_gather
+ * act on the local markers only.  Split runs drive their loops from the host.
+ * With reduce = NULL pic_init_split is pic_init.
+ * --------------------------------------------------------------------- */
+#define PIC_REDUCE_SUM      0
+#define PIC_REDUCE_MAX      1
+typedef int (*pic_reduce_fn)(void *ctx, int32_t op, double *buf, int64_t n, void *stream);
+
+int pic_init_split(const pic_config *cfg, const pic_arrays *in, int32_t mem, void *stream,
+                   pic_reduce_fn reduce, void *ctx, pic_handle **out);
 
 /* Copy the current state to `out` (members that are NULL are skipped), in
  * the caller's marker order.  Positions are returned wrapped into [0, L). */
@@ -133,13 +180,25 @@ int pic_get_state(pic_handle *h, const pic_arrays *out, int32_t mem);
  * Accumulation is in double. */
 int pic_deposit(pic_handle *h, int32_t kind, const double *aux, double *out);
 
-/* Gather a field at the current positions: out[N_p] (device), caller order. */
+/* Gather a field at the current positions: out[N_p] (device), caller order.
+ * PIC_FIELD_EX_PATHAVG: on entry out[a] holds a displacement d_a (length units,
+ * |d_a| within the handle's halo, about dt + 2 dx); on return out[a] is the
+ * path mean of E_x,h over the straight path x_a -> x_a + d_a, i.e.
+ * (1/d_a) int Lambda^1(xi) dxi . e_x (Sec. 4.2, subsystem I), and E_x,h(x_a)
+ * where d_a = 0.  Evaluated in double in both forms.  PIC_ERR_NUMERIC when a
+ * displacement is not finite or beyond the halo. */
 int pic_gather(pic_handle *h, int32_t field, double *out);
 
 /* Advance one subsystem by dt (Sec. 4.2).  which = PIC_SUBSYSTEM_I: Picard
  * iteration of the implicit discrete-gradient scheme for (X, P, e_x), one
  * global e_x update per sweep; PIC_SUBSYSTEM_II: fixed point for
- * (e_y, e_z, a_y, a_z) with the exact solve of (M0 + dt^2/4 G^T M1 G).
+ * (e_y, e_z, a_y, a_z) with the exact solve of (M0 + dt^2/4 G^T M1 G);
+ * PIC_SUBSYSTEM_III (hbar != 0): every spin rotated by the exact Rodrigues
+ * formula (Eq. spin_rodrigue), r = (0, dA_z/dx, -dA_y/dx) at its marker.
+ * With hbar != 0 subsystem I's momentum update carries the discrete gradient
+ * of the Zeeman energy, -dt hbar (s_y D2_z - s_z D2_y) with D2 the path mean
+ * of d^2A/dx^2, and subsystem II's right side the source
+ * -dt hbar G^T Lambda_1(X)^T W S_z (y), +dt hbar G^T Lambda_1(X)^T W S_y (z).
  * *iters (may be NULL) receives the number of particle sweeps.
  * Starting fields: subsystem I starts from e_x^n; subsystem II from e_y^n,
  * e_z^n extrapolated in time by the polynomial through the states after the
@@ -149,19 +208,23 @@ int pic_gather(pic_handle *h, int32_t field, double *out);
  * state is then the last iterate). */
 int pic_substep(pic_handle *h, int32_t which, int32_t *iters);
 
-/* nsteps Lie--Trotter steps Phi_II(dt) o Phi_I(dt) (Sec. 5).  Sweep counts
+/* nsteps steps: Lie--Trotter Phi_II(dt) o Phi_I(dt) (Sec. 5; with hbar != 0
+ * Phi_III(dt) o Phi_II(dt) o Phi_I(dt)), or with
+ * splitting = PIC_SPLIT_STRANG the symmetric Phi_I(dt/2) o Phi_II(dt) o
+ * Phi_I(dt/2), each substep the paper's energy-conserving scheme.  Sweep counts
  * summed over the steps go to *iters_I / *iters_II (may be NULL). */
 int pic_step(pic_handle *h, int32_t nsteps, int64_t *iters_I, int64_t *iters_II);
 
-/* Discrete Hamiltonian (Eq. discrete_H, hbar = 0) and Gauss-law residual,
- * evaluated in double from the stored state:
+/* Discrete Hamiltonian (Eq. discrete_H) and Gauss-law residual, evaluated in
+ * double from the stored state (out holds 7 doubles):
  *  out[0] = sum_a w (gamma(p_a, A_h(x_a)) - 1)     kinetic
  *  out[1] = 1/2 e_x^T M1 e_x
  *  out[2] = 1/2 (e_y^T M0 e_y + e_z^T M0 e_z)
  *  out[3] = 1/2 (a_y^T K a_y + a_z^T K a_z),  K = G^T M1 G
- *  out[4] = total = out[0]+out[1]+out[2]+out[3]
- *  out[5] = max_j |(G^T M1 e_x)_j + rho_j - dx|   (discrete Poisson residual) */
-int pic_energy(pic_handle *h, double out[6]);
+ *  out[4] = total = out[0]+out[1]+out[2]+out[3]+out[6]
+ *  out[5] = max_j |(G^T M1 e_x)_j + rho_j - dx|   (discrete Poisson residual)
+ *  out[6] = hbar sum_a w (s_y dA_z/dx - s_z dA_y/dx)(x_a)   Zeeman (0 without spin) */
+int pic_energy(pic_handle *h, double out[7]);
 
 /* Kernel timing of the hot loop (CUDA events on the handle's stream).
  * pic_timing_enable(h, 1) starts recording; pic_timing_read fills
@@ -224,19 +287,23 @@ const char *pic_last_error(const pic_handle *h);
  * device array inside the library (one per GPU that loads the library, kept
  * until the process exits).
  *   out[nx] (device)  = sum_a weight * int_{x_a}^{x_a + disp_a} Lambda^1_i,
- * the same quantity as pic_deposit(PIC_DEP_CURRENT), computed in double and
- * reduced in a fixed order (deterministic).  x[np], disp[np]: device arrays of
- * positions in [0, L) and signed displacements (length units, at most 64 cells).
- * L > 0, 8 <= nx <= 8192 (larger grids exceed the scratch and are rejected with
- * PIC_ERR_INVALID), 2 <= degree <= 5 (degree of V0; the deposit uses degree-1).
- * Work is ordered on `stream` (cudaStream_t as void*); the call returns when
- * out is complete.  The first call on a device (with that device current) sets
- * up the scratch address and kernel attributes; make that first call before
- * any stream capture.  All calls share the one scratch array, which keeps the
- * last call's contents: calls whose kernels overlap on the GPU (other streams
- * or threads) race and give wrong results.  Errors: PIC_ERR_INVALID,
- * PIC_ERR_NUMERIC (a displacement not finite or beyond 64 cells), PIC_ERR_CUDA;
- * message via pic_last_error(NULL). */
+ * the same quantity as pic_deposit(PIC_DEP_CURRENT), computed in double.  Each
+ * block sums its markers with shared-memory atomics (so repeated calls may
+ * differ in the last bits) and the blocks' partial rows are then added in a
+ * fixed order.  x[np], disp[np]: device arrays of positions (any finite value,
+ * read periodically; normally in [0, L)) and signed displacements (length
+ * units, at most 64 cells).  L > 0, 8 <= nx <= 8192 (larger grids exceed the
+ * scratch and are rejected with PIC_ERR_INVALID), 2 <= degree <= 5 (degree of
+ * V0; the deposit uses degree-1).  Work is ordered on `stream` (cudaStream_t
+ * as void*); every call reads a status word back and synchronises that stream,
+ * so it blocks the host until out is complete.  The first call on a device
+ * (with that device current) sets up the scratch address and kernel attributes;
+ * make that first call before any stream capture.  All calls share the one
+ * scratch array, which keeps the last call's contents: calls whose kernels
+ * overlap on the GPU (other streams or threads) race and give wrong results.
+ * Errors: PIC_ERR_INVALID, PIC_ERR_NUMERIC (a position or displacement that is
+ * not finite, or a displacement beyond 64 cells; out is then incomplete),
+ * PIC_ERR_CUDA; message via pic_last_error(NULL). */
 int pic_deposit_current_noalloc(double L, int32_t nx, int32_t degree, int64_t np, double weight,
                                 const double *x, const double *disp, double *out, void *stream);
 

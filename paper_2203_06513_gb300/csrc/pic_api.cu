@@ -123,6 +123,7 @@ static void release(pic_handle *h)
         f(h->jb[b]); f(h->sy[b]); f(h->sz[b]);
     }
     f(h->delta); f(h->pnew); f(h->a0);
+    f(h->spx); f(h->spy); f(h->spz); f(h->sdy); f(h->sdz); f(h->red);
     double *arr[] = {h->ex, h->ey, h->ez, h->ay, h->az, h->ek, h->ebar, h->ga_y, h->ga_z,
                      h->eky, h->ekz, h->aky, h->akz, h->by, h->bz, h->r0y, h->r0z, h->rho,
                      h->work, h->diag, h->d_rowM0, h->d_rowM1, h->d_rowK, h->d_rowPm,
@@ -180,6 +181,29 @@ static int read_ctrl(pic_handle *h)
 }
 
 static int particle_grid(pic_handle *h) { return h->num_sms * 4; }
+
+// Split runs: a sum or max over the processes that hold the plasma's markers.
+static int reduce(pic_handle *h, int op, double *buf, long long n)
+{
+    if (!h->reduce) return PIC_OK;
+    if (h->reduce(h->rctx, op, buf, (int64_t)n, (void *)h->stream) != 0)
+        return fail(h, PIC_ERR_CUDA, "the split run's reduction over processes failed");
+    return PIC_OK;
+}
+
+// After a sweep of a split run: the largest marker increment and the error bits of
+// every process.
+static int reduce_ctrl(pic_handle *h)
+{
+    if (!h->reduce) return PIC_OK;
+    launch_split_pack(h->ctrl, h->red, h->stream);
+    CKL_N("launch_split_pack");
+    int rc;
+    if ((rc = reduce(h, PIC_REDUCE_MAX, h->red, 3))) return rc;
+    launch_split_unpack(h->ctrl, h->red, h->stream);
+    CKL_N("launch_split_unpack");
+    return PIC_OK;
+}
 
 static size_t a256(size_t bytes) { return (bytes + 255) & ~size_t(255); }
 
@@ -263,6 +287,7 @@ static int solve_poisson(pic_handle *h)
 {
     int rc;
     if ((rc = deposit_charge(h, h->rho))) return rc;
+    if ((rc = reduce(h, PIC_REDUCE_SUM, h->rho, h->M))) return rc;
     launch_poisson_rhs(h->M, h->dx, h->rho, h->work, h->stream);
     CKL_N("launch_poisson_rhs");
     return conv_plain(h, h->d_tapM1, h->tapM1_start, h->tapM1_n, h->work, h->ex, nullptr, nullptr);
@@ -272,6 +297,12 @@ static int solve_poisson(pic_handle *h)
 extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem, void *stream,
                         pic_handle **out)
 {
+    return pic_init_split(cfg, in, mem, stream, nullptr, nullptr, out);
+}
+
+extern "C" int pic_init_split(const pic_config *cfg, const pic_arrays *in, int32_t mem, void *stream,
+                              pic_reduce_fn reduce_fn, void *ctx, pic_handle **out)
+{
     if (!cfg || !in || !out) return PIC_ERR_INVALID;
     *out = nullptr;
     const pic_config &c = *cfg;
@@ -279,8 +310,16 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
         c.np > 2147483647LL || !(c.dt > 0) || !(c.tol > 0) || c.max_iter < 1 || c.max_iter > 1000 ||
         (c.precision != PIC_FP64 && c.precision != PIC_FP32) ||
         (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE) || !in->x || !in->p || !in->ay || !in->az ||
-        !std::isfinite(c.weight) || c.warm_start < 0 || c.warm_start > 2 || c.sort_every < 0) {
+        !std::isfinite(c.weight) || c.warm_start < 0 || c.warm_start > 2 || c.sort_every < 0 ||
+        c.deposit < PIC_ACC_DEFAULT || c.deposit > PIC_ACC_DOUBLE ||
+        (c.splitting != PIC_SPLIT_LIE && c.splitting != PIC_SPLIT_STRANG) || !std::isfinite(c.hbar)) {
         g_init_error = "invalid configuration or missing input array";
+        return PIC_ERR_INVALID;
+    }
+    if (c.hbar != 0.0 && (c.precision != PIC_FP64 || c.splitting != PIC_SPLIT_LIE ||
+                          c.warm_start == PIC_WARM_MLP || !in->sx || !in->sy || !in->sz)) {
+        g_init_error = "spin (hbar != 0) needs the FP64 form, Lie--Trotter steps, no learned warm start "
+                       "and the sx, sy, sz arrays";
         return PIC_ERR_INVALID;
     }
     const double dx = c.L / c.nx;
@@ -293,12 +332,29 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
     if (!h) return PIC_ERR_NOMEM;
     h->cfg = c;
     h->stream = (cudaStream_t)stream;
+    h->reduce = reduce_fn;
+    h->rctx = ctx;
     h->M = c.nx;
     h->K = c.degree;
     h->np = c.np;
     h->dx = dx;
     h->fp32 = c.precision == PIC_FP32;
     h->rsize = h->fp32 ? sizeof(float) : sizeof(double);
+    if (!h->fp32) {
+        h->acc = ACC_NATIVE;                    // double lanes: the FP64 form
+        if (c.deposit != PIC_ACC_DEFAULT && c.deposit != PIC_ACC_DOUBLE) {
+            g_init_error = "the FP64 form accumulates deposits in double (deposit must be default or double)";
+            delete h;
+            return PIC_ERR_INVALID;
+        }
+    } else {
+        h->acc = c.deposit == PIC_ACC_FLOAT ? ACC_NATIVE : c.deposit == PIC_ACC_DOUBLE ? ACC_DOUBLE : ACC_COMP;
+    }
+    if (!sweep_variant_ok(c.degree, h->fp32, h->acc)) {
+        g_init_error = "this deposit accumulation is built for degrees 3 and 5 only";
+        delete h;
+        return PIC_ERR_INVALID;
+    }
     // |x^{n+1} - x^n| < dt because |p|/gamma < 1: at most ceil(dt/dx) cells
     h->Dlim = (int)std::ceil(c.dt / dx) + 1;
     h->H = h->K + h->Dlim + 2;
@@ -358,6 +414,17 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
         }
     }
     if ((rc = dalloc(h, &h->diag, 8))) return bail(rc);
+    if (reduce_fn && (rc = dalloc(h, &h->red, 4))) return bail(rc);
+    if (c.hbar != 0.0) {
+        if ((rc = dalloc(h, &h->spx, np)) || (rc = dalloc(h, &h->spy, np)) || (rc = dalloc(h, &h->spz, np)) ||
+            (rc = dalloc(h, &h->sdy, M)) || (rc = dalloc(h, &h->sdz, M)))
+            return bail(rc);
+        const cudaMemcpyKind k = mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        cudaMemcpyAsync(h->spx, in->sx, np * sizeof(double), k, h->stream);
+        cudaMemcpyAsync(h->spy, in->sy, np * sizeof(double), k, h->stream);
+        cudaMemcpyAsync(h->spz, in->sz, np * sizeof(double), k, h->stream);
+        if (spin_optin(h->M)) return bail(fail(h, PIC_ERR_CUDA, "spin deposit shared-memory opt-in failed"));
+    }
     if (h->fp32) {
         if ((rc = dalloc(h, &h->img.a, M)) || (rc = dalloc(h, &h->img.f, M)) || (rc = dalloc(h, &h->img.an, M)) ||
             (rc = dalloc(h, &h->img.ak, M)) || (rc = dalloc(h, &h->img.lo, M)))
@@ -424,8 +491,8 @@ extern "C" int pic_init(const pic_config *cfg, const pic_arrays *in, int32_t mem
                            charge_smem(h->M, h->H)))
         return bail(fail(h, PIC_ERR_CUDA, "cudaFuncSetAttribute failed"));
     {
-        const int b1 = sweep_blocks_per_sm(h->K, h->fp32, 1, h->sweep_block, h->smem1);
-        const int b2 = sweep_blocks_per_sm(h->K, h->fp32, 2, h->sweep_block, h->smem2);
+        const int b1 = sweep_blocks_per_sm(h->K, h->fp32, h->acc, 1, h->sweep_block, h->smem1);
+        const int b2 = sweep_blocks_per_sm(h->K, h->fp32, h->acc, 2, h->sweep_block, h->smem2);
         if (b1 < 1 || b2 < 1) return bail(fail(h, PIC_ERR_INVALID, "sweep kernels do not fit on an SM"));
         h->sweep_grid = h->num_sms * std::min(b1, b2);
     }
@@ -530,32 +597,58 @@ static int timing_fold(pic_handle *h)
     return PIC_OK;
 }
 
-static int substep1(pic_handle *h, int *iters)
+static SpinArgs spin_args(pic_handle *h)
+{
+    SpinArgs a{};
+    a.M = h->M; a.K = h->K; a.np = h->np; a.dx = h->dx; a.w = h->cfg.weight; a.dt = h->cfg.dt;
+    a.hbar = h->cfg.hbar;
+    a.P = cur_parts(h);
+    a.ay = h->ay; a.az = h->az;
+    a.sx = h->spx; a.sy = h->spy; a.sz = h->spz;
+    a.dy = h->sdy; a.dz = h->sdz;
+    a.acc = h->diag + 6;
+    return a;
+}
+
+// Subsystem III: the exact rotation of every spin (markers and fields frozen).
+static int substep3(pic_handle *h)
+{
+    if (h->cfg.hbar == 0.0) return fail(h, PIC_ERR_INVALID, "subsystem III needs hbar != 0");
+    if (launch_spin_rotate(spin_args(h), particle_grid(h), h->stream)) return fail(h, PIC_ERR_INVALID, "bad degree");
+    CKL_N("launch_spin_rotate");
+    return PIC_OK;
+}
+
+// Subsystem I over a time step dt (the handle's dt, or half of it in a Strang step).
+static int substep1(pic_handle *h, int *iters, double dt)
 {
     int rc;
     const RunDesc desc = handle_desc(h);
     launch_prep1(desc, h->stream);
     CKL_N("launch_prep1");
     Sweep1Args a{};
-    a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.np = h->np;
-    a.dx = h->dx; a.dt = h->cfg.dt; a.w = h->cfg.weight;
+    a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.acc = h->acc; a.np = h->np;
+    a.dx = h->dx; a.dt = dt; a.w = h->cfg.weight;
     a.P = cur_parts(h);
     a.ebar = h->ebar; a.ga_y = h->ga_y; a.ga_z = h->ga_z; a.ay = h->ay; a.az = h->az;
     a.ctrl = h->ctrl;
     a.img = h->img;
     a.a0 = h->a0;
+    a.hbar = h->cfg.hbar;
+    a.sy = h->spy;
+    a.sz = h->spz;
     ConvArgs c{};
     c.img = h->img;
     c.M = h->M; c.d_start = h->tapM1_start; c.ntap = h->tapM1_n; c.mode = CONV_SOLVE1; c.ncomp = 1;
     c.taps = h->d_tapM1;
     c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
-    c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6;   // FP32: estimated position error, cells relative to max(1, |delta|)
+    c.dt = dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6;   // FP32: estimated position error, cells relative to max(1, |delta|)
     c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 1; c.ctrl = h->ctrl;
     if (h->cfg.warm_start == PIC_WARM_MLP) {
         // learned proposal for delta^(0), written over the zero iterate
         if (!h->mlp) return fail(h, PIC_ERR_INVALID, "warm_start = PIC_WARM_MLP but no network attached");
         WarmArgs wa{};
-        wa.M = h->M; wa.K = h->K; wa.fp32 = h->fp32; wa.np = h->np; wa.dx = h->dx; wa.dt = h->cfg.dt;
+        wa.M = h->M; wa.K = h->K; wa.fp32 = h->fp32; wa.np = h->np; wa.dx = h->dx; wa.dt = dt;
         wa.P = cur_parts(h);
         wa.ex = h->ex; wa.ay = h->ay; wa.az = h->az;
         wa.params = mlp_params(h->mlp); wa.norm = mlp_norm(h->mlp);
@@ -577,6 +670,7 @@ static int substep1(pic_handle *h, int *iters)
         CKL_N("launch_sweep1");
         if ((rc = timed_end(h, 0))) return rc;
         h->marker_sweeps += h->np;
+        if ((rc = reduce(h, PIC_REDUCE_SUM, h->jb[it & 1], h->M)) || (rc = reduce_ctrl(h))) return rc;
         c.in[0] = h->jb[it & 1];
         c.zero[0] = h->jb[(it + 1) & 1];
         if ((rc = timed_begin(h))) return rc;
@@ -603,10 +697,22 @@ static int substep2(pic_handle *h, int *iters)
     const RunDesc desc = handle_desc(h);
     launch_prep2(desc, h->stream);
     CKL_N("launch_prep2");
+    if (h->cfg.hbar != 0.0) {
+        // Zeeman source of the right side (constant during the loop: x, s frozen)
+        SpinArgs sa = spin_args(h);
+        CK(cudaMemsetAsync(h->sdy, 0, sizeof(double) * h->M, h->stream));
+        CK(cudaMemsetAsync(h->sdz, 0, sizeof(double) * h->M, h->stream));
+        if (launch_spin_deposit(sa, particle_grid(h), h->stream)) return fail(h, PIC_ERR_INVALID, "bad degree");
+        CKL_N("launch_spin_deposit");
+        if ((rc = reduce(h, PIC_REDUCE_SUM, h->sdy, h->M)) || (rc = reduce(h, PIC_REDUCE_SUM, h->sdz, h->M)))
+            return rc;
+        launch_spin_rhs(h->M, h->dx, h->cfg.dt, h->cfg.hbar, h->sdy, h->sdz, h->by, h->bz, h->stream);
+        CKL_N("launch_spin_rhs");
+    }
     if ((rc = conv_plain(h, h->d_tapP, h->tapP_start, h->tapP_n, h->by, h->r0y, h->bz, h->r0z))) return rc;
     Sweep2Args a{};
     a.status = &h->ctrl->status;
-    a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.w = h->cfg.weight;
+    a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.acc = h->acc; a.np = h->np; a.w = h->cfg.weight;
     a.P = cur_parts(h);
     a.an_y = h->ay; a.an_z = h->az; a.ak_y = h->aky; a.ak_z = h->akz;
     a.img = h->img;
@@ -628,6 +734,9 @@ static int substep2(pic_handle *h, int *iters)
             return fail(h, PIC_ERR_INVALID, "sweep2: bad degree");
         CKL_N("launch_sweep2");
         if ((rc = timed_end(h, 1))) return rc;
+        if ((rc = reduce(h, PIC_REDUCE_SUM, h->sy[it & 1], h->M)) ||
+            (rc = reduce(h, PIC_REDUCE_SUM, h->sz[it & 1], h->M)) || (rc = reduce_ctrl(h)))
+            return rc;
         c.in[0] = h->sy[it & 1];
         c.in[1] = h->sz[it & 1];
         c.zero[0] = h->sy[(it + 1) & 1];
@@ -652,9 +761,10 @@ extern "C" int pic_substep(pic_handle *h, int32_t which, int32_t *iters)
 {
     if (!h) return PIC_ERR_INVALID;
     int it = 0, rc;
-    if (which == PIC_SUBSYSTEM_I) rc = substep1(h, &it);
+    if (which == PIC_SUBSYSTEM_I) rc = substep1(h, &it, h->cfg.dt);
     else if (which == PIC_SUBSYSTEM_II) rc = substep2(h, &it);
-    else return fail(h, PIC_ERR_INVALID, "which must be 1 or 2");
+    else if (which == PIC_SUBSYSTEM_III) rc = substep3(h);
+    else return fail(h, PIC_ERR_INVALID, "which must be 1, 2 or 3");
     if (iters) *iters = it;
     if (rc) return rc;
     return sync(h);
@@ -667,10 +777,17 @@ extern "C" int pic_step(pic_handle *h, int32_t nsteps, int64_t *iters_I, int64_t
     long long s1 = 0, s2 = 0;
     int rc = PIC_OK;
     for (int n = 0; n < nsteps; ++n) {
-        int i1 = 0, i2 = 0;
-        if ((rc = substep1(h, &i1))) break;
-        if ((rc = substep2(h, &i2))) break;
-        s1 += i1;
+        int i1 = 0, i2 = 0, i3 = 0;
+        if (h->cfg.splitting == PIC_SPLIT_STRANG) {
+            if ((rc = substep1(h, &i1, 0.5 * h->cfg.dt))) break;
+            if ((rc = substep2(h, &i2))) break;
+            if ((rc = substep1(h, &i3, 0.5 * h->cfg.dt))) break;
+        } else {
+            if ((rc = substep1(h, &i1, h->cfg.dt))) break;
+            if ((rc = substep2(h, &i2))) break;
+            if (h->cfg.hbar != 0.0 && (rc = substep3(h))) break;
+        }
+        s1 += i1 + i3;
         s2 += i2;
         ++h->steps_done;
         if (h->cfg.sort_every > 0 && h->steps_done % h->cfg.sort_every == 0)
@@ -683,7 +800,7 @@ extern "C" int pic_step(pic_handle *h, int32_t nsteps, int64_t *iters_I, int64_t
 }
 
 // ------------------------------------------------------------------ diagnostics
-extern "C" int pic_energy(pic_handle *h, double out[6])
+extern "C" int pic_energy(pic_handle *h, double out[7])
 {
     if (!h || !out) return h ? fail(h, PIC_ERR_INVALID, "out is NULL") : PIC_ERR_INVALID;
     int rc;
@@ -695,6 +812,14 @@ extern "C" int pic_energy(pic_handle *h, double out[6])
     a.c0 = h->ay; a.c1 = h->az; a.acc = h->diag;
     launch_kinetic(a, particle_grid(h), 256, h->stream);
     CKL_N("launch_kinetic");
+    if (h->cfg.hbar != 0.0) {
+        if (launch_spin_energy(spin_args(h), particle_grid(h), h->stream)) return fail(h, PIC_ERR_INVALID, "bad degree");
+        CKL_N("launch_spin_energy");
+    }
+    // split runs: the marker sums of every process (charge, kinetic, Zeeman)
+    if ((rc = reduce(h, PIC_REDUCE_SUM, h->rho, h->M)) || (rc = reduce(h, PIC_REDUCE_SUM, h->diag, 1)) ||
+        (rc = reduce(h, PIC_REDUCE_SUM, h->diag + 6, 1)))
+        return rc;
     launch_energy_grid(h->M, h->K, h->dx, h->d_rowM0, h->d_rowM1, h->d_rowK, h->ex, h->ey, h->ez,
                        h->ay, h->az, h->rho, h->diag, h->stream);
     CKL_N("launch_energy_grid");
@@ -705,7 +830,8 @@ extern "C" int pic_energy(pic_handle *h, double out[6])
     out[1] = d[1];
     out[2] = d[2];
     out[3] = d[3];
-    out[4] = d[0] + d[1] + d[2] + d[3];
+    out[6] = h->cfg.hbar != 0.0 ? h->cfg.hbar * d[6] : 0.0;
+    out[4] = d[0] + d[1] + d[2] + d[3] + out[6];
     out[5] = d[5];
     return PIC_OK;
 }
@@ -737,6 +863,11 @@ extern "C" int pic_get_state(pic_handle *h, const pic_arrays *o, int32_t mem)
         {o->ex, h->ex}, {o->ey, h->ey}, {o->ez, h->ez}, {o->ay, h->ay}, {o->az, h->az}};
     for (auto &f : g)
         if (f.dst) CK(cudaMemcpyAsync(f.dst, f.src, M * sizeof(double), kind, h->stream));
+    if (h->cfg.hbar != 0.0) {
+        struct { double *dst; const double *src; } sp[] = {{o->sx, h->spx}, {o->sy, h->spy}, {o->sz, h->spz}};
+        for (auto &f : sp)
+            if (f.dst) CK(cudaMemcpyAsync(f.dst, f.src, np * sizeof(double), kind, h->stream));
+    }
     return sync(h);
 }
 
@@ -770,7 +901,7 @@ extern "C" int pic_deposit(pic_handle *h, int32_t kind, const double *aux, doubl
         CK(cudaMemsetAsync(out, 0, sizeof(double) * 2 * h->M, h->stream));
         Sweep2Args a{};
         a.status = &h->ctrl->status;
-        a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.w = h->cfg.weight;
+        a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.acc = h->acc; a.np = h->np; a.w = h->cfg.weight;
         a.P = cur_parts(h);
         a.an_y = h->ay; a.an_z = h->az; a.ak_y = aux; a.ak_z = aux + h->M;
         a.s_y = out; a.s_z = out + h->M;
@@ -786,6 +917,24 @@ extern "C" int pic_gather(pic_handle *h, int32_t field, double *out)
 {
     if (!h) return PIC_ERR_INVALID;
     if (!out) return fail(h, PIC_ERR_INVALID, "out is NULL");
+    if (field == PIC_FIELD_EX_PATHAVG) {
+        launch_ctrl_reset(h->ctrl, h->stream);
+        CKL_N("launch_ctrl_reset");
+        DiagArgs a{};
+        a.M = h->M; a.K = h->K; a.fp32 = h->fp32; a.np = h->np; a.dx = h->dx; a.w = h->cfg.weight;
+        a.P = cur_parts(h);
+        a.c0 = h->ex;
+        a.out = out;
+        a.Dlim = h->Dlim;
+        a.status = &h->ctrl->status;
+        if (launch_gather_path(a, particle_grid(h), 256, h->stream)) return fail(h, PIC_ERR_INVALID, "bad degree");
+        CKL_N("launch_gather_path");
+        int rc;
+        if ((rc = read_ctrl(h))) return rc;
+        if (h->h_ctrl->status & STATUS_NUMERIC)
+            return fail(h, PIC_ERR_NUMERIC, "path gather: displacement beyond the halo or not finite");
+        return PIC_OK;
+    }
     const double *coef = nullptr;
     int d = h->K;
     switch (field) {

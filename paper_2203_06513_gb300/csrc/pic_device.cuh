@@ -7,6 +7,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -270,26 +271,80 @@ __device__ __forceinline__ int walk_path(R t0, R d, Visit &&visit)
 }
 
 // ---------------------------------------------------------------------------
+// Accumulators of the per-lane deposit windows.  A lane adds the contributions of
+// the markers it holds between two flushes (about a hundred at 5e4 markers a
+// cell); what it adds are float values in the float form.
+//  AccNative<R>: a plain R sum (the double form; the float form's fastest choice,
+//                whose rounding grows with the number of markers a lane adds).
+//  AccComp:      a compensated float pair (hi, lo): each add is an error-free
+//                two-sum, so hi + lo carries the lane's sum to about double
+//                accuracy (Knuth's TwoSum; the pair is read out in double).
+//  AccDouble:    a double sum of float values (exact adds of the products,
+//                on the FP64 pipe).
+// total() returns the lane's sum in double for the warp reduction.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct AccNative {
+    R v;
+    __device__ __forceinline__ void clear() { v = R(0); }
+    template <typename T> __device__ __forceinline__ void add(T x) { v += x; }
+    __device__ __forceinline__ double total() const { return (double)v; }
+};
+
+struct AccComp {
+    float hi, lo;
+    __device__ __forceinline__ void clear() { hi = 0.f; lo = 0.f; }
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = hi + x;
+        const float bp = s - hi;
+        const float e = (hi - (s - bp)) + (x - bp);   // hi + x = s + e exactly
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double total() const { return (double)hi + (double)lo; }
+};
+
+struct AccDouble {
+    double v;
+    __device__ __forceinline__ void clear() { v = 0.0; }
+    __device__ __forceinline__ void add(float x) { v += (double)x; }
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double total() const { return v; }
+};
+
+// accumulator kinds of the sweeps (pic_config.deposit)
+enum : int { ACC_NATIVE = 0, ACC_COMP = 1, ACC_DOUBLE = 2 };
+template <typename R, int ACC> struct AccOf;
+template <typename R> struct AccOf<R, ACC_NATIVE> { using T = AccNative<R>; };
+template <typename R> struct AccOf<R, ACC_COMP> { using T = AccComp; };
+template <typename R> struct AccOf<R, ACC_DOUBLE> { using T = AccDouble; };
+// the accumulator a form uses unless asked otherwise
+template <typename R> struct DefaultAcc { static constexpr int v = std::is_same<R, float>::value ? ACC_COMP : ACC_NATIVE; };
+
+// ---------------------------------------------------------------------------
 // Per-warp register window for deposits of cell-sorted markers.  Each lane keeps
 // NS partial sums for the consecutive grid nodes b0 .. b0+NS-1 around the warp's
 // base cell; a piece whose NV values fall on nodes cp - r (r = 0..NV-1) goes to
 // slots (cp - base) + OFF - r, chosen by a switch so that the array stays in
 // registers.  flush() sums each slot over the warp (butterfly) and adds it, in
 // double, to the block's shared-memory row; only lanes 0..NS-1 issue an atomic.
+// With a plain float accumulator the butterfly runs in float (the original
+// float form); the other accumulators are reduced in double.
 // ---------------------------------------------------------------------------
-template <typename R, int NS, int NV, int OFF, int OMIN, int OMAX>
+template <typename R, int NS, int NV, int OFF, int OMIN, int OMAX, typename A = AccNative<R>>
 struct DepWindow {
-    R acc[NS];
+    A acc[NS];
     __device__ __forceinline__ void clear()
     {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) acc[s] = R(0);
+        for (int s = 0; s < NS; ++s) acc[s].clear();
     }
     template <int O>
     __device__ __forceinline__ void add_at(const R *v)
     {
 #pragma unroll
-        for (int r = 0; r < NV; ++r) acc[O + OFF - r] += v[r];
+        for (int r = 0; r < NV; ++r) acc[O + OFF - r].add(v[r]);
     }
     // returns false when the piece lies outside the window (caller takes the slow path)
     __device__ __forceinline__ bool put(int o, const R *v)
@@ -311,16 +366,29 @@ struct DepWindow {
     __device__ __forceinline__ void flush(double *s_row, int row0, double scale)
     {
         const int lane = threadIdx.x & 31;
-        R mine = R(0);
+        if constexpr (std::is_same<A, AccNative<float>>::value) {
+            float mine = 0.f;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            R v = acc[s];
+            for (int s = 0; s < NS; ++s) {
+                float v = acc[s].v;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == s) mine = v;
-            acc[s] = R(0);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == s) mine = v;
+                acc[s].clear();
+            }
+            if (lane < NS && mine != 0.f) atomicAdd(&s_row[row0 + lane], scale * (double)mine);
+        } else {
+            double mine = 0.0;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                double v = acc[s].total();
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == s) mine = v;
+                acc[s].clear();
+            }
+            if (lane < NS && mine != 0.0) atomicAdd(&s_row[row0 + lane], scale * mine);
         }
-        if (lane < NS && mine != R(0)) atomicAdd(&s_row[row0 + lane], scale * (double)mine);
     }
 };
 

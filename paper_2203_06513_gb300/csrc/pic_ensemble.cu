@@ -113,7 +113,7 @@ static void build_tables(pic_ensemble *e)
 
         Sweep1Args &a = e->a1[r];
         a = Sweep1Args{};
-        a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.np = h->np;
+        a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.acc = h->acc; a.np = h->np;
         a.dx = h->dx; a.dt = h->cfg.dt; a.w = h->cfg.weight;
         a.P = P;
         a.ebar = h->ebar; a.ga_y = h->ga_y; a.ga_z = h->ga_z; a.ay = h->ay; a.az = h->az;
@@ -140,7 +140,7 @@ static void build_tables(pic_ensemble *e)
         Sweep2Args &b = e->a2[r];
         b = Sweep2Args{};
         b.status = &h->ctrl->status;
-        b.M = h->M; b.H = h->H; b.K = h->K; b.fp32 = h->fp32; b.np = h->np; b.w = h->cfg.weight;
+        b.M = h->M; b.H = h->H; b.K = h->K; b.fp32 = h->fp32; b.acc = h->acc; b.np = h->np; b.w = h->cfg.weight;
         b.P = P;
         b.an_y = h->ay; b.an_z = h->az; b.ak_y = h->aky; b.ak_z = h->akz;
         b.s_y = h->sy[0]; b.s_z = h->sz[0];
@@ -351,6 +351,13 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
         set_thread_error("ensemble: the learned warm start is not available for ensembles");
         return PIC_ERR_INVALID;
     }
+    for (int r = 0; r < nruns; ++r)
+        if ((cfgs[r].deposit != PIC_ACC_DEFAULT && cfgs[r].deposit != PIC_ACC_COMPENSATED &&
+             !(cfgs[r].precision == PIC_FP64 && cfgs[r].deposit == PIC_ACC_DOUBLE)) ||
+            cfgs[r].splitting != PIC_SPLIT_LIE || cfgs[r].hbar != 0.0) {
+            set_thread_error("ensemble: runs use the default deposit accumulation, Lie--Trotter steps and no spin");
+            return PIC_ERR_INVALID;
+        }
     pic_ensemble *e = new (std::nothrow) pic_ensemble();
     if (!e) return PIC_ERR_NOMEM;
     e->stream = (cudaStream_t)stream;
@@ -386,8 +393,8 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
     }
     e->fin_grid = (int)std::min<long long>(std::max<long long>((npmax + 255) / 256, 1), 64);
     {
-        const int b1 = sweep_blocks_per_sm(e->K, e->fp32, 1, kSweepThreads, e->smem1);
-        const int b2 = sweep_blocks_per_sm(e->K, e->fp32, 2, kSweepThreads, e->smem2);
+        const int b1 = sweep_blocks_per_sm(e->K, e->fp32, e->fp32 ? ACC_COMP : ACC_NATIVE, 1, kSweepThreads, e->smem1);
+        const int b2 = sweep_blocks_per_sm(e->K, e->fp32, e->fp32 ? ACC_COMP : ACC_NATIVE, 2, kSweepThreads, e->smem2);
         e->bps_max = std::max(1, std::min(b1, b2));
         e->bps = e->bps_max;
     }

@@ -744,3 +744,55 @@ int launch_ctrl_reset(DevCtrl *ctrl, cudaStream_t s)
 }
 
 }  // namespace pic
+
+// Zeeman source of subsystem II (Sec. 4.2): b_y -= dt hbar (G^T d_z)_j and
+// b_z += dt hbar (G^T d_y)_j, (G^T v)_j = (v_j - v_{j+1}) / dx, d = Lambda_1(X)^T W S.
+__global__ void k_spin_rhs(int M, double dx, double c, const double *dy, const double *dz, double *by,
+                           double *bz)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int jp = j + 1 == M ? 0 : j + 1;
+    by[j] -= c * (dz[j] - dz[jp]) / dx;
+    bz[j] += c * (dy[j] - dy[jp]) / dx;
+}
+
+namespace pic {
+int launch_spin_rhs(int M, double dx, double dt, double hbar, const double *dy, const double *dz, double *by,
+                    double *bz, cudaStream_t s)
+{
+    k_spin_rhs<<<(M + 255) / 256, 256, 0, s>>>(M, dx, dt * hbar, dy, dz, by, bz);
+    return 0;
+}
+}  // namespace pic
+
+// Split runs (markers over several processes): the marker-side results of a sweep
+// that every process must agree on, packed as doubles for a max-reduction over
+// processes: the largest position increment, and one entry per error bit (the max
+// of 0/1 entries is their logical or).
+__global__ void k_split_pack(const pic::DevCtrl *c, double *buf)
+{
+    buf[0] = pic::bits_to_double(c->dmax_bits);
+    buf[1] = (c->status & pic::STATUS_NUMERIC) ? 1.0 : 0.0;
+    buf[2] = (c->status & pic::STATUS_TIMEOUT) ? 1.0 : 0.0;
+}
+
+__global__ void k_split_unpack(pic::DevCtrl *c, const double *buf)
+{
+    c->dmax_bits = (unsigned long long)__double_as_longlong(buf[0]);
+    if (buf[1] != 0.0) c->status |= pic::STATUS_NUMERIC;
+    if (buf[2] != 0.0) c->status |= pic::STATUS_TIMEOUT;
+}
+
+namespace pic {
+int launch_split_pack(const DevCtrl *c, double *buf, cudaStream_t s)
+{
+    k_split_pack<<<1, 1, 0, s>>>(c, buf);
+    return 0;
+}
+int launch_split_unpack(DevCtrl *c, const double *buf, cudaStream_t s)
+{
+    k_split_unpack<<<1, 1, 0, s>>>(c, buf);
+    return 0;
+}
+}  // namespace pic

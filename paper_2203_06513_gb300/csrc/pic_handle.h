@@ -18,6 +18,7 @@ struct pic_handle {
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
     int M = 0, K = 0, H = 0, Dlim = 0, fp32 = 0;
+    int acc = 0;                    // deposit window accumulator of the sweeps (pic::ACC_*)
     long long np = 0;
     double dx = 0.0;
     size_t rsize = 8;               // bytes of one particle real
@@ -31,6 +32,15 @@ struct pic_handle {
     int cur = 0;
     void *delta = nullptr, *pnew = nullptr;
     void *a0 = nullptr;             // subsystem-I start-point cache (4 reals a marker; FP64 form)
+    // spin (hbar != 0, FP64 form): components in caller order, and the spin deposits
+    double *spx = nullptr, *spy = nullptr, *spz = nullptr;
+    double *sdy = nullptr, *sdz = nullptr;
+
+    // split run: the markers of one plasma spread over several processes; marker
+    // sums and maxima go through this reduction (NULL: all markers are here)
+    pic_reduce_fn reduce = nullptr;
+    void *rctx = nullptr;
+    double *red = nullptr;          // 4 doubles: packed control entries
 
     // grid state (double)
     double *ex = nullptr, *ey = nullptr, *ez = nullptr, *ay = nullptr, *az = nullptr;

@@ -39,6 +39,7 @@ struct StageImages {
 
 struct Sweep1Args {
     int M, H, Dlim, K, fp32;
+    int acc;            // deposit window accumulator (ACC_*)
     long long np;
     double dx, dt, w;
     PartPtrs P;
@@ -56,10 +57,14 @@ struct Sweep1Args {
     // start-point cache, 4 reals a marker (A_y(x^n), A_z(x^n), gamma(p^n, A(x^n)),
     // unused): written by the loop's first sweep, read by the later ones; NULL: none
     void *a0;
+    // spin (double form, hbar != 0): spin components in caller order (indexed by id)
+    double hbar;
+    const double *sy, *sz;
 };
 
 struct Sweep2Args {
     int M, H, K, fp32;
+    int acc;            // deposit window accumulator (ACC_*)
     long long np;
     double w;
     PartPtrs P;
@@ -91,6 +96,8 @@ struct DiagArgs {
     const double *c0, *c1;  // field coefficients (gather: c0; kinetic: a_y, a_z)
     double *out;            // gather output (caller order) or rho
     double *acc;            // kinetic sum
+    int Dlim;               // path gathers: largest displacement (cells)
+    int *status;            // path gathers: error bits (STATUS_NUMERIC)
 };
 
 int launch_sweep1(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s);
@@ -101,6 +108,7 @@ int launch_current(const CurrentArgs &a, int grid, int block, size_t smem, cudaS
 int launch_charge(const DiagArgs &a, int grid, int block, size_t smem, cudaStream_t s);
 size_t charge_smem(int M, int H);
 int launch_gather(const DiagArgs &a, int field_degree, int grid, int block, cudaStream_t s);
+int launch_gather_path(const DiagArgs &a, int grid, int block, cudaStream_t s);
 int launch_kinetic(const DiagArgs &a, int grid, int block, cudaStream_t s);
 int launch_finalize1(int fp32, long long np, int M, PartPtrs P, bool zero_delta, int grid, int block,
                      cudaStream_t s);
@@ -108,7 +116,9 @@ int launch_load(int fp32, long long np, int M, double dx, const double *x, const
                 PartPtrs P, int grid, int block, cudaStream_t s);
 int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, double *p,
                  int grid, int block, cudaStream_t s);
-int sweep_blocks_per_sm(int K, int fp32, int which, int block, size_t smem);
+int sweep_blocks_per_sm(int K, int fp32, int acc, int which, int block, size_t smem);
+// whether the sweep kernels are built for (degree, form, accumulator)
+bool sweep_variant_ok(int K, int fp32, int acc);
 int launch_sort(int fp32, long long np, int M, double tau, PartPtrs src, PartPtrs dst,
                 int32_t *counts, int grid, int block, cudaStream_t s);
 
@@ -139,6 +149,34 @@ struct ConvArgs {
 };
 
 int launch_conv(const ConvArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------- spin (double form)
+// Spin components are kept in caller order (sx[id], sy[id], sz[id]).
+struct SpinArgs {
+    int M, K;
+    long long np;
+    double dx, w, dt, hbar;
+    PartPtrs P;                 // markers in stored order (cell, t as double, id)
+    const double *ay, *az;
+    double *sx, *sy, *sz;
+    double *dy, *dz;            // spin deposit outputs (M each)
+    double *acc;                // Zeeman energy sum (without hbar)
+};
+// d_y,i = sum_a w s_y,a Lambda^1_i(x_a), d_z likewise (Lambda_1(X)^T W S of subsystem II)
+int launch_spin_deposit(const SpinArgs &a, int grid, cudaStream_t s);
+// subsystem III: exact rotation of every spin
+int launch_spin_rotate(const SpinArgs &a, int grid, cudaStream_t s);
+// *acc += sum_a w (s_y dA_z/dx - s_z dA_y/dx)(x_a)
+int launch_spin_energy(const SpinArgs &a, int grid, cudaStream_t s);
+// b_y -= dt hbar (G^T d_z), b_z += dt hbar (G^T d_y), (G^T v)_j = (v_j - v_{j+1}) / dx
+int launch_spin_rhs(int M, double dx, double dt, double hbar, const double *dy, const double *dz,
+                    double *by, double *bz, cudaStream_t s);
+// raise the spin deposit's dynamic shared-memory limit for a grid of M cells
+int spin_optin(int M);
+
+// split runs: buf[0..2] = (max increment, numeric bit, timeout bit) of the control block
+int launch_split_pack(const DevCtrl *c, double *buf, cudaStream_t s);
+int launch_split_unpack(DevCtrl *c, const double *buf, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched ensemble
 // Many independent runs advance together: one launch of each kernel covers every

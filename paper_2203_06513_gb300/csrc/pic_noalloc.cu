@@ -37,8 +37,10 @@ struct NoallocArgs {
     int *status;        // scratch header
 };
 
-// Per block: deposit its markers into a shared-memory row, then store the row
-// (no atomics outside the block, so the result does not depend on timing).
+// Per block: deposit its markers into a shared-memory row, then store the row.
+// Inside a block the row is accumulated with shared-memory atomics, whose order
+// depends on warp scheduling, so repeated calls may differ in the last bits;
+// the rows of the blocks are then summed in a fixed order.
 template <int K>
 __global__ void __launch_bounds__(256) k_noalloc_rows(NoallocArgs A)
 {
@@ -52,13 +54,17 @@ __global__ void __launch_bounds__(256) k_noalloc_rows(NoallocArgs A)
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
         const double u = A.x[a] / A.dx;
-        const double f = ::floor(u);
-        double t0 = u - f;
+        const double d = A.disp[a] / A.dx;
+        // positions and displacements must be finite (an infinite position would
+        // turn into NaN offsets below) and a displacement may span at most kMaxDisp cells
+        if (!isfinite(u) || !isfinite(d) || !(fabs(d) <= (double)kMaxDisp)) { bad = true; continue; }
+        // periodic: wrap the cell coordinate into [0, M) before taking its integer part
+        const double uw = u - (double)A.M * ::floor(u / (double)A.M);
+        const double f = ::floor(uw);
+        double t0 = uw - f;
         int c0 = (int)f;
         if (t0 >= 1.0) { t0 = 0.0; c0 += 1; }
         c0 = pic::wrap_cell(c0, A.M);
-        const double d = A.disp[a] / A.dx;
-        if (!(fabs(d) <= (double)kMaxDisp) || !(u == u)) { bad = true; continue; }
         pic::walk_path<K, double>(t0, d, [&](int c, double h, const double *m, bool) {
             const double hw = wdx * h;
 #pragma unroll
@@ -186,6 +192,6 @@ extern "C" int pic_deposit_current_noalloc(double L, int32_t nx, int32_t degree,
     if (e != cudaSuccess) return fail_nohandle(PIC_ERR_CUDA, cudaGetErrorString(e));
     if (status)
         return fail_nohandle(PIC_ERR_NUMERIC,
-                             "pic_deposit_current_noalloc: a displacement is not finite or spans more than 64 cells");
+                             "pic_deposit_current_noalloc: a position or displacement is not finite, or a displacement spans more than 64 cells");
     return PIC_OK;
 }

@@ -240,7 +240,72 @@ __device__ __forceinline__ void start_cache_load(const void *base, long long a, 
     }
 }
 
-template <int K, typename R>
+// Deposit of one marker's path integral as a difference of the cumulative sums
+// C_i(x) = sum_{j >= i} Lambda^0_j(x) at its two ends (see sweep1_range):
+// S0, S1 are the partial sums at x^n (cell c0) and x^(k+1) (cell c0 + n), in
+// the scaled units of bspline_scaled.  For |n| <= kCdMax the nonzero values lie
+// on the KB = K + kCdMax nodes a - r (a = max(c0, c0 + n)) and go into the warp
+// window as one block:  val[r] = C(S1, r - nl) - C(S0, r - nr), nl = max(0, -n),
+// nr = max(0, n), C(S, i) = 0 (i < 0), S[i] (i < K), K! (i >= K).  Longer paths
+// (rare) add the same values node by node to the shared row.
+constexpr int kCdMax = 2;
+
+template <int K, int NL, int NR, typename R>
+__device__ __forceinline__ void cdiff_block(const R *S0, const R *S1, R *val)
+{
+    constexpr int KB = K + kCdMax;
+    const R one = R(Fact<K>::v);
+#pragma unroll
+    for (int r = 0; r < KB; ++r) {
+        const int i1 = r - NL, i0 = r - NR;
+        const R c1 = i1 < 0 ? R(0) : (i1 < K ? S1[i1 < K ? i1 : 0] : one);
+        const R c0 = i0 < 0 ? R(0) : (i0 < K ? S0[i0 < K ? i0 : 0] : one);
+        val[r] = c1 - c0;
+    }
+}
+
+template <int K, class Win, typename R>
+__device__ __forceinline__ void deposit_cdiff(Win &win, const R *S0, const R *S1, int n, int c0, int wb, int H,
+                                              double *s_acc, double wdx)
+{
+    constexpr int KB = K + kCdMax;
+    R val[KB];
+    switch (n) {
+    case -2: cdiff_block<K, 2, 0>(S0, S1, val); break;
+    case -1: cdiff_block<K, 1, 0>(S0, S1, val); break;
+    case 0: cdiff_block<K, 0, 0>(S0, S1, val); break;
+    case 1: cdiff_block<K, 0, 1>(S0, S1, val); break;
+    case 2: cdiff_block<K, 0, 2>(S0, S1, val); break;
+    default: {
+        // a path across more than kCdMax knots: node by node into the shared row
+        const int nl = n < 0 ? -n : 0, nr = n > 0 ? n : 0;
+        const int a = c0 + nr;
+        const R one = R(Fact<K>::v);
+        for (int r = 0; r < K + nl + nr; ++r) {
+            const int i1 = r - nl, i0 = r - nr;
+            R c1 = R(0), cc0 = R(0);
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                if (i1 == q) c1 = S1[q];
+                if (i0 == q) cc0 = S0[q];
+            }
+            if (i1 >= K) c1 = one;
+            if (i0 >= K) cc0 = one;
+            const R d = c1 - cc0;
+            if (d != R(0)) atomicAdd(&s_acc[a - r + H], wdx * (double)d);
+        }
+        return;
+    }
+    }
+    const int a = c0 + (n > 0 ? n : 0);
+    if (!win.put(a - wb, val)) {
+#pragma unroll
+        for (int r = 0; r < KB; ++r)
+            if (val[r] != R(0)) atomicAdd(&s_acc[a - r + H], wdx * (double)val[r]);
+    }
+}
+
+template <int K, typename R, int ACC>
 __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg, long long end,
                                              unsigned char *smem, unsigned long long &q)
 {
@@ -325,13 +390,15 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     R *__restrict__ dp = static_cast<R *>(A.P.delta);
     R *__restrict__ pnp = static_cast<R *>(A.P.pnew);
     const R tau = (R)(A.dt / A.dx);
-    const double wdx = A.w * A.dx / S1;      // deposit flush scale
+    const double wdx = A.w * A.dx * inv_fact;   // deposit flush scale (C in units of K!)
     const R dlim = (R)A.Dlim;
     const R one = R(1);
     R dmax = R(0);
     bool bad = false;
-    // window: pieces in cells wb-3 .. wb+3, V1 nodes wb-K-2 .. wb+3
-    DepWindow<R, K + 6, K, K + 2, -3, 3> win;
+    // window: blocks of KB = K + kCdMax values anchored at the larger end cell,
+    // max(c0, c1) - wb in [0, 3]; V1 nodes wb - KB + 1 .. wb + 3
+    constexpr int KB = K + kCdMax;
+    DepWindow<R, KB + 3, KB, KB - 1, 0, 3, typename AccOf<R, ACC>::T> win;
     win.clear();
     int wb = INT_MIN;
 
@@ -349,14 +416,16 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
             if (lead == INT_MAX) break;                    // whole warp past the chunk end
             if (lead != wb) {
-                if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
+                if (wb != INT_MIN) win.flush(s_acc, wb - (KB - 1) + H, wdx);
                 wb = lead;
             }
             const unsigned amask = __ballot_sync(0xffffffffu, act);
             if (!act) continue;
             const R t0 = s_t(b)[jl];
             const R pn = s_p(b)[jl];
-            R v[K + 1];
+            // basis at the start point: A(x^n) and the partial sums of the deposit
+            R v0[K + 1];
+            bspline_scaled<K, R>(t0, v0);
             // A(x^n) and gamma(p^n, A(x^n)) do not change during the loop: in the
             // double form the first sweep stores them and the later ones read them
             // back (the float form recomputes: there the extra bytes cost more)
@@ -366,13 +435,12 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             if (cached) {
                 start_cache_load<R>(A.a0, a, A0y, A0z, g0);
             } else {
-                bspline_scaled<K, R>(t0, v);
 #pragma unroll
                 for (int r = 0; r <= K; ++r) {
                     R y, z;
                     F.aa(c0 - r + H, y, z);
-                    A0y += y * v[r];
-                    A0z += z * v[r];
+                    A0y += y * v0[r];
+                    A0z += z * v0[r];
                 }
                 g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
                 if constexpr (!Real<R>::fp32)
@@ -381,21 +449,14 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             R dold = warm ? fdiv_(tau * pn, g0) : s_d(b)[jl];
             if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
 
-            const R s = t0 + dold;
-            const R fs = floor_(s);
-            const int c1 = c0 + (int)fs;
-            bspline_scaled<K, R>(s - fs, v);
-            R A1y = R(0), A1z = R(0);
-#pragma unroll
-            for (int r = 0; r <= K; ++r) {
-                R y, z;
-                F.aa(c1 - r + H, y, z);
-                A1y += y * v[r];
-                A1z += z * v[r];
-            }
-
-            R Eb = R(0), Dy = R(0), Dz = R(0);
-            const R invd = (dold != R(0)) ? one / dold : R(0);
+            // Path integrals along x^n -> x^(k) (cell units), unnormalised:
+            //   EI = int ebar dt,  DI = int dA/dt dt / DK,
+            // the path means being EI/dold and DK DI/dold (the means at t0 when
+            // dold = 0).  A(x^(k)) = A(x^n) + DK DI exactly for the staged field (the
+            // staged differences of a are those of the staged coefficients), so the
+            // end point needs no basis evaluation of its own.
+            R EI = R(0), DIy = R(0), DIz = R(0);
+            const bool still = dold == R(0);
             const int n1 = __reduce_max_sync(amask, path_pieces(t0, dold));
             walk_uniform<K, R>(t0, dold, n1, [&](int c, R h, const R *m, int p) {
                 R e = R(0), gy = R(0), gz = R(0);
@@ -407,32 +468,81 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
                     gy += m[r] * y;
                     gz += m[r] * z;
                 }
-                const R f = (dold != R(0)) ? h * invd : (p == 0 ? one : R(0));
-                Eb += f * e;
-                Dy += f * gy;
-                Dz += f * gz;
+                const R hw = still ? (p == 0 ? one : R(0)) : h;
+                EI += hw * e;
+                DIy += hw * gy;
+                DIz += hw * gz;
             });
-            Dy *= R(DK);
-            Dz *= R(DK);
+            const R dn = still ? one : dold;
+            const R A1y = A0y + R(DK) * (still ? R(0) : DIy);
+            const R A1z = A0z + R(DK) * (still ? R(0) : DIz);
 
+            // p^(k+1) = p^n + tau (Ebar - (A1 + A0).D / (g1 + g0)) with Ebar = EI/dn,
+            // D = DK DI/dn, as one division
             const R q1 = one + A1y * A1y + A1z * A1z;
             const R g1 = sqrt_(q1 + pn * pn);
-            const R pnew = pn + tau * (Eb - fdiv_((A1y + A0y) * Dy + (A1z + A0z) * Dz, g1 + g0));
+            const R G = g1 + g0;
+            const R num = EI * G - R(DK) * ((A1y + A0y) * DIy + (A1z + A0z) * DIz);
+            R spin_term = R(0);
+            if constexpr (!Real<R>::fp32) {
+                if (A.hbar != 0.0) {
+                    // discrete gradient of the Zeeman energy: D2 = path mean of d^2A/dx^2
+                    // along x^n -> x^(k) (the exact difference quotient of dA/dx; its
+                    // limit at rest is the point value), from the second differences of
+                    // the staged coefficients and the means of the degree-(K-2) pieces
+                    const int id = A.P.id[a];
+                    double D2y = 0.0, D2z = 0.0;
+                    const double invd = still ? 0.0 : 1.0 / dold;
+                    walk_path<K - 1, double>(t0, dold, [&](int c, double h, const double *m2, bool single) {
+                        double gy = 0.0, gz = 0.0;
+#pragma unroll
+                        for (int r = 0; r <= K - 2; ++r) {
+                            const int i = c0 + c - r + H;
+                            double y0, z0, y1, z1, y2, z2;
+                            F.aa(i, y0, z0);
+                            F.aa(i - 1, y1, z1);
+                            F.aa(i - 2, y2, z2);
+                            gy += m2[r] * ((y0 - y1) - (y1 - y2));
+                            gz += m2[r] * ((z0 - z1) - (z1 - z2));
+                        }
+                        const double f = single ? 1.0 : h * invd;
+                        D2y += f * gy;
+                        D2z += f * gz;
+                    });
+                    // staged coefficients are a / K!; D2 is per cell^2, the update per dx
+                    const double fac = (double)Fact<K>::v / A.dx;
+                    spin_term = A.hbar * fac * (A.sy[id] * D2z - A.sz[id] * D2y);
+                }
+            }
+            const R pnew = pn + tau * (fdiv_(num, dn * G) - spin_term);
             const R g2 = sqrt_(q1 + pnew * pnew);
             R dnew = fdiv_(tau * (pn + pnew), g1 + g2);
             if (!(fabs(dnew) <= dlim)) { bad = true; dnew = R(0); }
 
-            const int n2 = __reduce_max_sync(amask, path_pieces(t0, dnew));
-            walk_uniform<K, R>(t0, dnew, n2, [&](int c, R h, const R *m, int) {
-                R val[K];
+            // Deposit j_i += w int_{x^n}^{x^(k+1)} Lambda^1_i = w dx (C_i(x^(k+1)) - C_i(x^n))
+            // with C_i(x) = sum_{j >= i} Lambda^0_j(x): the derivative relation of Sec. 3.1
+            // telescoped (the identity behind the paper's discrete Gauss law).  In a
+            // cell c at offset t, C_{c-r} = S[r] = sum_{r' <= r} N^K(r' + t) for
+            // r < K, 1 below, 0 above; here in the scaled units of bspline_scaled
+            // (K! N^K, so "1" is K!).  The end point's cell is that of finalize.
+            {
+                const R s1 = t0 + dnew;
+                const R f1 = floor_(s1);
+                int n = (int)f1;
+                R t1 = s1 - f1;
+                if (t1 >= one) { t1 = R(0); n += 1; }
+                R v1[K + 1];
+                bspline_scaled<K, R>(t1, v1);
+                R S0[K], S1[K];
+                S0[0] = v0[0];
+                S1[0] = v1[0];
 #pragma unroll
-                for (int r = 0; r < K; ++r) val[r] = h * m[r];
-                if (!win.put(c0 + c - wb, val)) {
-#pragma unroll
-                    for (int r = 0; r < K; ++r) atomicAdd(&s_acc[c0 + c - r + H], wdx * (double)val[r]);
+                for (int r = 1; r < K; ++r) {
+                    S0[r] = S0[r - 1] + v0[r];
+                    S1[r] = S1[r - 1] + v1[r];
                 }
-            });
-
+                deposit_cdiff<K>(win, S0, S1, n, c0, wb, H, s_acc, wdx);
+            }
             R inc = fabs(dnew - dold);
             if (Real<R>::fp32) inc = __fdividef(inc, fmax(one, fabs(dnew)));   // convergence metric only
             dmax = (inc > dmax || inc != inc) ? inc : dmax;
@@ -442,7 +552,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
         tile_release<NS>(Bars, q0 + i);
         if (threadIdx.x == 0 && i + NS < ntile) issue(i + NS);
     }
-    if (wb != INT_MIN) win.flush(s_acc, wb - (K + 2) + H, wdx);
+    if (wb != INT_MIN) win.flush(s_acc, wb - (KB - 1) + H, wdx);
     if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
     __syncthreads();
     const bool timeout = *reinterpret_cast<volatile int *>(&Bars.abort) != 0;
@@ -459,7 +569,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     return !timeout;
 }
 
-template <int K, typename R>
+template <int K, typename R, int ACC>
 __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1(Sweep1Args A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -467,7 +577,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
     long long beg, end;
     block_chunk(A.np, beg, end);
     unsigned long long q = 0;
-    sweep1_range<K, R>(A, beg, end, smem, q);
+    sweep1_range<K, R, ACC>(A, beg, end, smem, q);
 }
 
 size_t sweep1_smem(int M, int H, int fp32)
@@ -478,23 +588,32 @@ size_t sweep1_smem(int M, int H, int fp32)
            (fp32 ? FieldTile<float>::bytes(W) : FieldTile<double>::bytes(W));
 }
 
-template <typename R>
-static int launch_sweep1_t(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s)
+// Instantiations: double form with double windows; float form with compensated
+// windows for every degree, and with plain float or double windows (kept to
+// compare the deposit accumulations) for k = 3 and 5.
+#define PIC_FOR_SWEEP_VARIANTS(X)                                                                   \
+    X(2, double, ACC_NATIVE) X(3, double, ACC_NATIVE) X(4, double, ACC_NATIVE) X(5, double, ACC_NATIVE) \
+    X(2, float, ACC_COMP) X(3, float, ACC_COMP) X(4, float, ACC_COMP) X(5, float, ACC_COMP)             \
+    X(3, float, ACC_NATIVE) X(5, float, ACC_NATIVE) X(3, float, ACC_DOUBLE) X(5, float, ACC_DOUBLE)
+
+bool sweep_variant_ok(int K, int fp32, int acc)
 {
-    switch (a.K) {
-    case 2: k_sweep1<2, R><<<grid, block, smem, s>>>(a); break;
-    case 3: k_sweep1<3, R><<<grid, block, smem, s>>>(a); break;
-    case 4: k_sweep1<4, R><<<grid, block, smem, s>>>(a); break;
-    case 5: k_sweep1<5, R><<<grid, block, smem, s>>>(a); break;
-    default: return 1;
-    }
-    return 0;
+#define OKV(KK, RR, AA) if (K == KK && (fp32 != 0) == std::is_same<RR, float>::value && acc == AA) return true;
+    PIC_FOR_SWEEP_VARIANTS(OKV)
+#undef OKV
+    return false;
 }
 
 int launch_sweep1(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s)
 {
-    return a.fp32 ? launch_sweep1_t<float>(a, grid, block, smem, s)
-                  : launch_sweep1_t<double>(a, grid, block, smem, s);
+#define L1(KK, RR, AA)                                                                              \
+    if (a.K == KK && (a.fp32 != 0) == std::is_same<RR, float>::value && a.acc == AA) {              \
+        k_sweep1<KK, RR, AA><<<grid, block, smem, s>>>(a);                                          \
+        return 0;                                                                                   \
+    }
+    PIC_FOR_SWEEP_VARIANTS(L1)
+#undef L1
+    return 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -558,7 +677,7 @@ int launch_current(const CurrentArgs &a, int grid, int block, size_t smem, cudaS
 // the weight w enters at the window flush, in double.  Same tile pipeline
 // (bulk copies of cell, t, p two tiles ahead) as the subsystem-I sweep.
 // ---------------------------------------------------------------------------
-template <int K, typename R>
+template <int K, typename R, int ACC>
 __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg, long long end,
                                              unsigned char *smem, unsigned long long &q)
 {
@@ -641,7 +760,7 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     const double w = A.w * inv_fact;
     const R one = R(1);
     // window: marker cells wb .. wb+3 (wb = the warp's lowest), V0 nodes wb-K .. wb+3
-    DepWindow<R, K + 4, K + 1, K, 0, 3> wy, wz;
+    DepWindow<R, K + 4, K + 1, K, 0, 3, typename AccOf<R, ACC>::T> wy, wz;
     wy.clear();
     wz.clear();
     int wb = INT_MIN;
@@ -749,7 +868,7 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     return !timeout;
 }
 
-template <int K, typename R>
+template <int K, typename R, int ACC>
 __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2(Sweep2Args A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -757,7 +876,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep2
     long long beg, end;
     block_chunk(A.np, beg, end);
     unsigned long long q = 0;
-    sweep2_range<K, R>(A, beg, end, smem, q);
+    sweep2_range<K, R, ACC>(A, beg, end, smem, q);
 }
 
 size_t sweep2_smem(int M, int H, int fp32)
@@ -767,23 +886,16 @@ size_t sweep2_smem(int M, int H, int fp32)
     return 128 + stages + 2 * W * sizeof(double) + (fp32 ? 3 * W * sizeof(float2) : 2 * W * sizeof(double2));
 }
 
-template <typename R>
-static int launch_sweep2_t(const Sweep2Args &a, int grid, int block, size_t smem, cudaStream_t s)
-{
-    switch (a.K) {
-    case 2: k_sweep2<2, R><<<grid, block, smem, s>>>(a); break;
-    case 3: k_sweep2<3, R><<<grid, block, smem, s>>>(a); break;
-    case 4: k_sweep2<4, R><<<grid, block, smem, s>>>(a); break;
-    case 5: k_sweep2<5, R><<<grid, block, smem, s>>>(a); break;
-    default: return 1;
-    }
-    return 0;
-}
-
 int launch_sweep2(const Sweep2Args &a, int grid, int block, size_t smem, cudaStream_t s)
 {
-    return a.fp32 ? launch_sweep2_t<float>(a, grid, block, smem, s)
-                  : launch_sweep2_t<double>(a, grid, block, smem, s);
+#define L2(KK, RR, AA)                                                                              \
+    if (a.K == KK && (a.fp32 != 0) == std::is_same<RR, float>::value && a.acc == AA) {              \
+        k_sweep2<KK, RR, AA><<<grid, block, smem, s>>>(a);                                          \
+        return 0;                                                                                   \
+    }
+    PIC_FOR_SWEEP_VARIANTS(L2)
+#undef L2
+    return 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -914,6 +1026,173 @@ int launch_gather(const DiagArgs &a, int d, int grid, int block, cudaStream_t s)
 {
     return a.fp32 ? launch_gather_t<float>(a, d, grid, block, s)
                   : launch_gather_t<double>(a, d, grid, block, s);
+}
+
+// Path mean of E_x,h = sum_i e_i Lambda^1_i along x_a -> x_a + d_a (Sec. 4.2, the
+// (1/dt) int Lambda_1(X(tau)) dtau . e of subsystem I), in double: the path is
+// split at the knots and each piece contributes (h/d) times the exact means of
+// the degree-(K-1) pieces; a zero displacement gives E_x,h(x_a).  On entry
+// out[id] holds d (length units); it is overwritten with the mean.
+template <int K, typename R>
+__global__ void __launch_bounds__(256) k_gather_path(DiagArgs A)
+{
+    const R *tp = static_cast<const R *>(A.P.t);
+    bool bad = false;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
+        const int c0 = A.P.cell[a];
+        const int id = A.P.id[a];
+        const double d = A.out[id] / A.dx;
+        if (!(fabs(d) <= (double)A.Dlim)) { bad = true; A.out[id] = 0.0; continue; }
+        double mean = 0.0;
+        const double invd = d != 0.0 ? 1.0 / d : 0.0;
+        walk_path<K, double>((double)tp[a], d, [&](int c, double h, const double *m, bool single) {
+            double e = 0.0;
+#pragma unroll
+            for (int r = 0; r < K; ++r) e += m[r] * A.c0[wrap_cell(c0 + c - r, A.M)];
+            mean += single ? e : h * invd * e;
+        });
+        A.out[id] = mean;
+    }
+    if (bad) atomicOr(A.status, STATUS_NUMERIC);
+}
+
+// ---------------------------------------------------------------------------
+// Spin (double form): deposit, rotation (subsystem III) and Zeeman energy.  Spin
+// components live in caller order; markers are visited in stored order and
+// their spins addressed through id.
+// ---------------------------------------------------------------------------
+// dA/dx at a marker: sum_i (G a)_i Lambda^1_i(x), (G a)_i = (a_i - a_{i-1}) / dx
+template <int K>
+__device__ __forceinline__ void spin_field_grad(const SpinArgs &A, int c, double t, double &Y, double &Z)
+{
+    double v[K];
+    bspline_vals<K - 1, double>(t, v);
+    Y = 0.0;
+    Z = 0.0;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int i = wrap_cell(c - r, A.M), im = wrap_cell(c - r - 1, A.M);
+        Y += v[r] * (A.ay[i] - A.ay[im]);
+        Z += v[r] * (A.az[i] - A.az[im]);
+    }
+    Y /= A.dx;
+    Z /= A.dx;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_spin_deposit(SpinArgs A)
+{
+    extern __shared__ __align__(16) double s_dep[];
+    double *sy = s_dep, *sz = s_dep + A.M;
+    for (int i = threadIdx.x; i < 2 * A.M; i += blockDim.x) s_dep[i] = 0.0;
+    __syncthreads();
+    const double *tp = static_cast<const double *>(A.P.t);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
+        const int c = A.P.cell[a];
+        const int id = A.P.id[a];
+        double v[K];
+        bspline_vals<K - 1, double>(tp[a], v);
+        const double wy = A.w * A.sy[id], wz = A.w * A.sz[id];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const int i = wrap_cell(c - r, A.M);
+            atomicAdd(&sy[i], wy * v[r]);
+            atomicAdd(&sz[i], wz * v[r]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.M; i += blockDim.x) {
+        if (sy[i] != 0.0) atomicAdd(&A.dy[i], sy[i]);
+        if (sz[i] != 0.0) atomicAdd(&A.dz[i], sz[i]);
+    }
+}
+
+// Subsystem III (Eq. spin_rodrigue): s <- s + sin(dt|r|)/|r| (r x s)
+//                                         + (1/2) (sin(dt|r|/2)/(|r|/2))^2 r x (r x s),
+// r = (0, Z, -Y), Y = dA_y/dx, Z = dA_z/dx at the marker.
+template <int K>
+__global__ void __launch_bounds__(256) k_spin_rotate(SpinArgs A)
+{
+    const double *tp = static_cast<const double *>(A.P.t);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
+        const int id = A.P.id[a];
+        double Y, Z;
+        spin_field_grad<K>(A, A.P.cell[a], tp[a], Y, Z);
+        const double r1 = Z, r2 = -Y;
+        const double nr = sqrt(r1 * r1 + r2 * r2);
+        const double s0 = A.sx[id], s1 = A.sy[id], s2 = A.sz[id];
+        // c1 = r x s, c2 = r x c1, with r0 = 0
+        const double c1x = r1 * s2 - r2 * s1, c1y = r2 * s0, c1z = -r1 * s0;
+        const double c2x = r1 * c1z - r2 * c1y, c2y = r2 * c1x, c2z = -r1 * c1x;
+        double f1, f2;
+        if (nr > 0.0) {
+            f1 = sin(A.dt * nr) / nr;
+            const double hh = sin(0.5 * A.dt * nr) / (0.5 * nr);
+            f2 = 0.5 * hh * hh;
+        } else {
+            f1 = A.dt;
+            f2 = 0.5 * A.dt * A.dt;
+        }
+        A.sx[id] = s0 + f1 * c1x + f2 * c2x;
+        A.sy[id] = s1 + f1 * c1y + f2 * c2y;
+        A.sz[id] = s2 + f1 * c1z + f2 * c2z;
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_spin_energy(SpinArgs A)
+{
+    __shared__ double s_red[32];
+    const double *tp = static_cast<const double *>(A.P.t);
+    double acc = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < A.np; a += stride) {
+        const int id = A.P.id[a];
+        double Y, Z;
+        spin_field_grad<K>(A, A.P.cell[a], tp[a], Y, Z);
+        acc += A.w * (A.sy[id] * Z - A.sz[id] * Y);
+    }
+    block_sum_to(A.acc, acc, s_red);
+}
+
+#define PIC_SPIN_LAUNCH(NAME, SMEM)                                                      \
+    switch (a.K) {                                                                       \
+    case 2: NAME<2><<<grid, 256, SMEM, s>>>(a); break;                                   \
+    case 3: NAME<3><<<grid, 256, SMEM, s>>>(a); break;                                   \
+    case 4: NAME<4><<<grid, 256, SMEM, s>>>(a); break;                                   \
+    case 5: NAME<5><<<grid, 256, SMEM, s>>>(a); break;                                   \
+    default: return 1;                                                                   \
+    }                                                                                    \
+    return 0;
+
+int launch_spin_deposit(const SpinArgs &a, int grid, cudaStream_t s)
+{
+    const size_t smem = 2 * (size_t)a.M * sizeof(double);
+    PIC_SPIN_LAUNCH(k_spin_deposit, smem)
+}
+
+int launch_spin_rotate(const SpinArgs &a, int grid, cudaStream_t s) { PIC_SPIN_LAUNCH(k_spin_rotate, 0) }
+
+int launch_spin_energy(const SpinArgs &a, int grid, cudaStream_t s) { PIC_SPIN_LAUNCH(k_spin_energy, 0) }
+
+#undef PIC_SPIN_LAUNCH
+
+int launch_gather_path(const DiagArgs &a, int grid, int block, cudaStream_t s)
+{
+#define GP(KK)                                                                                  \
+    case KK:                                                                                    \
+        if (a.fp32) k_gather_path<KK, float><<<grid, block, 0, s>>>(a);                         \
+        else k_gather_path<KK, double><<<grid, block, 0, s>>>(a);                               \
+        break;
+    switch (a.K) {
+    GP(2) GP(3) GP(4) GP(5)
+    default: return 1;
+    }
+#undef GP
+    return 0;
 }
 
 template <typename R>
@@ -1192,7 +1471,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1)
     int run;
     long long beg, end;
     while (ens_claim(Q, runs, nruns, run, beg, end))
-        if (!sweep1_range<K, R>(runs[run], beg, end, smem, q)) break;
+        if (!sweep1_range<K, R, DefaultAcc<R>::v>(runs[run], beg, end, smem, q)) break;
 }
 
 template <int K, typename R>
@@ -1206,7 +1485,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1)
     int run;
     long long beg, end;
     while (ens_claim(Q, runs, nruns, run, beg, end))
-        if (!sweep2_range<K, R>(runs[run], beg, end, smem, q)) break;
+        if (!sweep2_range<K, R, DefaultAcc<R>::v>(runs[run], beg, end, smem, q)) break;
 }
 
 template <typename R>
@@ -1262,8 +1541,6 @@ int launch_finalize1_ens(int fp32, const RunDesc *R, int nruns, int grid_x, cuda
 template <int K, typename R>
 static int set_attrs_kr(size_t s1, size_t s2, size_t s3)
 {
-    if (cudaFuncSetAttribute(k_sweep1<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) return 1;
-    if (cudaFuncSetAttribute(k_sweep2<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) return 1;
     if (cudaFuncSetAttribute(k_sweep1_ens<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) return 1;
     if (cudaFuncSetAttribute(k_sweep2_ens<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) return 1;
     if (cudaFuncSetAttribute(k_current<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3)) return 1;
@@ -1278,16 +1555,50 @@ static int set_attrs_r(size_t s1, size_t s2, size_t s3)
            set_attrs_kr<4, R>(s1, s2, s3) | set_attrs_kr<5, R>(s1, s2, s3);
 }
 
-int sweep_blocks_per_sm(int K, int fp32, int which, int block, size_t smem)
+static int set_attrs_sweeps(size_t s1, size_t s2)
+{
+    int rc = 0;
+#define ATTRV(KK, RR, AA)                                                                               \
+    rc |= cudaFuncSetAttribute(k_sweep1<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1) != \
+          cudaSuccess;                                                                                  \
+    rc |= cudaFuncSetAttribute(k_sweep2<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2) != \
+          cudaSuccess;
+    PIC_FOR_SWEEP_VARIANTS(ATTRV)
+#undef ATTRV
+    return rc;
+}
+
+static int set_attrs_spin(size_t smem)
+{
+    int rc = 0;
+    rc |= cudaFuncSetAttribute(k_spin_deposit<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess;
+    rc |= cudaFuncSetAttribute(k_spin_deposit<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess;
+    rc |= cudaFuncSetAttribute(k_spin_deposit<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess;
+    rc |= cudaFuncSetAttribute(k_spin_deposit<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess;
+    return rc;
+}
+
+int spin_optin(int M)
+{
+    static std::mutex mu;
+    static size_t have = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    const size_t need = 2 * (size_t)M * sizeof(double);
+    if (need <= have) return 0;
+    if (set_attrs_spin(need)) return 1;
+    have = need;
+    return 0;
+}
+
+int sweep_blocks_per_sm(int K, int fp32, int acc, int which, int block, size_t smem)
 {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
-#define OCC(KK, RR)                                                                                  \
-    if (K == KK && (fp32 != 0) == std::is_same<RR, float>::value)                                    \
-        e = which == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep1<KK, RR>, block, smem) \
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep2<KK, RR>, block, smem);
-    OCC(2, float) OCC(3, float) OCC(4, float) OCC(5, float)
-    OCC(2, double) OCC(3, double) OCC(4, double) OCC(5, double)
+#define OCC(KK, RR, AA)                                                                                   \
+    if (K == KK && (fp32 != 0) == std::is_same<RR, float>::value && acc == AA)                           \
+        e = which == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep1<KK, RR, AA>, block, smem) \
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep2<KK, RR, AA>, block, smem);
+    PIC_FOR_SWEEP_VARIANTS(OCC)
 #undef OCC
     return e == cudaSuccess ? n : 0;
 }
@@ -1304,7 +1615,8 @@ int pic_set_smem_attrs(size_t s1, size_t s2, size_t s3)
     std::lock_guard<std::mutex> lock(mu);
     const size_t n1 = std::max(m1, s1), n2 = std::max(m2, s2), n3 = std::max(m3, s3);
     if (n1 == m1 && n2 == m2 && n3 == m3) return 0;
-    const int rc = pic::set_attrs_r<float>(n1, n2, n3) | pic::set_attrs_r<double>(n1, n2, n3);
+    const int rc = pic::set_attrs_r<float>(n1, n2, n3) | pic::set_attrs_r<double>(n1, n2, n3) |
+                   pic::set_attrs_sweeps(n1, n2);
     if (rc == 0) { m1 = n1; m2 = n2; m3 = n3; }
     return rc;
 }

@@ -10,10 +10,13 @@ Recipe (one electron species on a neutralising unit ion background):
   i.e. x + (eps/kappa) sin(kappa x) = u L with u ~ U[0,1), solved by Newton;
 * momenta p ~ N(0, vth^2) (a Maxwellian in p with c = 1);
 * equal weights w = L / Np, so that sum w = L balances the background;
-* pump A_y = amp cos(k0 x), A_z = 0, E_y = E_z = 0 (released from rest).  The
-  A_y coefficients are the values of the pump at the Greville abscissae
-  x_j + (k+1) dx / 2 of the degree-k basis (the Schoenberg quasi-interpolant,
-  one reading of the projector Pi_0 of Sec. 3.1);
+* pump A_y = amp cos(k0 x), A_z = 0, E_y = E_z = 0 (released from rest); or,
+  for the paper's parametric-instability runs (Sec. 5), the circularly
+  polarised wave E_y = E0 cos(k0 x), E_z = E0 sin(k0 x), A_y = -E0 sin(k0 x),
+  A_z = E0 cos(k0 x).  Coefficients are the values of the fields at the
+  Greville abscissae x_j + (k+1) dx / 2 of the degree-k basis (the Schoenberg
+  quasi-interpolant, one reading of the projector Pi_0 of Sec. 3.1);
+* spins (runs with hbar != 0): every marker starts with s = (0, 0, 1);
 * E_x is not an input: each side solves the discrete Poisson equation.
 """
 from __future__ import annotations
@@ -41,6 +44,8 @@ class Workload:
     k0_mode: int = 4           # k0 = 2 pi k0_mode / L
     seed: int = 0
     max_iter: int = 100
+    pump_kind: str = "standing"   # "standing": A_y = pump cos(k0 x); "circular": the wave of Sec. 5
+    hbar: float = 0.0          # normalised Planck constant (spin runs)
 
     @property
     def dx(self) -> float:
@@ -69,6 +74,16 @@ WORKLOADS = {
     # learned warm start: C2 shape
     "C5": Workload("C5", nx=2048, degree=3, np=100_000_000, dt=0.05, steps=1000,
                    vth=0.1, pump=0.2),
+    # the paper's runs (Sec. 5): parametric instability of a circularly polarised
+    # wave, E0 = sqrt(3), k = 1/sqrt(2), L = 2 pi / k, T = 3/511 (vth = sqrt(T)),
+    # homogeneous density, M = 128, cubic V0, dt = 0.02; without spin to t = 80
+    # with 4e3 markers, with spin (hbar = 0.1, s = (0, 0, 1)) to t = 200 with 1e4
+    "P1": Workload("P1", L=2.0 * math.pi * math.sqrt(2.0), nx=128, degree=3, np=4000, dt=0.02,
+                   steps=4000, eps=0.0, vth=math.sqrt(3.0 / 511.0), pump=math.sqrt(3.0), k0_mode=1,
+                   pump_kind="circular"),
+    "P2": Workload("P2", L=2.0 * math.pi * math.sqrt(2.0), nx=128, degree=3, np=10000, dt=0.02,
+                   steps=10000, eps=0.0, vth=math.sqrt(3.0 / 511.0), pump=math.sqrt(3.0), k0_mode=1,
+                   pump_kind="circular", hbar=0.1),
 }
 
 
@@ -152,8 +167,16 @@ def fields(w: Workload):
     """(ay, az, ey, ez) initial coefficients, float64 arrays of length nx."""
     j = np.arange(w.nx, dtype=np.float64)
     greville = (j + 0.5 * (w.degree + 1)) * w.dx
+    if w.pump_kind == "circular":
+        kx = w.k0 * greville
+        return -w.pump * np.sin(kx), w.pump * np.cos(kx), w.pump * np.cos(kx), w.pump * np.sin(kx)
     ay = w.pump * np.cos(w.k0 * greville)
     az = np.zeros(w.nx)
     ey = np.zeros(w.nx)
     ez = np.zeros(w.nx)
     return ay, az, ey, ez
+
+
+def spins(w: Workload):
+    """(sx, sy, sz) initial spins of the markers: s = (0, 0, 1) (Sec. 5)."""
+    return np.zeros(w.np), np.zeros(w.np), np.ones(w.np)

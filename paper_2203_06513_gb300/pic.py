@@ -23,8 +23,10 @@ PIC_FP64, PIC_FP32 = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 PIC_WARM_NONE, PIC_WARM_EXPLICIT, PIC_WARM_MLP = 0, 1, 2
 PIC_DEP_CHARGE, PIC_DEP_CURRENT, PIC_DEP_SUSCEPT = 0, 1, 2
-PIC_FIELD_EX, PIC_FIELD_EY, PIC_FIELD_EZ, PIC_FIELD_AY, PIC_FIELD_AZ = range(5)
-PIC_SUBSYSTEM_I, PIC_SUBSYSTEM_II = 1, 2
+PIC_FIELD_EX, PIC_FIELD_EY, PIC_FIELD_EZ, PIC_FIELD_AY, PIC_FIELD_AZ, PIC_FIELD_EX_PATHAVG = range(6)
+PIC_ACC_DEFAULT, PIC_ACC_FLOAT, PIC_ACC_COMPENSATED, PIC_ACC_DOUBLE = range(4)
+PIC_SPLIT_LIE, PIC_SPLIT_STRANG = 0, 1
+PIC_SUBSYSTEM_I, PIC_SUBSYSTEM_II, PIC_SUBSYSTEM_III = 1, 2, 3
 
 
 class PicError(RuntimeError):
@@ -42,7 +44,8 @@ class pic_config(ctypes.Structure):
                 ("np", ctypes.c_int64), ("weight", ctypes.c_double), ("dt", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("warm_start", ctypes.c_int32),
-                ("sort_every", ctypes.c_int32)]
+                ("sort_every", ctypes.c_int32), ("deposit", ctypes.c_int32),
+                ("splitting", ctypes.c_int32), ("hbar", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -50,7 +53,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 class pic_arrays(ctypes.Structure):
     _fields_ = [("x", _dp), ("p", _dp), ("ex", _dp), ("ey", _dp), ("ez", _dp),
-                ("ay", _dp), ("az", _dp)]
+                ("ay", _dp), ("az", _dp), ("sx", _dp), ("sy", _dp), ("sz", _dp)]
 
 
 _lib = None
@@ -74,6 +77,9 @@ def load(path: str | None = None):
     H = ctypes.POINTER(ctypes.c_void_p)
     L.pic_init.argtypes = [ctypes.POINTER(pic_config), ctypes.POINTER(pic_arrays), ctypes.c_int32,
                            ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.pic_init_split.argtypes = [ctypes.POINTER(pic_config), ctypes.POINTER(pic_arrays), ctypes.c_int32,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_void_p)]
     L.pic_get_state.argtypes = [ctypes.c_void_p, ctypes.POINTER(pic_arrays), ctypes.c_int32]
     L.pic_deposit.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
     L.pic_gather.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
@@ -122,33 +128,50 @@ class Config:
     precision: int = PIC_FP64
     warm_start: int = PIC_WARM_NONE
     sort_every: int = 0
+    deposit: int = PIC_ACC_DEFAULT
+    splitting: int = PIC_SPLIT_LIE
+    hbar: float = 0.0
 
     def c(self) -> pic_config:
         return pic_config(self.L, self.nx, self.degree, self.np, self.weight, self.dt, self.tol,
-                          self.max_iter, self.precision, self.warm_start, self.sort_every)
+                          self.max_iter, self.precision, self.warm_start, self.sort_every,
+                          self.deposit, self.splitting, self.hbar)
 
     @staticmethod
     def from_workload(w, precision=PIC_FP64, warm_start=PIC_WARM_NONE, sort_every=0,
-                      tol=None, max_iter=None) -> "Config":
+                      tol=None, max_iter=None, deposit=PIC_ACC_DEFAULT,
+                      splitting=PIC_SPLIT_LIE, hbar=None) -> "Config":
         return Config(w.L, w.nx, w.degree, w.np, w.weight, w.dt,
                       w.tol if tol is None else tol,
                       w.max_iter if max_iter is None else max_iter,
-                      precision, warm_start, sort_every)
+                      precision, warm_start, sort_every, deposit, splitting,
+                      getattr(w, "hbar", 0.0) if hbar is None else hbar)
 
 
 class Pic:
     """One simulation handle.  Arrays are float64 numpy (host) or torch (device)."""
 
-    def __init__(self, cfg: Config, x, p, ay, az, ey=None, ez=None, stream=None):
+    def __init__(self, cfg: Config, x, p, ay, az, ey=None, ez=None, stream=None, spin=None, reducer=None):
+        """spin: (sx, sy, sz) marker spins, required when cfg.hbar != 0.  reducer: an
+        object whose `cfunc` is the reduction callback of a split run (see split.py);
+        None: all markers are in this handle."""
         L = load()
         self._lib = L
         self.cfg = cfg
         host = isinstance(x, np.ndarray)
-        arrs = pic_arrays(_ptr(x), _ptr(p), _dp(), _ptr(ey), _ptr(ez), _ptr(ay), _ptr(az))
+        sx, sy, sz = spin if spin is not None else (None, None, None)
+        arrs = pic_arrays(_ptr(x), _ptr(p), _dp(), _ptr(ey), _ptr(ez), _ptr(ay), _ptr(az),
+                          _ptr(sx), _ptr(sy), _ptr(sz))
         h = ctypes.c_void_p()
         s = ctypes.c_void_p(0 if stream is None else int(stream))
-        rc = L.pic_init(ctypes.byref(cfg.c()), ctypes.byref(arrs),
-                        PIC_MEM_HOST if host else PIC_MEM_DEVICE, s, ctypes.byref(h))
+        self._reducer = reducer
+        if reducer is None:
+            rc = L.pic_init(ctypes.byref(cfg.c()), ctypes.byref(arrs),
+                            PIC_MEM_HOST if host else PIC_MEM_DEVICE, s, ctypes.byref(h))
+        else:
+            fn = ctypes.cast(reducer.cfunc, ctypes.c_void_p)
+            rc = L.pic_init_split(ctypes.byref(cfg.c()), ctypes.byref(arrs),
+                                  PIC_MEM_HOST if host else PIC_MEM_DEVICE, s, fn, None, ctypes.byref(h))
         if rc != PIC_OK:
             raise PicError(rc, L.pic_last_error(None).decode())
         self._h = h
@@ -199,15 +222,17 @@ class Pic:
         return i1.value, i2.value
 
     def energy(self) -> dict:
-        out = (ctypes.c_double * 6)()
+        out = (ctypes.c_double * 7)()
         self._check(self._lib.pic_energy(self._h, out))
         return {"kinetic": out[0], "ex": out[1], "eperp": out[2], "aperp": out[3],
-                "total": out[4], "gauss": out[5]}
+                "total": out[4], "gauss": out[5], "spin": out[6]}
 
-    def get_state(self, x=None, p=None, ex=None, ey=None, ez=None, ay=None, az=None):
-        arrays = [a for a in (x, p, ex, ey, ez, ay, az) if a is not None]
+    def get_state(self, x=None, p=None, ex=None, ey=None, ez=None, ay=None, az=None,
+                  sx=None, sy=None, sz=None):
+        arrays = [a for a in (x, p, ex, ey, ez, ay, az, sx, sy, sz) if a is not None]
         host = isinstance(arrays[0], np.ndarray) if arrays else True
-        arrs = pic_arrays(_ptr(x), _ptr(p), _ptr(ex), _ptr(ey), _ptr(ez), _ptr(ay), _ptr(az))
+        arrs = pic_arrays(_ptr(x), _ptr(p), _ptr(ex), _ptr(ey), _ptr(ez), _ptr(ay), _ptr(az),
+                          _ptr(sx), _ptr(sy), _ptr(sz))
         self._check(self._lib.pic_get_state(self._h, ctypes.byref(arrs),
                                             PIC_MEM_HOST if host else PIC_MEM_DEVICE))
 
@@ -215,6 +240,8 @@ class Pic:
         n, M = self.cfg.np, self.cfg.nx
         out = {k: np.empty(n) for k in ("x", "p")}
         out.update({k: np.empty(M) for k in ("ex", "ey", "ez", "ay", "az")})
+        if self.cfg.hbar != 0.0:
+            out.update({k: np.empty(n) for k in ("sx", "sy", "sz")})
         self.get_state(**out)
         return out
 
@@ -223,6 +250,8 @@ class Pic:
         self._check(self._lib.pic_deposit(self._h, kind, _vptr(aux), _vptr(out)))
 
     def gather(self, field: int, out):
+        """out: torch float64 CUDA tensor (N_p); for PIC_FIELD_EX_PATHAVG it holds the
+        displacements on entry (see pic_gather)."""
         self._check(self._lib.pic_gather(self._h, field, _vptr(out)))
 
     def timing_enable(self, on: bool = True):
@@ -270,7 +299,8 @@ class Ensemble:
         carr = (pic_config * n)(*[c.c() for c in cfgs])
         self._keep = [tuple(np.ascontiguousarray(a, dtype=np.float64) if a is not None else None for a in inp)
                       for inp in inputs]
-        aarr = (pic_arrays * n)(*[pic_arrays(_ptr(x), _ptr(p), _dp(), _ptr(ey), _ptr(ez), _ptr(ay), _ptr(az))
+        aarr = (pic_arrays * n)(*[pic_arrays(_ptr(x), _ptr(p), _dp(), _ptr(ey), _ptr(ez), _ptr(ay), _ptr(az),
+                                             _dp(), _dp(), _dp())
                                   for (x, p, ay, az, ey, ez) in self._keep])
         h = vp()
         s = vp(0 if stream is None else int(stream))

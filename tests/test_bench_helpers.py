@@ -24,11 +24,11 @@ def test_roofline_entries(bench):
     ks = bench.kernel_rooflines(timing(), np_, 6000.0, 1700.0, "measured", sms=152, sm_mhz=2070.0)
     by = {k["kernel"]: k for k in ks}
     s1 = by["k_sweep1<3,float>"]
-    # 24 bytes a marker in 2 ms a launch
+    # 28 bytes a marker (x^n 8, p^n 4, x^(k) 8 read; x^(k+1) 8 written) in 2 ms a launch
     assert s1["launch_ms"] == pytest.approx(2.0)
-    assert s1["achieved"] == pytest.approx(24 * np_ / 2e-3 / 1e9)
+    assert s1["achieved"] == pytest.approx(28 * np_ / 2e-3 / 1e9)
     assert s1["frac"] == pytest.approx(s1["achieved"] / 6000.0)
-    assert s1["algorithmic_per_launch"] == 24 * np_
+    assert s1["algorithmic_per_launch"] == 28 * np_
     assert s1["traffic"] == pytest.approx(bench.NCU_DRAM_PER_MARKER["k_sweep1<3,float>"] * np_)
     # issue slots: instructions / 32 per marker against SMs x 4 x clock
     inst = bench.NCU_INST_PER_MARKER["k_sweep1<3,float>"]
