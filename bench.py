@@ -166,16 +166,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=None, deposit=0):
-    """Advance one replica from host arrays; CUDA-event timing of `steps` steps."""
+def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=None, deposit=0,
+             kernel_steps=5, split_run=None):
+    """Advance one replica (or, with split_run = (reducer, local count), this rank's
+    share of one plasma) from host arrays; CUDA-event timing of `steps` steps."""
     x, p, ay, az, ey, ez = arrays
     cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2, deposit=deposit)
-    g = pic.Pic(cfg, x, p, ay, az, ey, ez, stream=stream.cuda_stream)
+    reducer = None
+    if split_run is not None:
+        reducer, cfg.np = split_run
+    g = pic.Pic(cfg, x, p, ay, az, ey, ez, stream=stream.cuda_stream, reducer=reducer)
     if mlp is not None:
         mlp.attach(g)
     H0 = g.energy()["total"]
     it_warm = g.step(warmup)
-    g.timing_enable(True)
+    # timed steps: one CUDA graph per step with device-ended loops (no per-launch
+    # events); the launch counter is reset first and read after
+    g.timing_enable(False)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -184,11 +191,25 @@ def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
-    tr = g.timing_read()
+    launches = g.timing_read()["launches"]
     E = g.energy()
+    # per-kernel durations: further steps of the same run with an event pair
+    # around every launch (loops driven from the host)
+    g.timing_enable(True)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    nk = max(1, min(steps, kernel_steps))
+    k0.record(stream)
+    it_k = g.step(nk)
+    k1.record(stream)
+    k1.synchronize()
+    tr = g.timing_read()
+    tr["steps"] = nk
+    tr["ms_per_step_host_loops"] = k0.elapsed_time(k1) / nk
     g.close()
-    return {"ms": ms, "iters": it, "iters_warm": it_warm, "timing": tr, "H0": H0, "H": E["total"],
-            "gauss": E["gauss"], "rel_energy_err": abs(E["total"] - H0) / abs(H0)}
+    return {"ms": ms, "iters": it, "iters_warm": it_warm, "timing": tr, "launches": launches, "H0": H0,
+            "H": E["total"], "gauss": E["gauss"], "rel_energy_err": abs(E["total"] - H0) / abs(H0)}
 
 
 def drift_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None, every=100):
@@ -380,10 +401,19 @@ def main():
     ap.add_argument("--ensemble-scale", type=float, default=1.0, help="scale of the runs' marker counts")
     ap.add_argument("--ensemble-host-loop", action="store_true",
                     help="drive the ensemble's loops from the host (same kernels, no graph; for profiling)")
+    ap.add_argument("--split", action="store_true",
+                    help="with N > 1: one plasma of N x Np markers split over the ranks (an all-reduce of the "
+                         "deposits per sweep) instead of N independent replicas; only the timed forms run")
     args = ap.parse_args()
     ws, rank, local = R.dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
+    split_mode = args.split and ws > 1
+    if split_mode:                      # only the timed forms of the split plasma
+        args.ensemble_runs = 0
+        args.drift_steps = 0
+        args.deposit_variants = 0
+        args.no_e2e = True
     ens_in = None
     if args.ensemble_runs > 0:          # host inputs first: the pool starts before any CUDA call
         ens_in = ensemble_inputs(args.ensemble_runs, args.ensemble_scale, seed=R.replica_seed(0, rank))
@@ -398,7 +428,17 @@ def main():
     if args.np:
         kw["np"] = int(args.np)
     w = I.workload(WORKLOAD, **kw)
-    x, p = I.particles(w, workers=max(1, min(16, os.cpu_count() or 1)))
+    split_run = None
+    if split_mode:
+        # one plasma of ws x Np markers (one seed), this rank's contiguous share
+        from paper_2203_06513_gb300 import split as S
+        w_local = w
+        w = I.workload(WORKLOAD, seed=0, np=w_local.np * ws)
+        lo, hi = S.shard(w.np, rank, ws)
+        x, p = I.particles_range(w, lo, hi, workers=max(1, min(16, os.cpu_count() or 1)))
+        split_run = (S.TorchDeviceReducer(), hi - lo)
+    else:
+        x, p = I.particles(w, workers=max(1, min(16, os.cpu_count() or 1)))
     ay, az, ey, ez = I.fields(w)
     arrays = (x, p, ay, az, ey, ez)
     stream = torch.cuda.Stream()
@@ -418,15 +458,15 @@ def main():
     barrier()
     clocks.start()
     r_head = run_form(pic, torch, w, arrays, pic.PIC_FP32, head_warm, args.steps, args.warmup, stream,
-                      mlp if mlp is not None else None)
+                      mlp if mlp is not None else None, split_run=split_run)
     clk = clocks.stop()
     barrier()
     r_expl = run_form(pic, torch, w, arrays, pic.PIC_FP32, pic.PIC_WARM_EXPLICIT, args.steps,
-                      args.warmup, stream)
+                      args.warmup, stream, split_run=split_run)
     barrier()
     k64 = args.fp64_steps if args.fp64_steps is not None else max(1, min(args.steps, 4))
     r64 = run_form(pic, torch, w, arrays, pic.PIC_FP64, pic.PIC_WARM_NONE, k64, max(1, min(args.warmup, 3)),
-                   stream)
+                   stream, split_run=split_run)
     barrier()
     e2e = None if args.no_e2e else e2e_run(pic, torch, w, arrays, pic.PIC_FP32, head_warm, args.steps,
                                            stream, mlp)
@@ -462,13 +502,14 @@ def main():
     ms_expl = max_over_ranks(r_expl["ms"])
     ms64 = max_over_ranks(r64["ms"])
     e2e_s = max_over_ranks(e2e["s"]) if e2e else None
-    value = R.whole_job_rate(w.np, ws, args.steps, ms_head / 1e3)
-    v_expl = R.whole_job_rate(w.np, ws, args.steps, ms_expl / 1e3)
-    v64 = R.whole_job_rate(w.np, ws, k64, ms64 / 1e3)
+    per_rank = w.np / ws if split_mode else w.np          # markers each rank advances
+    value = R.whole_job_rate(per_rank, ws, args.steps, ms_head / 1e3)
+    v_expl = R.whole_job_rate(per_rank, ws, args.steps, ms_expl / 1e3)
+    v64 = R.whole_job_rate(per_rank, ws, k64, ms64 / 1e3)
     tr = r_head["timing"]
     hbm, tflops, peak_kind = peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
-    kernels = kernel_rooflines(tr, w.np, hbm, tflops, peak_kind,
+    kernels = kernel_rooflines(tr, int(per_rank), hbm, tflops, peak_kind,
                                torch.cuda.get_device_properties(local).multi_processor_count, sm_mhz)
     dominant = max(kernels, key=lambda k: k["share_ms"])
     if rank == 0:
@@ -493,12 +534,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_head / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "C2: L=4pi, M=2048, k=3, Np=%d per GPU, dt=0.05, pump 0.2, vth 0.1"
-                                   % w.np,
+                                   % per_rank,
                        "form": "FP32 particles + FP64 grid",
                        "warm_start": "learned (MLP)" if mlp is not None else "explicit (no weights file)",
                        "l2": "inputs larger than L2 (markers %.1f GB)" % (w.np * 24 / 1e9),
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "gpu_launches": tr["launches"],
+                       "parallelism": ("one plasma split by markers, all-reduce per sweep" if split_mode
+                                       else "replicas" if ws > 1 else "single GPU")},
+            "gpu_launches": r_head["launches"],
             "roofline": dominant,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -507,8 +549,9 @@ def main():
                 "h2d_bytes_per_step": e2e["h2d"] / args.steps,
                 "d2h_bytes_per_step": e2e["d2h"] / args.steps},
             "kernels": [_compact_kernel(k) for k in kernels],
-            "kernel_ms": {"sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"], "solve": tr["solve_ms"],
-                          "warm_start": tr["warm_ms"]},
+            "kernel_ms": {"steps": tr["steps"], "sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"],
+                          "solve": tr["solve_ms"], "warm_start": tr["warm_ms"],
+                          "ms_per_step_host_loops": tr["ms_per_step_host_loops"]},
             "ensemble": ens,
             "deposit_accumulation": dep,
             "fp64": {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,

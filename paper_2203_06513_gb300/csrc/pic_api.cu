@@ -113,6 +113,8 @@ static int dalloc(pic_handle *h, T **p, size_t n)
     return PIC_OK;
 }
 
+static void drop_graphs(pic_handle *h);
+
 // Returns the handle's device memory to the pool (in stream order, then waits).
 static void release(pic_handle *h)
 {
@@ -131,11 +133,15 @@ static void release(pic_handle *h)
     for (double *a : arr) f(a);
     f(h->counts);
     f(h->ctrl);
+    f(h->d_count);
+    drop_graphs(h);
     f(h->img.a); f(h->img.f); f(h->img.an); f(h->img.ak); f(h->img.lo);
     for (int m = 0; m < kMaxStartOrder; ++m) { f(h->fh.x[m]); f(h->fh.y[m]); f(h->fh.z[m]); }
     cudaStreamSynchronize(s);
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+    if (h->h_count) cudaFreeHost(h->h_count);
+    if (h->cap) cudaStreamDestroy(h->cap);
     for (auto &t : h->timed) { cudaEventDestroy(t.b); cudaEventDestroy(t.e); }
     for (auto &t : h->spare) { cudaEventDestroy(t.first); cudaEventDestroy(t.second); }
     h->timed.clear();
@@ -620,12 +626,8 @@ static int substep3(pic_handle *h)
 }
 
 // Subsystem I over a time step dt (the handle's dt, or half of it in a Strang step).
-static int substep1(pic_handle *h, int *iters, double dt)
+static Sweep1Args sweep1_args(pic_handle *h, double dt)
 {
-    int rc;
-    const RunDesc desc = handle_desc(h);
-    launch_prep1(desc, h->stream);
-    CKL_N("launch_prep1");
     Sweep1Args a{};
     a.M = h->M; a.H = h->H; a.Dlim = h->Dlim; a.K = h->K; a.fp32 = h->fp32; a.acc = h->acc; a.np = h->np;
     a.dx = h->dx; a.dt = dt; a.w = h->cfg.weight;
@@ -637,6 +639,12 @@ static int substep1(pic_handle *h, int *iters, double dt)
     a.hbar = h->cfg.hbar;
     a.sy = h->spy;
     a.sz = h->spz;
+    a.jpair[0] = h->jb[0]; a.jpair[1] = h->jb[1];
+    return a;
+}
+
+static ConvArgs conv1_args(pic_handle *h, double dt)
+{
     ConvArgs c{};
     c.img = h->img;
     c.M = h->M; c.d_start = h->tapM1_start; c.ntap = h->tapM1_n; c.mode = CONV_SOLVE1; c.ncomp = 1;
@@ -644,15 +652,63 @@ static int substep1(pic_handle *h, int *iters, double dt)
     c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
     c.dt = dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6;   // FP32: estimated position error, cells relative to max(1, |delta|)
     c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 1; c.ctrl = h->ctrl;
+    c.pair[0][0] = h->jb[0]; c.pair[0][1] = h->jb[1];
+    return c;
+}
+
+static Sweep2Args sweep2_args(pic_handle *h)
+{
+    Sweep2Args a{};
+    a.status = &h->ctrl->status;
+    a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.acc = h->acc; a.np = h->np; a.w = h->cfg.weight;
+    a.P = cur_parts(h);
+    a.an_y = h->ay; a.an_z = h->az; a.ak_y = h->aky; a.ak_z = h->akz;
+    a.img = h->img;
+    a.ctrl = h->ctrl;
+    a.sypair[0] = h->sy[0]; a.sypair[1] = h->sy[1];
+    a.szpair[0] = h->sz[0]; a.szpair[1] = h->sz[1];
+    return a;
+}
+
+static ConvArgs conv2_args(pic_handle *h)
+{
+    ConvArgs c{};
+    c.img = h->img;
+    c.M = h->M; c.d_start = h->tapP_start; c.ntap = h->tapP_n; c.mode = CONV_SOLVE2; c.ncomp = 2;
+    c.taps = h->d_tapP;
+    c.en[0] = h->ey; c.en[1] = h->ez; c.ek[0] = h->eky; c.ek[1] = h->ekz;
+    c.aux[0] = h->aky; c.aux[1] = h->akz; c.an[0] = h->ay; c.an[1] = h->az;
+    c.r0[0] = h->r0y; c.r0[1] = h->r0z;
+    c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 0.0;
+    c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 2; c.ctrl = h->ctrl;
+    c.pair[0][0] = h->sy[0]; c.pair[0][1] = h->sy[1];
+    c.pair[1][0] = h->sz[0]; c.pair[1][1] = h->sz[1];
+    return c;
+}
+
+static WarmArgs warm_args(pic_handle *h, double dt)
+{
+    WarmArgs wa{};
+    wa.M = h->M; wa.K = h->K; wa.fp32 = h->fp32; wa.np = h->np; wa.dx = h->dx; wa.dt = dt;
+    wa.P = cur_parts(h);
+    wa.ex = h->ex; wa.ay = h->ay; wa.az = h->az;
+    wa.params = mlp_params(h->mlp); wa.norm = mlp_norm(h->mlp);
+    wa.status = &h->ctrl->status;
+    return wa;
+}
+
+static int substep1(pic_handle *h, int *iters, double dt)
+{
+    int rc;
+    const RunDesc desc = handle_desc(h);
+    launch_prep1(desc, h->stream);
+    CKL_N("launch_prep1");
+    Sweep1Args a = sweep1_args(h, dt);
+    ConvArgs c = conv1_args(h, dt);
     if (h->cfg.warm_start == PIC_WARM_MLP) {
         // learned proposal for delta^(0), written over the zero iterate
         if (!h->mlp) return fail(h, PIC_ERR_INVALID, "warm_start = PIC_WARM_MLP but no network attached");
-        WarmArgs wa{};
-        wa.M = h->M; wa.K = h->K; wa.fp32 = h->fp32; wa.np = h->np; wa.dx = h->dx; wa.dt = dt;
-        wa.P = cur_parts(h);
-        wa.ex = h->ex; wa.ay = h->ay; wa.az = h->az;
-        wa.params = mlp_params(h->mlp); wa.norm = mlp_norm(h->mlp);
-        wa.status = &h->ctrl->status;
+        const WarmArgs wa = warm_args(h, dt);
         if ((rc = timed_begin(h))) return rc;
         if (launch_warm_mlp(wa, h->num_sms, h->stream))
             return fail(h, PIC_ERR_CUDA, "warm-start network: launch setup failed");
@@ -710,21 +766,8 @@ static int substep2(pic_handle *h, int *iters)
         CKL_N("launch_spin_rhs");
     }
     if ((rc = conv_plain(h, h->d_tapP, h->tapP_start, h->tapP_n, h->by, h->r0y, h->bz, h->r0z))) return rc;
-    Sweep2Args a{};
-    a.status = &h->ctrl->status;
-    a.M = h->M; a.H = h->H; a.K = h->K; a.fp32 = h->fp32; a.acc = h->acc; a.np = h->np; a.w = h->cfg.weight;
-    a.P = cur_parts(h);
-    a.an_y = h->ay; a.an_z = h->az; a.ak_y = h->aky; a.ak_z = h->akz;
-    a.img = h->img;
-    ConvArgs c{};
-    c.img = h->img;
-    c.M = h->M; c.d_start = h->tapP_start; c.ntap = h->tapP_n; c.mode = CONV_SOLVE2; c.ncomp = 2;
-    c.taps = h->d_tapP;
-    c.en[0] = h->ey; c.en[1] = h->ez; c.ek[0] = h->eky; c.ek[1] = h->ekz;
-    c.aux[0] = h->aky; c.aux[1] = h->akz; c.an[0] = h->ay; c.an[1] = h->az;
-    c.r0[0] = h->r0y; c.r0[1] = h->r0z;
-    c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 0.0;
-    c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 2; c.ctrl = h->ctrl;
+    Sweep2Args a = sweep2_args(h);
+    ConvArgs c = conv2_args(h);
     int it = 0;
     for (;;) {
         a.s_y = h->sy[it & 1];
@@ -770,6 +813,202 @@ extern "C" int pic_substep(pic_handle *h, int32_t which, int32_t *iters)
     return sync(h);
 }
 
+// ------------------------------------------------------------------ step graphs
+// One step as a CUDA graph: the linear segments as child graphs, the two
+// fixed-point loops as conditional WHILE nodes whose bodies (sweep, solve) read
+// the sweep's parity from the control block and whose solve takes the loop's
+// decision on the device (no host round trip per sweep).  The markers' buffers
+// enter the kernel arguments, so there is one graph per marker copy (the sort
+// alternates them).  Host loops are kept for split runs (their reductions call
+// back into the host), spin runs, kernel timing and PIC_DEBUG_SYNC.
+static bool graph_eligible(const pic_handle *h)
+{
+    return !h->reduce && h->cfg.hbar == 0.0 && !h->timing && !debug_sync() &&
+           (h->cfg.warm_start != PIC_WARM_MLP || h->mlp) && getenv("PIC_NO_GRAPH") == nullptr;
+}
+
+static void drop_graphs(pic_handle *h)
+{
+    for (int b = 0; b < 2; ++b)
+        if (h->step_exec[b]) {
+            cudaGraphExecDestroy(h->step_exec[b]);
+            h->step_exec[b] = nullptr;
+        }
+}
+
+#define GCK(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(h, PIC_ERR_CUDA, "step graph: %s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static int seg_sub1_head(pic_handle *h, cudaStream_t s, double dt, int *nodes)
+{
+    launch_prep1(handle_desc(h), s);
+    ++*nodes;
+    if (h->cfg.warm_start == PIC_WARM_MLP) {
+        if (launch_warm_mlp(warm_args(h, dt), h->num_sms, s)) return fail(h, PIC_ERR_CUDA, "warm-start launch");
+        ++*nodes;
+    }
+    return PIC_OK;
+}
+
+static int seg_sub1_tail(pic_handle *h, cudaStream_t s, int *nodes)
+{
+    launch_finalize1(h->fp32, h->np, h->M, cur_parts(h), h->cfg.warm_start == PIC_WARM_NONE, particle_grid(h), 256,
+                     s);
+    launch_commit(handle_desc(h), 1, s);
+    *nodes += 2;
+    return PIC_OK;
+}
+
+static int seg_sub2_head(pic_handle *h, cudaStream_t s, int *nodes)
+{
+    launch_prep2(handle_desc(h), s);
+    ConvArgs c{};
+    c.M = h->M; c.d_start = h->tapP_start; c.ntap = h->tapP_n; c.mode = CONV_PLAIN; c.ncomp = 2;
+    c.taps = h->d_tapP;
+    c.in[0] = h->by; c.in[1] = h->bz;
+    c.out[0] = h->r0y; c.out[1] = h->r0z;
+    c.ctrl = h->ctrl;
+    if (launch_conv(c, s)) return fail(h, PIC_ERR_CUDA, "k_conv launch");
+    *nodes += 2;
+    return PIC_OK;
+}
+
+static int seg_sub2_tail(pic_handle *h, cudaStream_t s, int *nodes)
+{
+    launch_commit(handle_desc(h), 2, s);
+    *nodes += 1;
+    return PIC_OK;
+}
+
+static int loop_body(pic_handle *h, cudaStream_t s, int which, double dt, unsigned long long cond)
+{
+    if (which == 1) {
+        Sweep1Args a = sweep1_args(h, dt);
+        a.graph = 1;
+        a.warm = h->cfg.warm_start == PIC_WARM_EXPLICIT ? 1 : 0;   // applied when iter == 0
+        a.j = h->jb[0];
+        if (launch_sweep1(a, h->sweep_grid, h->sweep_block, h->smem1, s)) return fail(h, PIC_ERR_INVALID, "sweep1");
+        ConvArgs c = conv1_args(h, dt);
+        c.graph = 1;
+        c.cond_handle = cond;
+        c.count = h->d_count;
+        if (launch_conv(c, s)) return fail(h, PIC_ERR_CUDA, "k_conv launch");
+    } else {
+        Sweep2Args a = sweep2_args(h);
+        a.graph = 1;
+        a.s_y = h->sy[0];
+        a.s_z = h->sz[0];
+        if (launch_sweep2(a, h->sweep_grid, h->sweep_block, h->smem2, s)) return fail(h, PIC_ERR_INVALID, "sweep2");
+        ConvArgs c = conv2_args(h);
+        c.graph = 1;
+        c.cond_handle = cond;
+        c.count = h->d_count + 1;
+        if (launch_conv(c, s)) return fail(h, PIC_ERR_CUDA, "k_conv launch");
+    }
+    return PIC_OK;
+}
+
+static int build_step_graph(pic_handle *h)
+{
+    if (!h->cap) GCK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    GCK(cudaGraphCreate(&g, 0));
+    cudaGraphNode_t prev = nullptr;
+    int nodes = 0;
+    auto add_segment = [&](auto &&seg) -> int {
+        cudaGraph_t child = nullptr;
+        GCK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        const int r = seg(h->cap);
+        cudaError_t ce = cudaStreamEndCapture(h->cap, &child);
+        if (r) { if (child) cudaGraphDestroy(child); return r; }
+        GCK(ce);
+        cudaGraphNode_t n = nullptr;
+        ce = cudaGraphAddChildGraphNode(&n, g, prev ? &prev : nullptr, prev ? 1 : 0, child);
+        cudaGraphDestroy(child);
+        GCK(ce);
+        prev = n;
+        return PIC_OK;
+    };
+    auto add_loop = [&](int which, double dt) -> int {
+        cudaGraphConditionalHandle hnd;
+        GCK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = hnd;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t n = nullptr;
+        GCK(cudaGraphAddNode(&n, g, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &p));
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        GCK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        const int r = loop_body(h, h->cap, which, dt, (unsigned long long)hnd);
+        cudaError_t ce = cudaStreamEndCapture(h->cap, &body);
+        if (r) return r;
+        GCK(ce);
+        prev = n;
+        return PIC_OK;
+    };
+    const bool strang = h->cfg.splitting == PIC_SPLIT_STRANG;
+    const double dt1 = strang ? 0.5 * h->cfg.dt : h->cfg.dt;
+    int rc = PIC_OK;
+    if (!rc) rc = add_segment([&](cudaStream_t s) { return seg_sub1_head(h, s, dt1, &nodes); });
+    if (!rc) rc = add_loop(1, dt1);
+    if (!rc) rc = add_segment([&](cudaStream_t s) {
+        int r = seg_sub1_tail(h, s, &nodes);
+        return r ? r : seg_sub2_head(h, s, &nodes);
+    });
+    if (!rc) rc = add_loop(2, h->cfg.dt);
+    if (!rc) rc = add_segment([&](cudaStream_t s) {
+        int r = seg_sub2_tail(h, s, &nodes);
+        return (r || !strang) ? r : seg_sub1_head(h, s, dt1, &nodes);
+    });
+    if (!rc && strang) rc = add_loop(1, dt1);
+    if (!rc && strang) rc = add_segment([&](cudaStream_t s) { return seg_sub1_tail(h, s, &nodes); });
+    if (rc) {
+        cudaGraphDestroy(g);
+        return rc;
+    }
+    cudaGraphExec_t x = nullptr;
+    cudaError_t ce = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    GCK(ce);
+    h->step_exec[h->cur] = x;
+    h->step_graph_nodes[h->cur] = nodes;
+    return PIC_OK;
+}
+
+// nsteps steps as graph launches; counts and status read back once at the end
+static int step_graphs(pic_handle *h, int nsteps, long long *s1, long long *s2)
+{
+    int rc;
+    if (!h->d_count) {
+        if ((rc = dalloc(h, &h->d_count, 2))) return rc;
+        GCK(cudaMallocHost((void **)&h->h_count, 2 * sizeof(int)));
+    }
+    GCK(cudaMemsetAsync(h->d_count, 0, 2 * sizeof(int), h->stream));
+    for (int n = 0; n < nsteps; ++n) {
+        if (!h->step_exec[h->cur] && (rc = build_step_graph(h))) return rc;
+        GCK(cudaGraphLaunch(h->step_exec[h->cur], h->stream));
+        h->launches += h->step_graph_nodes[h->cur];
+        ++h->steps_done;
+        if (h->cfg.sort_every > 0 && h->steps_done % h->cfg.sort_every == 0)
+            if ((rc = sort_markers(h))) return rc;
+    }
+    GCK(cudaMemcpyAsync(h->h_count, h->d_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if ((rc = read_ctrl(h))) return rc;
+    *s1 = h->h_count[0];
+    *s2 = h->h_count[1];
+    h->launches += 2 * (*s1 + *s2);
+    h->marker_sweeps += *s1 * h->np;
+    for (int which = 1; which <= 2; ++which)
+        if ((rc = check_status(h, which))) return rc;
+    return PIC_OK;
+}
+
 extern "C" int pic_step(pic_handle *h, int32_t nsteps, int64_t *iters_I, int64_t *iters_II)
 {
     if (!h) return PIC_ERR_INVALID;
@@ -777,6 +1016,14 @@ extern "C" int pic_step(pic_handle *h, int32_t nsteps, int64_t *iters_I, int64_t
     long long s1 = 0, s2 = 0;
     int rc = PIC_OK;
     for (int n = 0; n < nsteps; ++n) {
+        // graph steps once a host-loop step has opted the kernels in to their shared memory
+        if (h->host_steps > 0 && graph_eligible(h)) {
+            long long g1 = 0, g2 = 0;
+            rc = step_graphs(h, nsteps - n, &g1, &g2);
+            s1 += g1;
+            s2 += g2;
+            break;
+        }
         int i1 = 0, i2 = 0, i3 = 0;
         if (h->cfg.splitting == PIC_SPLIT_STRANG) {
             if ((rc = substep1(h, &i1, 0.5 * h->cfg.dt))) break;
@@ -790,6 +1037,7 @@ extern "C" int pic_step(pic_handle *h, int32_t nsteps, int64_t *iters_I, int64_t
         s1 += i1 + i3;
         s2 += i2;
         ++h->steps_done;
+        ++h->host_steps;
         if (h->cfg.sort_every > 0 && h->steps_done % h->cfg.sort_every == 0)
             if ((rc = sort_markers(h))) break;
     }
@@ -958,6 +1206,7 @@ extern "C" int pic_gather(pic_handle *h, int32_t field, double *out)
 extern "C" int pic_set_warm_mlp(pic_handle *h, pic_mlp *m)
 {
     if (!h) return PIC_ERR_INVALID;
+    if (h->mlp != m) drop_graphs(h);
     h->mlp = m;
     return PIC_OK;
 }

@@ -288,37 +288,91 @@ struct AccNative {
     R v;
     __device__ __forceinline__ void clear() { v = R(0); }
     template <typename T> __device__ __forceinline__ void add(T x) { v += x; }
-    __device__ __forceinline__ double total() const { return (double)v; }
+    // sum over the warp, in every lane, in the accumulator's own precision
+    __device__ __forceinline__ double warp_total() const
+    {
+        R t = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        return (double)t;
+    }
 };
 
+// Knuth's TwoSum: a + b = s + e exactly (float, any magnitudes)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// Compensated float pair with a bias: hi starts at 2^BL, far above any lane sum
+// of the deposits it collects, so every add satisfies |hi| >= |x| and Dekker's
+// Fast2Sum (three operations) recovers its rounding error exactly into lo, and
+// hi - 2^BL is exact at read-out (Sterbenz, as long as the lane sum stays below
+// 2^(BL-1)).  The sweeps take 2^BL = 4096 K! (rounded up to a power of two): their
+// values are at most about K! in the scaled units of bspline_scaled, so a lane may
+// collect some two thousand full-size values between flushes.  The error left is
+// lo's own rounding: each add's error is at most ulp(2^BL)/2 (about 1e-3 K!), so
+// lo stays a small random sum whose rounding is near 1e-11 of the lane sum, against
+// about eps sqrt(n) of the sum for a plain float sum of n markers.
+template <int BL>
 struct AccComp {
     float hi, lo;
-    __device__ __forceinline__ void clear() { hi = 0.f; lo = 0.f; }
+    static constexpr float bias() { return (float)(1u << BL); }
+    __device__ __forceinline__ void clear() { hi = bias(); lo = 0.f; }
     __device__ __forceinline__ void add(float x)
     {
         const float s = hi + x;
-        const float bp = s - hi;
-        const float e = (hi - (s - bp)) + (x - bp);   // hi + x = s + e exactly
+        lo += x - (s - hi);
         hi = s;
-        lo += e;
     }
-    __device__ __forceinline__ double total() const { return (double)hi + (double)lo; }
+    // the warp sum of (hi - bias) + lo as a float pair (the butterfly adds pairs
+    // with TwoSum, so no float rounding of the partial sums is lost), read out in
+    // double
+    __device__ __forceinline__ double warp_total() const
+    {
+        float h = hi - bias(), l = lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            float sum, e;
+            two_sum(h, h2, sum, e);
+            h = sum;
+            l = (l + l2) + e;
+        }
+        return (double)h + (double)l;
+    }
 };
+
+// log2 of the bias for degree K: 12 + ceil(log2 K!)
+template <int K> struct CompBias;
+template <> struct CompBias<2> { static constexpr int v = 13; };
+template <> struct CompBias<3> { static constexpr int v = 15; };
+template <> struct CompBias<4> { static constexpr int v = 17; };
+template <> struct CompBias<5> { static constexpr int v = 19; };
 
 struct AccDouble {
     double v;
     __device__ __forceinline__ void clear() { v = 0.0; }
     __device__ __forceinline__ void add(float x) { v += (double)x; }
     __device__ __forceinline__ void add(double x) { v += x; }
-    __device__ __forceinline__ double total() const { return v; }
+    __device__ __forceinline__ double warp_total() const
+    {
+        double t = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        return t;
+    }
 };
 
-// accumulator kinds of the sweeps (pic_config.deposit)
+// accumulator kinds of the sweeps (pic_config.deposit), for degree K
 enum : int { ACC_NATIVE = 0, ACC_COMP = 1, ACC_DOUBLE = 2 };
-template <typename R, int ACC> struct AccOf;
-template <typename R> struct AccOf<R, ACC_NATIVE> { using T = AccNative<R>; };
-template <typename R> struct AccOf<R, ACC_COMP> { using T = AccComp; };
-template <typename R> struct AccOf<R, ACC_DOUBLE> { using T = AccDouble; };
+template <typename R, int ACC, int K> struct AccOf;
+template <typename R, int K> struct AccOf<R, ACC_NATIVE, K> { using T = AccNative<R>; };
+template <typename R, int K> struct AccOf<R, ACC_COMP, K> { using T = AccComp<CompBias<K>::v>; };
+template <typename R, int K> struct AccOf<R, ACC_DOUBLE, K> { using T = AccDouble; };
 // the accumulator a form uses unless asked otherwise
 template <typename R> struct DefaultAcc { static constexpr int v = std::is_same<R, float>::value ? ACC_COMP : ACC_NATIVE; };
 
@@ -327,10 +381,13 @@ template <typename R> struct DefaultAcc { static constexpr int v = std::is_same<
 // NS partial sums for the consecutive grid nodes b0 .. b0+NS-1 around the warp's
 // base cell; a piece whose NV values fall on nodes cp - r (r = 0..NV-1) goes to
 // slots (cp - base) + OFF - r, chosen by a switch so that the array stays in
-// registers.  flush() sums each slot over the warp (butterfly) and adds it, in
-// double, to the block's shared-memory row; only lanes 0..NS-1 issue an atomic.
-// With a plain float accumulator the butterfly runs in float (the original
-// float form); the other accumulators are reduced in double.
+// registers.  When the warp's base cell advances by one (the common case for
+// sorted markers) only the lowest slot leaves the window: it is summed over the
+// warp and added to the block's shared-memory row, and the other slots move
+// down; any other change of base flushes every slot.  Warp sums of the plain
+// float accumulator are formed in float; those of the compensated pair as float
+// pairs; only the one value written per node is converted to double (GB300's
+// FP64 pipe is narrow, so the window keeps double arithmetic out of its loop).
 // ---------------------------------------------------------------------------
 template <typename R, int NS, int NV, int OFF, int OMIN, int OMAX, typename A = AccNative<R>>
 struct DepWindow {
@@ -361,33 +418,45 @@ struct DepWindow {
         default: return false;
         }
     }
-    // all 32 lanes must call; row0 = shared-memory index of slot 0; the warp sums
-    // are multiplied by `scale` in double (the marker weight enters here)
+    // slot S summed over the warp, added (times `scale`, in double) to s_row[row0 + S]
+    // by lane 0; all 32 lanes must call
+    template <int S>
+    __device__ __forceinline__ void flush_slot(double *s_row, int row0, double scale)
+    {
+        const double t = acc[S].warp_total();
+        if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(&s_row[row0 + S], scale * t);
+        acc[S].clear();
+    }
+    // every slot to the row (row0 = shared-memory index of slot 0): lane s keeps the
+    // warp sum of slot s, and lanes 0..NS-1 write in one step; all lanes call
     __device__ __forceinline__ void flush(double *s_row, int row0, double scale)
     {
         const int lane = threadIdx.x & 31;
-        if constexpr (std::is_same<A, AccNative<float>>::value) {
-            float mine = 0.f;
+        double mine = 0.0;
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                float v = acc[s].v;
+        for (int q = 0; q < NS; ++q) {
+            const double t = acc[q].warp_total();
+            if (lane == q) mine = t;
+            acc[q].clear();
+        }
+        if (lane < NS && mine != 0.0) atomicAdd(&s_row[row0 + lane], scale * mine);
+    }
+    // the warp's base cell moved by `d` (warp-uniform); row0 = index of slot 0 for
+    // the old base.  All lanes must call.
+    __device__ __forceinline__ void advance(int d, double *s_row, int row0, double scale)
+    {
+        if (d == 1) {
+            flush_slot<0>(s_row, row0, scale);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == s) mine = v;
-                acc[s].clear();
-            }
-            if (lane < NS && mine != 0.f) atomicAdd(&s_row[row0 + lane], scale * (double)mine);
+            for (int q = 0; q + 1 < NS; ++q) acc[q] = acc[q + 1];
+            acc[NS - 1].clear();
+        } else if (d == -1) {
+            flush_slot<NS - 1>(s_row, row0, scale);
+#pragma unroll
+            for (int q = NS - 1; q > 0; --q) acc[q] = acc[q - 1];
+            acc[0].clear();
         } else {
-            double mine = 0.0;
-#pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                double v = acc[s].total();
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == s) mine = v;
-                acc[s].clear();
-            }
-            if (lane < NS && mine != 0.0) atomicAdd(&s_row[row0 + lane], scale * mine);
+            flush(s_row, row0, scale);
         }
     }
 };

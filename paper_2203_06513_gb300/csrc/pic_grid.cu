@@ -163,6 +163,7 @@ __device__ void decide(const ConvArgs &A)
 {
     DevCtrl *c = A.ctrl;
     __threadfence();
+    if (A.count) *A.count += 1;
     const double d = (A.subsystem == 1) ? bits_to_double(c->dmax_bits) : 0.0;
     const double e = bits_to_double(c->emax_bits);
     const double ep = bits_to_double(c->eprev_bits);

@@ -42,6 +42,14 @@ struct pic_handle {
     void *rctx = nullptr;
     double *red = nullptr;          // 4 doubles: packed control entries
 
+    // one step as a CUDA graph with device-ended loops (one per marker copy cur)
+    cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+    int step_graph_nodes[2] = {0, 0};   // kernel nodes outside the loops
+    cudaStream_t cap = nullptr;         // private capture stream
+    int *d_count = nullptr;             // sweeps of subsystems I and II (graph mode)
+    int *h_count = nullptr;             // pinned readback of d_count
+    int host_steps = 0;                 // steps taken by host loops (the first one opts kernels in)
+
     // grid state (double)
     double *ex = nullptr, *ey = nullptr, *ez = nullptr, *ay = nullptr, *az = nullptr;
     double *ek = nullptr, *ebar = nullptr, *ga_y = nullptr, *ga_z = nullptr, *jb[2] = {nullptr, nullptr};

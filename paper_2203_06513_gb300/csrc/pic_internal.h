@@ -146,6 +146,7 @@ struct ConvArgs {
     double *pair[2][2];
     unsigned long long cond_handle;
     StageImages img;    // SOLVE1: f.x = ebar image; SOLVE2: ak, lo
+    int *count;         // graph mode of single runs: sweeps counted by the decision (or NULL)
 };
 
 int launch_conv(const ConvArgs &a, cudaStream_t s);

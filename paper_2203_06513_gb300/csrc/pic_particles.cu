@@ -398,7 +398,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     // window: blocks of KB = K + kCdMax values anchored at the larger end cell,
     // max(c0, c1) - wb in [0, 3]; V1 nodes wb - KB + 1 .. wb + 3
     constexpr int KB = K + kCdMax;
-    DepWindow<R, KB + 3, KB, KB - 1, 0, 3, typename AccOf<R, ACC>::T> win;
+    DepWindow<R, KB + 3, KB, KB - 1, 0, 3, typename AccOf<R, ACC, K>::T> win;
     win.clear();
     int wb = INT_MIN;
 
@@ -416,7 +416,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
             if (lead == INT_MAX) break;                    // whole warp past the chunk end
             if (lead != wb) {
-                if (wb != INT_MIN) win.flush(s_acc, wb - (KB - 1) + H, wdx);
+                if (wb != INT_MIN) win.advance(lead - wb, s_acc, wb - (KB - 1) + H, wdx);
                 wb = lead;
             }
             const unsigned amask = __ballot_sync(0xffffffffu, act);
@@ -759,8 +759,8 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     __syncthreads();
     const double w = A.w * inv_fact;
     const R one = R(1);
-    // window: marker cells wb .. wb+3 (wb = the warp's lowest), V0 nodes wb-K .. wb+3
-    DepWindow<R, K + 4, K + 1, K, 0, 3, typename AccOf<R, ACC>::T> wy, wz;
+    // window: marker cells wb .. wb+2 (wb = the warp's lowest), V0 nodes wb-K .. wb+2
+    DepWindow<R, K + 3, K + 1, K, 0, 2, typename AccOf<R, ACC, K>::T> wy, wz;
     wy.clear();
     wz.clear();
     int wb = INT_MIN;
@@ -778,8 +778,8 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
             if (lead == INT_MAX) break;
             if (lead != wb) {
                 if (wb != INT_MIN) {
-                    wy.flush(s_sy, wb - K + H, w);
-                    wz.flush(s_sz, wb - K + H, w);
+                    wy.advance(lead - wb, s_sy, wb - K + H, w);
+                    wz.advance(lead - wb, s_sz, wb - K + H, w);
                 }
                 wb = lead;
             }
@@ -829,11 +829,12 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
                 vy[r] = fy * v[r];
                 vz[r] = fz * v[r];
             }
+            // a zero factor deposits nothing (a linearly polarised pump keeps A_z = 0)
             if (!wy.put(c - wb, vy)) {
 #pragma unroll
                 for (int r = 0; r <= K; ++r) atomicAdd(&s_sy[c - r + H], w * (double)vy[r]);
             }
-            if (!wz.put(c - wb, vz)) {
+            if (fz != R(0) && !wz.put(c - wb, vz)) {
 #pragma unroll
                 for (int r = 0; r <= K; ++r) atomicAdd(&s_sz[c - r + H], w * (double)vz[r]);
             }
@@ -926,7 +927,7 @@ __global__ void __launch_bounds__(256) k_charge(DiagArgs A)
         const int lead = __reduce_min_sync(0xffffffffu, act ? c : INT_MAX);
         if (lead == INT_MAX) break;                    // whole warp past the chunk end
         if (lead != wb) {
-            if (wb != INT_MIN) win.flush(s_acc, wb - K + H, A.w);
+            if (wb != INT_MIN) win.advance(lead - wb, s_acc, wb - K + H, A.w);
             wb = lead;
         }
         if (!act) continue;

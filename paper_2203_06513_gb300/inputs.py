@@ -142,10 +142,26 @@ def particles(w: Workload, np_override: int | None = None, workers: int = 1):
     seed (w.seed, c), so the arrays do not depend on how many processes draw
     them; workers > 1 uses a pool of spawned processes (safe after CUDA start)."""
     n = w.np if np_override is None else int(np_override)
-    x = np.empty(n, dtype=np.float64)
-    p = np.empty(n, dtype=np.float64)
-    starts = list(range(0, n, CHUNK))
-    jobs = [(w.seed, c, min(CHUNK, n - s), w.L, w.eps, w.kappa, w.vth) for c, s in enumerate(starts)]
+    return particles_range(w, 0, n, workers=workers, total=n)
+
+
+def particles_range(w: Workload, lo: int, hi: int, workers: int = 1, total: int | None = None):
+    """Markers [lo, hi) of the plasma of `total` (default w.np) markers: the same
+    values as particles() at those indices, drawing only the chunks they lie in."""
+    total = w.np if total is None else int(total)
+    if not 0 <= lo <= hi <= total:
+        raise ValueError("bad marker range")
+    x = np.empty(hi - lo, dtype=np.float64)
+    p = np.empty(hi - lo, dtype=np.float64)
+    c0, c1 = lo // CHUNK, (hi + CHUNK - 1) // CHUNK
+    starts = [c * CHUNK for c in range(c0, c1)]
+    jobs = [(w.seed, c, min(CHUNK, total - c * CHUNK), w.L, w.eps, w.kappa, w.vth) for c in range(c0, c1)]
+
+    def place(s, xc, pc):
+        a, b = max(s, lo), min(s + xc.size, hi)
+        if b > a:
+            x[a - lo:b - lo] = xc[a - s:b - s]
+            p[a - lo:b - lo] = pc[a - s:b - s]
     if workers > 1 and len(jobs) > 1:
         import concurrent.futures as cf
         import multiprocessing as mp
@@ -153,13 +169,11 @@ def particles(w: Workload, np_override: int | None = None, workers: int = 1):
                                     mp_context=mp.get_context("spawn")) as ex:
             results = ex.map(_chunk, jobs)
             for s, (xc, pc) in zip(starts, results):
-                x[s:s + xc.size] = xc
-                p[s:s + pc.size] = pc
+                place(s, xc, pc)
     else:
         for s, job in zip(starts, jobs):
             xc, pc = _chunk(job)
-            x[s:s + xc.size] = xc
-            p[s:s + pc.size] = pc
+            place(s, xc, pc)
     return x, p
 
 

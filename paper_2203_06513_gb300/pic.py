@@ -77,9 +77,10 @@ def load(path: str | None = None):
     H = ctypes.POINTER(ctypes.c_void_p)
     L.pic_init.argtypes = [ctypes.POINTER(pic_config), ctypes.POINTER(pic_arrays), ctypes.c_int32,
                            ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
-    L.pic_init_split.argtypes = [ctypes.POINTER(pic_config), ctypes.POINTER(pic_arrays), ctypes.c_int32,
-                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                 ctypes.POINTER(ctypes.c_void_p)]
+    if hasattr(L, "pic_init_split"):
+        L.pic_init_split.argtypes = [ctypes.POINTER(pic_config), ctypes.POINTER(pic_arrays), ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_void_p)]
     L.pic_get_state.argtypes = [ctypes.c_void_p, ctypes.POINTER(pic_arrays), ctypes.c_int32]
     L.pic_deposit.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
     L.pic_gather.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
