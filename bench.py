@@ -167,11 +167,15 @@ class ClockSampler:
 
 
 def run_form(pic, torch, w, arrays, precision, warm, steps, warmup, stream, mlp=None, deposit=0,
-             kernel_steps=5, split_run=None):
+             kernel_steps=5, split_run=None, warm_field=None):
     """Advance one replica (or, with split_run = (reducer, local count), this rank's
-    share of one plasma) from host arrays; CUDA-event timing of `steps` steps."""
+    share of one plasma) from host arrays; CUDA-event timing of `steps` steps.  With a
+    warm start the field starts from the proposal's (warm_field) unless told otherwise."""
     x, p, ay, az, ey, ez = arrays
-    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2, deposit=deposit)
+    if warm_field is None:
+        warm_field = 1 if warm != pic.PIC_WARM_NONE else 0
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2, deposit=deposit,
+                                   warm_field=warm_field)
     reducer = None
     if split_run is not None:
         reducer, cfg.np = split_run
@@ -216,7 +220,8 @@ def drift_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None, e
     """The workload over its configured length: relative energy error and Gauss
     residual sampled every `every` steps (untimed)."""
     x, p, ay, az, ey, ez = arrays
-    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2)
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2,
+                                   warm_field=1 if warm != pic.PIC_WARM_NONE else 0)
     g = pic.Pic(cfg, x, p, ay, az, ey, ez, stream=stream.cuda_stream)
     if mlp is not None:
         mlp.attach(g)
@@ -249,7 +254,8 @@ def e2e_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None):
     hp = torch.from_numpy(p).pin_memory().numpy()
     out = {k: torch.empty(w.np, dtype=torch.float64).pin_memory().numpy() for k in ("x", "p")}
     out.update({k: np.empty(w.nx) for k in ("ex", "ey", "ez", "ay", "az")})
-    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2)
+    cfg = pic.Config.from_workload(w, precision=precision, warm_start=warm, sort_every=2,
+                                   warm_field=1 if warm != pic.PIC_WARM_NONE else 0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = pic.Pic(cfg, hx, hp, ay, az, ey, ez, stream=stream.cuda_stream)
@@ -391,6 +397,7 @@ def main():
     ap.add_argument("--impl", default="libpic", choices=["libpic", "reference"])
     ap.add_argument("--np", type=float, default=None, help="override N_p (smaller runs)")
     ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-fp64-warm", action="store_true", help="skip the FP64 runs with a predicted start")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--drift-steps", type=int, default=1000,
@@ -468,6 +475,17 @@ def main():
     r64 = run_form(pic, torch, w, arrays, pic.PIC_FP64, pic.PIC_WARM_NONE, k64, max(1, min(args.warmup, 3)),
                    stream, split_run=split_run)
     barrier()
+    # the FP64 form started from a proposal and its field: the explicit predictor
+    # and the learned one (what the network gains over the plain method)
+    r64w = {}
+    if not args.no_fp64_warm:
+        for name, wm in (("explicit", pic.PIC_WARM_EXPLICIT), ("learned", pic.PIC_WARM_MLP)):
+            if wm == pic.PIC_WARM_MLP and mlp is None:
+                continue
+            r64w[name] = run_form(pic, torch, w, arrays, pic.PIC_FP64, wm, k64, max(1, min(args.warmup, 3)),
+                                  stream, mlp if wm == pic.PIC_WARM_MLP else None, split_run=split_run,
+                                  kernel_steps=1)
+        barrier()
     e2e = None if args.no_e2e else e2e_run(pic, torch, w, arrays, pic.PIC_FP32, head_warm, args.steps,
                                            stream, mlp)
     barrier()
@@ -501,6 +519,7 @@ def main():
     ms_head = max_over_ranks(r_head["ms"])
     ms_expl = max_over_ranks(r_expl["ms"])
     ms64 = max_over_ranks(r64["ms"])
+    ms64w = {k: max_over_ranks(r["ms"]) for k, r in r64w.items()}
     e2e_s = max_over_ranks(e2e["s"]) if e2e else None
     per_rank = w.np / ws if split_mode else w.np          # markers each rank advances
     value = R.whole_job_rate(per_rank, ws, args.steps, ms_head / 1e3)
@@ -558,6 +577,10 @@ def main():
                      "rel_energy_err": r64["rel_energy_err"], "gauss_residual": r64["gauss"],
                      "sweeps_per_step": sweeps(r64, k64),
                      "speedup_fp32_learned_over_fp64": value / v64},
+            "fp64_predicted_start": {
+                k: {"value": R.whole_job_rate(per_rank, ws, k64, ms64w[k] / 1e3),
+                    "ms_per_step": ms64w[k] / k64, "rel_energy_err": r["rel_energy_err"],
+                    "sweeps_per_step": sweeps(r, k64)} for k, r in r64w.items()},
             "fp32_explicit": {"value": v_expl, "unit": UNIT, "ms_per_step": ms_expl / args.steps,
                               "rel_energy_err": r_expl["rel_energy_err"],
                               "sweeps_per_step": sweeps(r_expl, args.steps)},

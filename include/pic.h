@@ -118,6 +118,10 @@ typedef struct {
     int32_t splitting;   /* PIC_SPLIT_LIE or PIC_SPLIT_STRANG                       */
     double  hbar;        /* normalised Planck constant; nonzero turns the spin on
                             (FP64 form, Lie--Trotter steps, no learned warm start) */
+    int32_t warm_field;  /* with a warm start: 1 = also start subsystem I's field from
+                            the proposal, e^(0) = e^n - M1^{-1} j(x^n -> x^(0)), so that
+                            the first sweep's kick uses a field consistent with x^(0)
+                            (the fixed point is the same; only the sweep count changes) */
 } pic_config;
 
 /* FP64 arrays of the discrete state u = (X, P, S, e_x, e_y, e_z, a_y, a_z), Sec. 3.1.

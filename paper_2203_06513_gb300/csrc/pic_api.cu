@@ -318,7 +318,8 @@ extern "C" int pic_init_split(const pic_config *cfg, const pic_arrays *in, int32
         (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE) || !in->x || !in->p || !in->ay || !in->az ||
         !std::isfinite(c.weight) || c.warm_start < 0 || c.warm_start > 2 || c.sort_every < 0 ||
         c.deposit < PIC_ACC_DEFAULT || c.deposit > PIC_ACC_DOUBLE ||
-        (c.splitting != PIC_SPLIT_LIE && c.splitting != PIC_SPLIT_STRANG) || !std::isfinite(c.hbar)) {
+        (c.splitting != PIC_SPLIT_LIE && c.splitting != PIC_SPLIT_STRANG) || !std::isfinite(c.hbar) ||
+        c.warm_field < 0 || c.warm_field > 1 || (c.warm_field && c.warm_start == PIC_WARM_NONE)) {
         g_init_error = "invalid configuration or missing input array";
         return PIC_ERR_INVALID;
     }
@@ -651,6 +652,7 @@ static ConvArgs conv1_args(pic_handle *h, double dt)
     c.taps = h->d_tapM1;
     c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
     c.dt = dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6;   // FP32: estimated position error, cells relative to max(1, |delta|)
+    c.erel = h->cfg.warm_field ? kFieldIncrementRelPredicted : kFieldIncrementRel;
     c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 1; c.ctrl = h->ctrl;
     c.pair[0][0] = h->jb[0]; c.pair[0][1] = h->jb[1];
     return c;
@@ -697,6 +699,23 @@ static WarmArgs warm_args(pic_handle *h, double dt)
     return wa;
 }
 
+// The predicted start of subsystem I (warm_field): delta^(0) and j^(0) into jb[1]
+// (cleared by the preparation; the first sweep deposits into jb[0] and its solve
+// clears jb[1]), then e^(0) = e^n - M1^{-1} j^(0) and ebar^(0).
+static int predicted_start(pic_handle *h, double dt, cudaStream_t s)
+{
+    Sweep1Args a = sweep1_args(h, dt);
+    a.warm = h->cfg.warm_start == PIC_WARM_EXPLICIT ? 1 : 0;   // else the network's delta is there
+    if (launch_predeposit(a, h->jb[1], h->num_sms * 4, s)) return fail(h, PIC_ERR_INVALID, "predeposit");
+    int rc;
+    if (s == h->stream && (rc = reduce(h, PIC_REDUCE_SUM, h->jb[1], h->M))) return rc;   // split runs
+    ConvArgs c = conv1_args(h, dt);
+    c.mode = CONV_START1;
+    c.in[0] = h->jb[1];
+    if (launch_conv(c, s)) return fail(h, PIC_ERR_CUDA, "k_conv launch");
+    return PIC_OK;
+}
+
 static int substep1(pic_handle *h, int *iters, double dt)
 {
     int rc;
@@ -715,10 +734,15 @@ static int substep1(pic_handle *h, int *iters, double dt)
         CKL_N("launch_warm_mlp");
         if ((rc = timed_end(h, 3))) return rc;
     }
+    if (h->cfg.warm_field) {
+        if ((rc = predicted_start(h, dt, h->stream))) return rc;
+        CKL_N("predicted start");
+        ++h->launches;
+    }
     int it = 0;
     for (;;) {
         a.j = h->jb[it & 1];
-        a.warm = (it == 0 && h->cfg.warm_start == PIC_WARM_EXPLICIT) ? 1 : 0;
+        a.warm = (it == 0 && h->cfg.warm_start == PIC_WARM_EXPLICIT && !h->cfg.warm_field) ? 1 : 0;
         a.first = it == 0 ? 1 : 0;
         if ((rc = timed_begin(h))) return rc;
         if (launch_sweep1(a, h->sweep_grid, h->sweep_block, h->smem1, h->stream))
@@ -851,6 +875,11 @@ static int seg_sub1_head(pic_handle *h, cudaStream_t s, double dt, int *nodes)
         if (launch_warm_mlp(warm_args(h, dt), h->num_sms, s)) return fail(h, PIC_ERR_CUDA, "warm-start launch");
         ++*nodes;
     }
+    if (h->cfg.warm_field) {
+        int rc;
+        if ((rc = predicted_start(h, dt, s))) return rc;
+        *nodes += 2;
+    }
     return PIC_OK;
 }
 
@@ -889,7 +918,7 @@ static int loop_body(pic_handle *h, cudaStream_t s, int which, double dt, unsign
     if (which == 1) {
         Sweep1Args a = sweep1_args(h, dt);
         a.graph = 1;
-        a.warm = h->cfg.warm_start == PIC_WARM_EXPLICIT ? 1 : 0;   // applied when iter == 0
+        a.warm = (h->cfg.warm_start == PIC_WARM_EXPLICIT && !h->cfg.warm_field) ? 1 : 0;   // applied when iter == 0
         a.j = h->jb[0];
         if (launch_sweep1(a, h->sweep_grid, h->sweep_block, h->smem1, s)) return fail(h, PIC_ERR_INVALID, "sweep1");
         ConvArgs c = conv1_args(h, dt);

@@ -130,7 +130,7 @@ static void build_tables(pic_ensemble *e)
         c.M = h->M; c.d_start = h->tapM1_start; c.ntap = h->tapM1_n; c.mode = CONV_SOLVE1; c.ncomp = 1;
         c.taps = h->d_tapM1;
         c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
-        c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6;
+        c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6; c.erel = kFieldIncrementRel;
         c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 1; c.ctrl = h->ctrl;
         c.graph = 1;
         c.pair[0][0] = h->jb[0]; c.pair[0][1] = h->jb[1];
@@ -354,7 +354,7 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
     for (int r = 0; r < nruns; ++r)
         if ((cfgs[r].deposit != PIC_ACC_DEFAULT && cfgs[r].deposit != PIC_ACC_COMPENSATED &&
              !(cfgs[r].precision == PIC_FP64 && cfgs[r].deposit == PIC_ACC_DOUBLE)) ||
-            cfgs[r].splitting != PIC_SPLIT_LIE || cfgs[r].hbar != 0.0) {
+            cfgs[r].splitting != PIC_SPLIT_LIE || cfgs[r].hbar != 0.0 || cfgs[r].warm_field) {
             set_thread_error("ensemble: runs use the default deposit accumulation, Lie--Trotter steps and no spin");
             return PIC_ERR_INVALID;
         }

@@ -101,6 +101,8 @@ struct DiagArgs {
 };
 
 int launch_sweep1(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s);
+// the predicted start of subsystem I: delta^(0) (explicit when a.warm) and its current into jout
+int launch_predeposit(const Sweep1Args &a, double *jout, int grid, cudaStream_t s);
 size_t sweep1_smem(int M, int H, int fp32);
 int launch_sweep2(const Sweep2Args &a, int grid, int block, size_t smem, cudaStream_t s);
 size_t sweep2_smem(int M, int H, int fp32);
@@ -123,7 +125,18 @@ int launch_sort(int fp32, long long np, int M, double tau, PartPtrs src, PartPtr
                 int32_t *counts, int grid, int block, cudaStream_t s);
 
 // ---------------------------------------------------------------- grid
-enum ConvMode { CONV_PLAIN = 0, CONV_SOLVE1 = 1, CONV_SOLVE2 = 2 };
+// FP32 form, subsystem I: the last field increment must be below this fraction of
+// the field's max-norm.  The momenta of the last sweep were updated with the field
+// of the sweep before, so the energy error of a step is proportional to that
+// increment.  Started from e^n the field converges from one side and the error has
+// one sign, step after step (a drift, measured 1e-12 of the energy a step on C2 at
+// 1e-9): 1e-10 is needed.  Started from the field of the proposal (warm_field) the
+// last increment's sign varies and 3e-9 leaves no drift.
+constexpr double kFieldIncrementRel = 1e-10;
+constexpr double kFieldIncrementRelPredicted = 3e-9;
+
+// CONV_START1: e^(0) = e^n - M1^{-1} j^(0) and ebar^(0), without a convergence decision
+enum ConvMode { CONV_PLAIN = 0, CONV_SOLVE1 = 1, CONV_SOLVE2 = 2, CONV_START1 = 3 };
 
 struct ConvArgs {
     int M, d_start, ntap, mode, ncomp;
@@ -137,6 +150,7 @@ struct ConvArgs {
     const double *r0[2];    // SOLVE2: P^{-1} b
     double *zero[2];        // deposit buffers of the next sweep, cleared here
     double dt, dx, tol, dtol;
+    double erel;        // FP32 subsystem I: field increment tolerance relative to the field's max-norm
     int max_iter, fp32, subsystem;
     DevCtrl *ctrl;
     // graph mode: in[c] = pair[c][iter & 1], zero[c] = pair[c][(iter + 1) & 1]

@@ -580,6 +580,109 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
     sweep1_range<K, R, ACC>(A, beg, end, smem, q);
 }
 
+// ---------------------------------------------------------------------------
+// Start of subsystem I with a predicted field: the proposal x^(0) = x^n + delta^(0)
+// (the explicit predictor dt p^n / gamma(p^n, A(x^n)), written here, or the learned
+// one already in delta) and its path-integrated current j^(0), deposited as in the
+// sweeps, so that the fixed-point loop can start from e^(0) = e^n - M1^{-1} j^(0),
+// the field consistent with x^(0).  The fixed point does not depend on the start;
+// the starting field sets how far the first sweep's kick is off.
+// ---------------------------------------------------------------------------
+template <int K, typename R, int ACC>
+__global__ void __launch_bounds__(256) k_predeposit(Sweep1Args A, double *jout)
+{
+    extern __shared__ __align__(16) double s_row[];
+    using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
+    const int H = A.H;
+    const int W = A.M + 2 * H;
+    R2 *s_a = reinterpret_cast<R2 *>(s_row + W);      // a / K! with the periodic halo
+    const double inv_fact_s = 1.0 / (double)Fact<K>::v;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        s_row[i] = 0.0;
+        const int g = wrap_cell(i - H, A.M);
+        if constexpr (Real<R>::fp32) {
+            if (A.img.a) s_a[i] = A.img.a[g];
+            else s_a[i] = make_float2((float)(A.ay[g] * inv_fact_s), (float)(A.az[g] * inv_fact_s));
+        } else {
+            s_a[i] = make_double2(A.ay[g] * inv_fact_s, A.az[g] * inv_fact_s);
+        }
+    }
+    __syncthreads();
+    const R *tp = static_cast<const R *>(A.P.t);
+    const R *pp = static_cast<const R *>(A.P.p);
+    R *dp = static_cast<R *>(A.P.delta);
+    const R tau = (R)(A.dt / A.dx);
+    const double inv_fact = 1.0 / (double)Fact<K>::v;
+    const double wdx = A.w * A.dx * inv_fact;
+    const R dlim = (R)A.Dlim;
+    constexpr int KB = K + kCdMax;
+    DepWindow<R, KB + 3, KB, KB - 1, 0, 3, typename AccOf<R, ACC, K>::T> win;
+    win.clear();
+    int wb = INT_MIN;
+    bool bad = false;
+    long long beg, end;
+    {
+        long long chunk = (A.np + gridDim.x - 1) / gridDim.x;
+        chunk = (chunk + 31) & ~31LL;
+        beg = (long long)blockIdx.x * chunk;
+        end = beg + chunk < A.np ? beg + chunk : A.np;
+    }
+    for (long long base = beg; base < end; base += blockDim.x) {
+        const long long a = base + threadIdx.x;
+        const bool act = a < end;
+        const int c0 = warp_unwrap_cell(act ? A.P.cell[a] : 0, act, A.M, H - A.Dlim);
+        const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
+        if (lead == INT_MAX) break;
+        if (lead != wb) {
+            if (wb != INT_MIN) win.advance(lead - wb, s_row, wb - (KB - 1) + H, wdx);
+            wb = lead;
+        }
+        if (!act) continue;
+        const R t0 = tp[a];
+        R v0[K + 1];
+        bspline_scaled<K, R>(t0, v0);
+        R d;
+        if (A.warm) {
+            R A0y = R(0), A0z = R(0);
+#pragma unroll
+            for (int r = 0; r <= K; ++r) {
+                const R2 q = s_a[c0 - r + H];
+                A0y += q.x * v0[r];
+                A0z += q.y * v0[r];
+            }
+            const R pn = pp[a];
+            d = fdiv_(tau * pn, sqrt_(R(1) + pn * pn + A0y * A0y + A0z * A0z));
+            dp[a] = d;
+        } else {
+            d = dp[a];
+        }
+        if (!(fabs(d) <= dlim)) { bad = true; d = R(0); dp[a] = d; }
+        const R s1 = t0 + d;
+        const R f1 = floor_(s1);
+        int n = (int)f1;
+        R t1 = s1 - f1;
+        if (t1 >= R(1)) { t1 = R(0); n += 1; }
+        R v1[K + 1];
+        bspline_scaled<K, R>(t1, v1);
+        R S0[K], S1[K];
+        S0[0] = v0[0];
+        S1[0] = v1[0];
+#pragma unroll
+        for (int r = 1; r < K; ++r) {
+            S0[r] = S0[r - 1] + v0[r];
+            S1[r] = S1[r - 1] + v1[r];
+        }
+        deposit_cdiff<K>(win, S0, S1, n, c0, wb, H, s_row, wdx);
+    }
+    if (wb != INT_MIN) win.flush(s_row, wb - (KB - 1) + H, wdx);
+    if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
+    __syncthreads();
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        const double v = s_row[i];
+        if (v != 0.0) atomicAdd(&jout[wrap_cell(i - H, A.M)], v);
+    }
+}
+
 size_t sweep1_smem(int M, int H, int fp32)
 {
     const size_t W = (size_t)M + 2 * (size_t)H;
@@ -885,6 +988,25 @@ size_t sweep2_smem(int M, int H, int fp32)
     const size_t W = (size_t)M + 2 * (size_t)H;
     const size_t stages = (size_t)stage_count(fp32) * kTile * (sizeof(int32_t) + 2 * (fp32 ? sizeof(float) : sizeof(double)));
     return 128 + stages + 2 * W * sizeof(double) + (fp32 ? 3 * W * sizeof(float2) : 2 * W * sizeof(double2));
+}
+
+size_t predeposit_smem(int M, int H, int fp32)
+{
+    const size_t W = (size_t)M + 2 * (size_t)H;
+    return W * sizeof(double) + W * (fp32 ? sizeof(float2) : sizeof(double2));
+}
+
+int launch_predeposit(const Sweep1Args &a, double *jout, int grid, cudaStream_t s)
+{
+    const size_t smem = predeposit_smem(a.M, a.H, a.fp32);
+#define LP(KK, RR, AA)                                                                              \
+    if (a.K == KK && (a.fp32 != 0) == std::is_same<RR, float>::value && a.acc == AA) {              \
+        k_predeposit<KK, RR, AA><<<grid, 256, smem, s>>>(a, jout);                                  \
+        return 0;                                                                                   \
+    }
+    PIC_FOR_SWEEP_VARIANTS(LP)
+#undef LP
+    return 1;
 }
 
 int launch_sweep2(const Sweep2Args &a, int grid, int block, size_t smem, cudaStream_t s)
@@ -1556,10 +1678,12 @@ static int set_attrs_r(size_t s1, size_t s2, size_t s3)
            set_attrs_kr<4, R>(s1, s2, s3) | set_attrs_kr<5, R>(s1, s2, s3);
 }
 
-static int set_attrs_sweeps(size_t s1, size_t s2)
+static int set_attrs_sweeps(size_t s1, size_t s2, size_t s3)
 {
     int rc = 0;
 #define ATTRV(KK, RR, AA)                                                                               \
+    rc |= cudaFuncSetAttribute(k_predeposit<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1) != \
+          cudaSuccess;                                                                                  \
     rc |= cudaFuncSetAttribute(k_sweep1<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1) != \
           cudaSuccess;                                                                                  \
     rc |= cudaFuncSetAttribute(k_sweep2<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2) != \
@@ -1617,7 +1741,7 @@ int pic_set_smem_attrs(size_t s1, size_t s2, size_t s3)
     const size_t n1 = std::max(m1, s1), n2 = std::max(m2, s2), n3 = std::max(m3, s3);
     if (n1 == m1 && n2 == m2 && n3 == m3) return 0;
     const int rc = pic::set_attrs_r<float>(n1, n2, n3) | pic::set_attrs_r<double>(n1, n2, n3) |
-                   pic::set_attrs_sweeps(n1, n2);
+                   pic::set_attrs_sweeps(n1, n2, n3);
     if (rc == 0) { m1 = n1; m2 = n2; m3 = n3; }
     return rc;
 }

@@ -45,7 +45,7 @@ class pic_config(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("sort_every", ctypes.c_int32), ("deposit", ctypes.c_int32),
-                ("splitting", ctypes.c_int32), ("hbar", ctypes.c_double)]
+                ("splitting", ctypes.c_int32), ("hbar", ctypes.c_double), ("warm_field", ctypes.c_int32)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -132,21 +132,22 @@ class Config:
     deposit: int = PIC_ACC_DEFAULT
     splitting: int = PIC_SPLIT_LIE
     hbar: float = 0.0
+    warm_field: int = 0
 
     def c(self) -> pic_config:
         return pic_config(self.L, self.nx, self.degree, self.np, self.weight, self.dt, self.tol,
                           self.max_iter, self.precision, self.warm_start, self.sort_every,
-                          self.deposit, self.splitting, self.hbar)
+                          self.deposit, self.splitting, self.hbar, self.warm_field)
 
     @staticmethod
     def from_workload(w, precision=PIC_FP64, warm_start=PIC_WARM_NONE, sort_every=0,
                       tol=None, max_iter=None, deposit=PIC_ACC_DEFAULT,
-                      splitting=PIC_SPLIT_LIE, hbar=None) -> "Config":
+                      splitting=PIC_SPLIT_LIE, hbar=None, warm_field=0) -> "Config":
         return Config(w.L, w.nx, w.degree, w.np, w.weight, w.dt,
                       w.tol if tol is None else tol,
                       w.max_iter if max_iter is None else max_iter,
                       precision, warm_start, sort_every, deposit, splitting,
-                      getattr(w, "hbar", 0.0) if hbar is None else hbar)
+                      getattr(w, "hbar", 0.0) if hbar is None else hbar, warm_field)
 
 
 class Pic:

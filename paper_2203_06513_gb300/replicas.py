@@ -1,12 +1,15 @@
-"""Host logic for runs on several GPUs of one node: independent replicas.
+"""Host logic for runs on several GPUs of one node: ranks, barrier, slowest time.
 
-The step of Sec. 4.2 couples every marker to the whole grid twice per substep
-(the deposit and the field solve), so a single plasma does not partition into
-pieces that advance without an exchange. What does partition is the ensemble:
-each rank advances its own plasma, drawn from its own seed, and no data crosses
-ranks. The only collectives are the timing barrier and the max-over-ranks of the
-timed durations; the whole-job rate is the units all ranks processed divided by
-the slowest rank's time (weak scaling: the work per rank is fixed).
+Two kinds of multi-rank run use it.  Independent replicas (ensembles, and the
+default of the measurement): each rank advances its own plasma, drawn from its
+own seed, and no data crosses ranks.  One plasma split by markers
+(`split.py`): the markers are independent given the fields, so each rank holds
+a share of them and every sum over markers (deposits, charge, energies, the
+fixed-point test's largest increment) is all-reduced through the library's
+reduction callback.  In both, the only collectives added here are the timing
+barrier and the max-over-ranks of the timed durations; the whole-job rate is
+the units all ranks processed divided by the slowest rank's time (weak scaling:
+the work per rank is fixed).
 """
 from __future__ import annotations
 

@@ -33,7 +33,7 @@ def _run(w, cfg, steps, no_graph):
     return st, its, E
 
 
-@pytest.mark.parametrize("case", ["fp64", "fp32_explicit", "fp32_none", "strang"])
+@pytest.mark.parametrize("case", ["fp64", "fp32_explicit", "fp32_none", "strang", "fp32_predicted", "fp64_predicted"])
 def test_graph_steps_match_host_loops(case):
     w = I.Workload("g", nx=96, degree=3, np=30011, seed=23, vth=0.15, pump=0.25)
     kw = {"sort_every": 2}
@@ -43,6 +43,11 @@ def test_graph_steps_match_host_loops(case):
         cfg = pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=pic.PIC_WARM_EXPLICIT, **kw)
     elif case == "fp32_none":
         cfg = pic.Config.from_workload(w, precision=pic.PIC_FP32, **kw)
+    elif case == "fp32_predicted":
+        cfg = pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=pic.PIC_WARM_EXPLICIT, warm_field=1,
+                                       **kw)
+    elif case == "fp64_predicted":
+        cfg = pic.Config.from_workload(w, warm_start=pic.PIC_WARM_EXPLICIT, warm_field=1, **kw)
     else:
         cfg = pic.Config.from_workload(w, splitting=pic.PIC_SPLIT_STRANG, **kw)
     a, ia, Ea = _run(w, cfg, 7, no_graph=False)

@@ -1,11 +1,12 @@
 """What the trained warm-start network gains over the method without it: on the
 C2 grid (M = 2048, cubic, pump 0.2, vth 0.1, dt = 0.05), the same markers stepped
 three ways at identical tolerance -- x^(0) = x^n (the plain method), the explicit
-predictor, and the trained network -- with the mean subsystem-I sweeps a step and
-the final states compared, in the FP32 form (2e7 markers) and in the FP64 form
-(2e6 markers, tolerance 1e-13 on the increments).  The counts are printed for the
-design notes; the network must not need more sweeps than the plain method, and
-all three must reach the same fixed point."""
+predictor, and the trained network, each proposal with the field of its path
+(warm_field) -- with the mean subsystem-I sweeps a step and the final states
+compared, in the FP32 form (2e7 markers) and in the FP64 form (2e6 markers,
+tolerance 1e-13 on the increments).  The counts are printed for the design notes;
+the network must save at least a sweep a step over the plain method, and all
+three must reach the same fixed point."""
 import os
 
 import numpy as np
@@ -34,7 +35,8 @@ def test_learned_warm_start_ab_fp64():
     res = {}
     for name, warm in (("none", pic.PIC_WARM_NONE), ("explicit", pic.PIC_WARM_EXPLICIT),
                        ("learned", pic.PIC_WARM_MLP)):
-        g = pic.Pic(pic.Config.from_workload(w, sort_every=2, warm_start=warm), x, p, ay, az, ey, ez)
+        g = pic.Pic(pic.Config.from_workload(w, sort_every=2, warm_start=warm,
+                                             warm_field=int(warm != pic.PIC_WARM_NONE)), x, p, ay, az, ey, ez)
         if warm == pic.PIC_WARM_MLP:
             mlp.attach(g)
         i1, i2 = g.step(steps)
@@ -42,7 +44,7 @@ def test_learned_warm_start_ab_fp64():
         g.close()
     print("\nsubsystem-I sweeps a step (C2 grid, 2e6 markers, FP64, tol 1e-13): "
           + ", ".join(f"{k} {v[0]:.2f}" for k, v in res.items()))
-    assert res["learned"][0] <= res["none"][0]
+    assert res["learned"][0] <= res["none"][0] - 1
     ref = res["none"][1]
     for name in ("explicit", "learned"):
         st = res[name][1]
@@ -63,7 +65,8 @@ def test_learned_warm_start_ab():
     res = {}
     for name, warm in (("none", pic.PIC_WARM_NONE), ("explicit", pic.PIC_WARM_EXPLICIT),
                        ("learned", pic.PIC_WARM_MLP)):
-        g = pic.Pic(pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=warm, sort_every=2),
+        g = pic.Pic(pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=warm, sort_every=2,
+                                             warm_field=int(warm != pic.PIC_WARM_NONE)),
                     x, p, ay, az, ey, ez)
         if warm == pic.PIC_WARM_MLP:
             mlp.attach(g)
@@ -75,7 +78,7 @@ def test_learned_warm_start_ab():
         res[name] = (i1 / steps, i2 / steps, abs(E["total"] - H0) / H0, st)
     print("\nsubsystem-I sweeps a step (C2 grid, 2e7 markers, FP32): "
           + ", ".join(f"{k} {v[0]:.2f}" for k, v in res.items()))
-    assert res["learned"][0] <= res["none"][0]
+    assert res["learned"][0] <= res["none"][0] - 1
     ref = res["none"][3]
     for name in ("explicit", "learned"):
         st = res[name][3]
