@@ -706,7 +706,10 @@ static int predicted_start(pic_handle *h, double dt, cudaStream_t s)
 {
     Sweep1Args a = sweep1_args(h, dt);
     a.warm = h->cfg.warm_start == PIC_WARM_EXPLICIT ? 1 : 0;   // else the network's delta is there
-    if (launch_predeposit(a, h->jb[1], h->num_sms * 4, s)) return fail(h, PIC_ERR_INVALID, "predeposit");
+    a.j = h->jb[1];
+    a.first = 1;
+    if (launch_predeposit(a, h->sweep_grid, h->sweep_block, h->smem1, s))
+        return fail(h, PIC_ERR_INVALID, "predeposit");
     int rc;
     if (s == h->stream && (rc = reduce(h, PIC_REDUCE_SUM, h->jb[1], h->M))) return rc;   // split runs
     ConvArgs c = conv1_args(h, dt);

@@ -281,21 +281,25 @@ __device__ __forceinline__ int walk_path(R t0, R d, Visit &&visit)
 //                accuracy (Knuth's TwoSum; the pair is read out in double).
 //  AccDouble:    a double sum of float values (exact adds of the products,
 //                on the FP64 pipe).
-// total() returns the lane's sum in double for the warp reduction.
+// warp_part() sums a slot over the warp in the accumulator's own type; value()
+// converts such a sum to double (done by the one lane that writes it).
 // ---------------------------------------------------------------------------
 template <typename R>
 struct AccNative {
     R v;
     __device__ __forceinline__ void clear() { v = R(0); }
     template <typename T> __device__ __forceinline__ void add(T x) { v += x; }
-    // sum over the warp, in every lane, in the accumulator's own precision
-    __device__ __forceinline__ double warp_total() const
+    // sum over the warp, in every lane, in the accumulator's own precision;
+    // value() reads a sum out in double (called by the writing lane only)
+    using Part = R;
+    __device__ __forceinline__ Part warp_part() const
     {
         R t = v;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        return (double)t;
+        return t;
     }
+    __device__ __forceinline__ static double value(Part t) { return (double)t; }
 };
 
 // Knuth's TwoSum: a + b = s + e exactly (float, any magnitudes)
@@ -328,9 +332,10 @@ struct AccComp {
         hi = s;
     }
     // the warp sum of (hi - bias) + lo as a float pair (the butterfly adds pairs
-    // with TwoSum, so no float rounding of the partial sums is lost), read out in
-    // double
-    __device__ __forceinline__ double warp_total() const
+    // with TwoSum, so no float rounding of the partial sums is lost); value()
+    // reads the pair out in double
+    using Part = float2;
+    __device__ __forceinline__ Part warp_part() const
     {
         float h = hi - bias(), l = lo;
 #pragma unroll
@@ -342,8 +347,9 @@ struct AccComp {
             h = sum;
             l = (l + l2) + e;
         }
-        return (double)h + (double)l;
+        return make_float2(h, l);
     }
+    __device__ __forceinline__ static double value(Part t) { return (double)t.x + (double)t.y; }
 };
 
 // log2 of the bias for degree K: 12 + ceil(log2 K!)
@@ -358,13 +364,15 @@ struct AccDouble {
     __device__ __forceinline__ void clear() { v = 0.0; }
     __device__ __forceinline__ void add(float x) { v += (double)x; }
     __device__ __forceinline__ void add(double x) { v += x; }
-    __device__ __forceinline__ double warp_total() const
+    using Part = double;
+    __device__ __forceinline__ Part warp_part() const
     {
         double t = v;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         return t;
     }
+    __device__ __forceinline__ static double value(Part t) { return t; }
 };
 
 // accumulator kinds of the sweeps (pic_config.deposit), for degree K
@@ -389,19 +397,24 @@ template <typename R> struct DefaultAcc { static constexpr int v = std::is_same<
 // pairs; only the one value written per node is converted to double (GB300's
 // FP64 pipe is narrow, so the window keeps double arithmetic out of its loop).
 // ---------------------------------------------------------------------------
-template <typename R, int NS, int NV, int OFF, int OMIN, int OMAX, typename A = AccNative<R>>
+template <typename R, int NS, int NV, int OFF, int OMIN, int OMAX, typename A = AccNative<R>, bool TRACK = false>
 struct DepWindow {
     A acc[NS];
+    // with TRACK: this lane added to the window since its last full flush, so that
+    // moves and flushes of a window nobody wrote to (e.g. A_z = 0) cost one vote
+    bool dirty;
     __device__ __forceinline__ void clear()
     {
 #pragma unroll
         for (int s = 0; s < NS; ++s) acc[s].clear();
+        dirty = false;
     }
     template <int O>
     __device__ __forceinline__ void add_at(const R *v)
     {
 #pragma unroll
         for (int r = 0; r < NV; ++r) acc[O + OFF - r].add(v[r]);
+        dirty = true;
     }
     // returns false when the piece lies outside the window (caller takes the slow path)
     __device__ __forceinline__ bool put(int o, const R *v)
@@ -419,32 +432,44 @@ struct DepWindow {
         }
     }
     // slot S summed over the warp, added (times `scale`, in double) to s_row[row0 + S]
-    // by lane 0; all 32 lanes must call
+    // by lane 0; all 32 lanes must call.  The warp sum stays in the accumulator's
+    // own type and only the writing lane converts it: the double arithmetic of a
+    // flush is then one lane's, not the warp's.
     template <int S>
     __device__ __forceinline__ void flush_slot(double *s_row, int row0, double scale)
     {
-        const double t = acc[S].warp_total();
-        if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(&s_row[row0 + S], scale * t);
+        const typename A::Part t = acc[S].warp_part();
+        if ((threadIdx.x & 31) == 0) {
+            const double v = A::value(t);
+            if (v != 0.0) atomicAdd(&s_row[row0 + S], scale * v);
+        }
         acc[S].clear();
     }
     // every slot to the row (row0 = shared-memory index of slot 0): lane s keeps the
-    // warp sum of slot s, and lanes 0..NS-1 write in one step; all lanes call
+    // warp sum of slot s, and lanes 0..NS-1 convert and write in one step; all
+    // lanes call
     __device__ __forceinline__ void flush(double *s_row, int row0, double scale)
     {
+        if (TRACK && !__any_sync(0xffffffffu, dirty)) return;     // every slot is clear
+        dirty = false;
         const int lane = threadIdx.x & 31;
-        double mine = 0.0;
+        typename A::Part mine{};
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            const double t = acc[q].warp_total();
+            const typename A::Part t = acc[q].warp_part();
             if (lane == q) mine = t;
             acc[q].clear();
         }
-        if (lane < NS && mine != 0.0) atomicAdd(&s_row[row0 + lane], scale * mine);
+        if (lane < NS) {
+            const double v = A::value(mine);
+            if (v != 0.0) atomicAdd(&s_row[row0 + lane], scale * v);
+        }
     }
     // the warp's base cell moved by `d` (warp-uniform); row0 = index of slot 0 for
     // the old base.  All lanes must call.
     __device__ __forceinline__ void advance(int d, double *s_row, int row0, double scale)
     {
+        if (TRACK && !__any_sync(0xffffffffu, dirty)) return;     // nothing to move
         if (d == 1) {
             flush_slot<0>(s_row, row0, scale);
 #pragma unroll

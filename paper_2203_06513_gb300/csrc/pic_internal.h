@@ -101,8 +101,9 @@ struct DiagArgs {
 };
 
 int launch_sweep1(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s);
-// the predicted start of subsystem I: delta^(0) (explicit when a.warm) and its current into jout
-int launch_predeposit(const Sweep1Args &a, double *jout, int grid, cudaStream_t s);
+// the predicted start of subsystem I: delta^(0) (explicit when a.warm) and its current
+// into a.j; the sweep's launch shape and shared memory
+int launch_predeposit(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s);
 size_t sweep1_smem(int M, int H, int fp32);
 int launch_sweep2(const Sweep2Args &a, int grid, int block, size_t smem, cudaStream_t s);
 size_t sweep2_smem(int M, int H, int fp32);

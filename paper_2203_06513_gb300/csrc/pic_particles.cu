@@ -305,7 +305,10 @@ __device__ __forceinline__ void deposit_cdiff(Win &win, const R *S0, const R *S1
     }
 }
 
-template <int K, typename R, int ACC>
+// PRE: the predicted start instead of a sweep -- the proposal delta^(0) (the
+// explicit predictor when A.warm, else the one already in delta) is written back
+// and its path current deposited into A.j; no gather walk, no momentum update.
+template <int K, typename R, int ACC, bool PRE = false>
 __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg, long long end,
                                              unsigned char *smem, unsigned long long &q)
 {
@@ -331,7 +334,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
     double *jout = A.j;
     bool warm = A.warm != 0;
     bool first = A.first != 0;
-    if (A.graph) {                          // replayed by a graph: buffers by sweep parity
+    if (!PRE && A.graph) {                  // replayed by a graph: buffers by sweep parity
         const int it = *reinterpret_cast<volatile const int *>(&A.ctrl->iter);
         jout = A.jpair[it & 1];
         warm = warm && it == 0;
@@ -431,7 +434,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
             // back (the float form recomputes: there the extra bytes cost more)
             R A0y = R(0), A0z = R(0), g0;
             bool cached = false;
-            if constexpr (!Real<R>::fp32) cached = !first && A.a0 != nullptr;
+            if constexpr (!Real<R>::fp32 && !PRE) cached = !first && A.a0 != nullptr;
             if (cached) {
                 start_cache_load<R>(A.a0, a, A0y, A0z, g0);
             } else {
@@ -443,81 +446,85 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
                     A0z += z * v0[r];
                 }
                 g0 = sqrt_(one + pn * pn + A0y * A0y + A0z * A0z);
-                if constexpr (!Real<R>::fp32)
+                if constexpr (!Real<R>::fp32 && !PRE)
                     if (A.a0) start_cache_store<R>(A.a0, a, A0y, A0z, g0);
             }
             R dold = warm ? fdiv_(tau * pn, g0) : s_d(b)[jl];
             if (!(fabs(dold) <= dlim)) { bad = true; dold = R(0); }
-
-            // Path integrals along x^n -> x^(k) (cell units), unnormalised:
-            //   EI = int ebar dt,  DI = int dA/dt dt / DK,
-            // the path means being EI/dold and DK DI/dold (the means at t0 when
-            // dold = 0).  A(x^(k)) = A(x^n) + DK DI exactly for the staged field (the
-            // staged differences of a are those of the staged coefficients), so the
-            // end point needs no basis evaluation of its own.
-            R EI = R(0), DIy = R(0), DIz = R(0);
-            const bool still = dold == R(0);
-            const int n1 = __reduce_max_sync(amask, path_pieces(t0, dold));
-            walk_uniform<K, R>(t0, dold, n1, [&](int c, R h, const R *m, int p) {
-                R e = R(0), gy = R(0), gz = R(0);
+            R dnew = R(0), pnew = R(0);
+            if constexpr (PRE) {
+                dnew = dold;
+            } else {
+                // Path integrals along x^n -> x^(k) (cell units), unnormalised:
+                //   EI = int ebar dt,  DI = int dA/dt dt / DK,
+                // the path means being EI/dold and DK DI/dold (the means at t0 when
+                // dold = 0).  A(x^(k)) = A(x^n) + DK DI exactly for the staged field (the
+                // staged differences of a are those of the staged coefficients), so the
+                // end point needs no basis evaluation of its own.
+                R EI = R(0), DIy = R(0), DIz = R(0);
+                const bool still = dold == R(0);
+                const int n1 = __reduce_max_sync(amask, path_pieces(t0, dold));
+                walk_uniform<K, R>(t0, dold, n1, [&](int c, R h, const R *m, int p) {
+                    R e = R(0), gy = R(0), gz = R(0);
 #pragma unroll
-                for (int r = 0; r < K; ++r) {
-                    R ev, y, z;
-                    F.eg(c0 + c - r + H, ev, y, z);
-                    e += m[r] * ev;
-                    gy += m[r] * y;
-                    gz += m[r] * z;
-                }
-                const R hw = still ? (p == 0 ? one : R(0)) : h;
-                EI += hw * e;
-                DIy += hw * gy;
-                DIz += hw * gz;
-            });
-            const R dn = still ? one : dold;
-            const R A1y = A0y + R(DK) * (still ? R(0) : DIy);
-            const R A1z = A0z + R(DK) * (still ? R(0) : DIz);
+                    for (int r = 0; r < K; ++r) {
+                        R ev, y, z;
+                        F.eg(c0 + c - r + H, ev, y, z);
+                        e += m[r] * ev;
+                        gy += m[r] * y;
+                        gz += m[r] * z;
+                    }
+                    const R hw = still ? (p == 0 ? one : R(0)) : h;
+                    EI += hw * e;
+                    DIy += hw * gy;
+                    DIz += hw * gz;
+                });
+                const R dn = still ? one : dold;
+                const R A1y = A0y + R(DK) * (still ? R(0) : DIy);
+                const R A1z = A0z + R(DK) * (still ? R(0) : DIz);
 
-            // p^(k+1) = p^n + tau (Ebar - (A1 + A0).D / (g1 + g0)) with Ebar = EI/dn,
-            // D = DK DI/dn, as one division
-            const R q1 = one + A1y * A1y + A1z * A1z;
-            const R g1 = sqrt_(q1 + pn * pn);
-            const R G = g1 + g0;
-            const R num = EI * G - R(DK) * ((A1y + A0y) * DIy + (A1z + A0z) * DIz);
-            R spin_term = R(0);
-            if constexpr (!Real<R>::fp32) {
-                if (A.hbar != 0.0) {
-                    // discrete gradient of the Zeeman energy: D2 = path mean of d^2A/dx^2
-                    // along x^n -> x^(k) (the exact difference quotient of dA/dx; its
-                    // limit at rest is the point value), from the second differences of
-                    // the staged coefficients and the means of the degree-(K-2) pieces
-                    const int id = A.P.id[a];
-                    double D2y = 0.0, D2z = 0.0;
-                    const double invd = still ? 0.0 : 1.0 / dold;
-                    walk_path<K - 1, double>(t0, dold, [&](int c, double h, const double *m2, bool single) {
-                        double gy = 0.0, gz = 0.0;
+                // p^(k+1) = p^n + tau (Ebar - (A1 + A0).D / (g1 + g0)) with Ebar = EI/dn,
+                // D = DK DI/dn, as one division
+                const R q1 = one + A1y * A1y + A1z * A1z;
+                const R g1 = sqrt_(q1 + pn * pn);
+                const R G = g1 + g0;
+                const R num = EI * G - R(DK) * ((A1y + A0y) * DIy + (A1z + A0z) * DIz);
+                R spin_term = R(0);
+                if constexpr (!Real<R>::fp32) {
+                    if (A.hbar != 0.0) {
+                        // discrete gradient of the Zeeman energy: D2 = path mean of d^2A/dx^2
+                        // along x^n -> x^(k) (the exact difference quotient of dA/dx; its
+                        // limit at rest is the point value), from the second differences of
+                        // the staged coefficients and the means of the degree-(K-2) pieces
+                        const int id = A.P.id[a];
+                        double D2y = 0.0, D2z = 0.0;
+                        const double invd = still ? 0.0 : 1.0 / dold;
+                        walk_path<K - 1, double>(t0, dold, [&](int c, double h, const double *m2, bool single) {
+                            double gy = 0.0, gz = 0.0;
 #pragma unroll
-                        for (int r = 0; r <= K - 2; ++r) {
-                            const int i = c0 + c - r + H;
-                            double y0, z0, y1, z1, y2, z2;
-                            F.aa(i, y0, z0);
-                            F.aa(i - 1, y1, z1);
-                            F.aa(i - 2, y2, z2);
-                            gy += m2[r] * ((y0 - y1) - (y1 - y2));
-                            gz += m2[r] * ((z0 - z1) - (z1 - z2));
-                        }
-                        const double f = single ? 1.0 : h * invd;
-                        D2y += f * gy;
-                        D2z += f * gz;
-                    });
-                    // staged coefficients are a / K!; D2 is per cell^2, the update per dx
-                    const double fac = (double)Fact<K>::v / A.dx;
-                    spin_term = A.hbar * fac * (A.sy[id] * D2z - A.sz[id] * D2y);
+                            for (int r = 0; r <= K - 2; ++r) {
+                                const int i = c0 + c - r + H;
+                                double y0, z0, y1, z1, y2, z2;
+                                F.aa(i, y0, z0);
+                                F.aa(i - 1, y1, z1);
+                                F.aa(i - 2, y2, z2);
+                                gy += m2[r] * ((y0 - y1) - (y1 - y2));
+                                gz += m2[r] * ((z0 - z1) - (z1 - z2));
+                            }
+                            const double f = single ? 1.0 : h * invd;
+                            D2y += f * gy;
+                            D2z += f * gz;
+                        });
+                        // staged coefficients are a / K!; D2 is per cell^2, the update per dx
+                        const double fac = (double)Fact<K>::v / A.dx;
+                        spin_term = A.hbar * fac * (A.sy[id] * D2z - A.sz[id] * D2y);
+                    }
                 }
+                pnew = pn + tau * (fdiv_(num, dn * G) - spin_term);
+                const R g2 = sqrt_(q1 + pnew * pnew);
+                dnew = fdiv_(tau * (pn + pnew), g1 + g2);
+                if (!(fabs(dnew) <= dlim)) { bad = true; dnew = R(0); }
             }
-            const R pnew = pn + tau * (fdiv_(num, dn * G) - spin_term);
-            const R g2 = sqrt_(q1 + pnew * pnew);
-            R dnew = fdiv_(tau * (pn + pnew), g1 + g2);
-            if (!(fabs(dnew) <= dlim)) { bad = true; dnew = R(0); }
 
             // Deposit j_i += w int_{x^n}^{x^(k+1)} Lambda^1_i = w dx (C_i(x^(k+1)) - C_i(x^n))
             // with C_i(x) = sum_{j >= i} Lambda^0_j(x): the derivative relation of Sec. 3.1
@@ -543,11 +550,15 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
                 }
                 deposit_cdiff<K>(win, S0, S1, n, c0, wb, H, s_acc, wdx);
             }
-            R inc = fabs(dnew - dold);
-            if (Real<R>::fp32) inc = __fdividef(inc, fmax(one, fabs(dnew)));   // convergence metric only
-            dmax = (inc > dmax || inc != inc) ? inc : dmax;
-            dp[a] = dnew;
-            pnp[a] = pnew;
+            if constexpr (PRE) {
+                dp[a] = dnew;
+            } else {
+                R inc = fabs(dnew - dold);
+                if (Real<R>::fp32) inc = __fdividef(inc, fmax(one, fabs(dnew)));   // convergence metric only
+                dmax = (inc > dmax || inc != inc) ? inc : dmax;
+                dp[a] = dnew;
+                pnp[a] = pnew;
+            }
         }
         tile_release<NS>(Bars, q0 + i);
         if (threadIdx.x == 0 && i + NS < ntile) issue(i + NS);
@@ -560,7 +571,7 @@ __device__ __forceinline__ bool sweep1_range(const Sweep1Args &A, long long beg,
         atomicOr(&A.ctrl->status, STATUS_TIMEOUT);
         tile_drain<NS>(Bars);
     }
-    block_max_to(&A.ctrl->dmax_bits, (double)dmax, s_red);
+    if (!PRE) block_max_to(&A.ctrl->dmax_bits, (double)dmax, s_red);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         const double val = s_acc[i];
         if (val != 0.0) atomicAdd(&jout[wrap_cell(i - H, A.M)], val);
@@ -589,98 +600,14 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_sweep1
 // the starting field sets how far the first sweep's kick is off.
 // ---------------------------------------------------------------------------
 template <int K, typename R, int ACC>
-__global__ void __launch_bounds__(256) k_predeposit(Sweep1Args A, double *jout)
+__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1) k_predeposit(Sweep1Args A)
 {
-    extern __shared__ __align__(16) double s_row[];
-    using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
-    const int H = A.H;
-    const int W = A.M + 2 * H;
-    R2 *s_a = reinterpret_cast<R2 *>(s_row + W);      // a / K! with the periodic halo
-    const double inv_fact_s = 1.0 / (double)Fact<K>::v;
-    for (int i = threadIdx.x; i < W; i += blockDim.x) {
-        s_row[i] = 0.0;
-        const int g = wrap_cell(i - H, A.M);
-        if constexpr (Real<R>::fp32) {
-            if (A.img.a) s_a[i] = A.img.a[g];
-            else s_a[i] = make_float2((float)(A.ay[g] * inv_fact_s), (float)(A.az[g] * inv_fact_s));
-        } else {
-            s_a[i] = make_double2(A.ay[g] * inv_fact_s, A.az[g] * inv_fact_s);
-        }
-    }
-    __syncthreads();
-    const R *tp = static_cast<const R *>(A.P.t);
-    const R *pp = static_cast<const R *>(A.P.p);
-    R *dp = static_cast<R *>(A.P.delta);
-    const R tau = (R)(A.dt / A.dx);
-    const double inv_fact = 1.0 / (double)Fact<K>::v;
-    const double wdx = A.w * A.dx * inv_fact;
-    const R dlim = (R)A.Dlim;
-    constexpr int KB = K + kCdMax;
-    DepWindow<R, KB + 3, KB, KB - 1, 0, 3, typename AccOf<R, ACC, K>::T> win;
-    win.clear();
-    int wb = INT_MIN;
-    bool bad = false;
+    extern __shared__ __align__(128) unsigned char smem[];
+    tile_bars_init(*reinterpret_cast<TileBars *>(smem));
     long long beg, end;
-    {
-        long long chunk = (A.np + gridDim.x - 1) / gridDim.x;
-        chunk = (chunk + 31) & ~31LL;
-        beg = (long long)blockIdx.x * chunk;
-        end = beg + chunk < A.np ? beg + chunk : A.np;
-    }
-    for (long long base = beg; base < end; base += blockDim.x) {
-        const long long a = base + threadIdx.x;
-        const bool act = a < end;
-        const int c0 = warp_unwrap_cell(act ? A.P.cell[a] : 0, act, A.M, H - A.Dlim);
-        const int lead = __reduce_min_sync(0xffffffffu, act ? c0 : INT_MAX);
-        if (lead == INT_MAX) break;
-        if (lead != wb) {
-            if (wb != INT_MIN) win.advance(lead - wb, s_row, wb - (KB - 1) + H, wdx);
-            wb = lead;
-        }
-        if (!act) continue;
-        const R t0 = tp[a];
-        R v0[K + 1];
-        bspline_scaled<K, R>(t0, v0);
-        R d;
-        if (A.warm) {
-            R A0y = R(0), A0z = R(0);
-#pragma unroll
-            for (int r = 0; r <= K; ++r) {
-                const R2 q = s_a[c0 - r + H];
-                A0y += q.x * v0[r];
-                A0z += q.y * v0[r];
-            }
-            const R pn = pp[a];
-            d = fdiv_(tau * pn, sqrt_(R(1) + pn * pn + A0y * A0y + A0z * A0z));
-            dp[a] = d;
-        } else {
-            d = dp[a];
-        }
-        if (!(fabs(d) <= dlim)) { bad = true; d = R(0); dp[a] = d; }
-        const R s1 = t0 + d;
-        const R f1 = floor_(s1);
-        int n = (int)f1;
-        R t1 = s1 - f1;
-        if (t1 >= R(1)) { t1 = R(0); n += 1; }
-        R v1[K + 1];
-        bspline_scaled<K, R>(t1, v1);
-        R S0[K], S1[K];
-        S0[0] = v0[0];
-        S1[0] = v1[0];
-#pragma unroll
-        for (int r = 1; r < K; ++r) {
-            S0[r] = S0[r - 1] + v0[r];
-            S1[r] = S1[r - 1] + v1[r];
-        }
-        deposit_cdiff<K>(win, S0, S1, n, c0, wb, H, s_row, wdx);
-    }
-    if (wb != INT_MIN) win.flush(s_row, wb - (KB - 1) + H, wdx);
-    if (bad) atomicOr(&A.ctrl->status, STATUS_NUMERIC);
-    __syncthreads();
-    for (int i = threadIdx.x; i < W; i += blockDim.x) {
-        const double v = s_row[i];
-        if (v != 0.0) atomicAdd(&jout[wrap_cell(i - H, A.M)], v);
-    }
+    block_chunk(A.np, beg, end);
+    unsigned long long q = 0;
+    sweep1_range<K, R, ACC, true>(A, beg, end, smem, q);
 }
 
 size_t sweep1_smem(int M, int H, int fp32)
@@ -863,7 +790,8 @@ __device__ __forceinline__ bool sweep2_range(const Sweep2Args &A, long long beg,
     const double w = A.w * inv_fact;
     const R one = R(1);
     // window: marker cells wb .. wb+2 (wb = the warp's lowest), V0 nodes wb-K .. wb+2
-    DepWindow<R, K + 3, K + 1, K, 0, 2, typename AccOf<R, ACC, K>::T> wy, wz;
+    DepWindow<R, K + 3, K + 1, K, 0, 2, typename AccOf<R, ACC, K>::T> wy;
+    DepWindow<R, K + 3, K + 1, K, 0, 2, typename AccOf<R, ACC, K>::T, true> wz;
     wy.clear();
     wz.clear();
     int wb = INT_MIN;
@@ -990,18 +918,11 @@ size_t sweep2_smem(int M, int H, int fp32)
     return 128 + stages + 2 * W * sizeof(double) + (fp32 ? 3 * W * sizeof(float2) : 2 * W * sizeof(double2));
 }
 
-size_t predeposit_smem(int M, int H, int fp32)
+int launch_predeposit(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s)
 {
-    const size_t W = (size_t)M + 2 * (size_t)H;
-    return W * sizeof(double) + W * (fp32 ? sizeof(float2) : sizeof(double2));
-}
-
-int launch_predeposit(const Sweep1Args &a, double *jout, int grid, cudaStream_t s)
-{
-    const size_t smem = predeposit_smem(a.M, a.H, a.fp32);
 #define LP(KK, RR, AA)                                                                              \
     if (a.K == KK && (a.fp32 != 0) == std::is_same<RR, float>::value && a.acc == AA) {              \
-        k_predeposit<KK, RR, AA><<<grid, 256, smem, s>>>(a, jout);                                  \
+        k_predeposit<KK, RR, AA><<<grid, block, smem, s>>>(a);                                      \
         return 0;                                                                                   \
     }
     PIC_FOR_SWEEP_VARIANTS(LP)
