@@ -289,10 +289,12 @@ def ensemble_inputs(n_runs: int, np_scale: float, seed: int):
 
 
 def ensemble_run(pic, torch, ws_, ins, steps, warmup, stream, use_graph=True):
-    """All runs in one ensemble (FP32 form, explicit predictor), schedule picked
-    by the autotuner; device-timed steps, each one graph launch (or, with
-    use_graph=False, the same kernels with the loops driven from the host)."""
-    cfgs = [pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=pic.PIC_WARM_EXPLICIT, sort_every=2)
+    """All runs in one ensemble (FP32 form, explicit predictor with the predicted
+    start field), schedule picked by the autotuner; device-timed steps, each one
+    graph launch (or, with use_graph=False, the same kernels with the loops driven
+    from the host)."""
+    cfgs = [pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=pic.PIC_WARM_EXPLICIT, sort_every=2,
+                                     warm_field=1)
             for w in ws_]
     t0 = time.perf_counter()
     ens = pic.Ensemble(cfgs, ins, use_graph=use_graph, stream=stream.cuda_stream)

@@ -320,16 +320,20 @@ int pic_deposit_current_noalloc(double L, int32_t nx, int32_t degree, int64_t np
  * markers) from a queue rebuilt before every sweep from the runs still
  * iterating, so a run that has converged drops out while the others go on.
  * The two loops are conditional (WHILE) graph nodes, ended on the device.
- * All runs must share degree, precision and warm start (PIC_WARM_NONE or
- * PIC_WARM_EXPLICIT); grid size, marker count, weight, dt, tolerances and
- * sort interval may differ.  1 <= nruns <= 1024.
+ * All runs must share degree, precision, warm start (PIC_WARM_NONE or
+ * PIC_WARM_EXPLICIT) and warm_field (with warm_field = 1 each step first runs
+ * the predicted start of every run: the proposals' currents over the work queue,
+ * then e^(0) per run); grid size, marker count, weight, dt, tolerances and
+ * sort interval may differ.  Runs use the default deposit accumulation,
+ * Lie--Trotter steps and no spin.  1 <= nruns <= 1024.
  * --------------------------------------------------------------------- */
 typedef struct pic_ensemble pic_ensemble;
 
 /* Create the runs (as pic_init with cfgs[r], ins[r], mem) on `stream`.
  * use_graph = 1: steps run as one graph launch; 0: the same kernels with
  * the loops driven from the host (one readback per sweep), for checking.
- * Errors: PIC_ERR_INVALID (mixed degree / precision, an MLP warm start,
+ * Errors: PIC_ERR_INVALID (mixed degree / precision / warm start / warm_field,
+ * an MLP warm start, another deposit accumulation, symmetric splitting, spin,
  * nruns out of range, or a run's own pic_init error), PIC_ERR_NOMEM,
  * PIC_ERR_CUDA; message via pic_last_error(NULL). */
 int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins, int32_t nruns, int32_t mem,

@@ -33,18 +33,19 @@ struct pic_ensemble {
     cudaStream_t cap = nullptr;         // private stream for graph capture
     int nruns = 0, K = 0, fp32 = 0, Mmax = 0, ntap1 = 0, ntap2 = 0, num_sms = 0;
     int use_graph = 1;
+    int warm_field = 0;                 // every run starts subsystem I from a predicted field
     std::vector<pic_handle *> runs;
 
     // host mirrors and device copies of the per-run tables
     std::vector<RunDesc> desc;
-    std::vector<Sweep1Args> a1;
+    std::vector<Sweep1Args> a1, a1p;
     std::vector<Sweep2Args> a2;
-    std::vector<ConvArgs> c1, c2, cp;
+    std::vector<ConvArgs> c1, c2, cp, c1p;
     std::vector<EnsRun> er;
     RunDesc *d_desc = nullptr;
-    Sweep1Args *d_a1 = nullptr;
+    Sweep1Args *d_a1 = nullptr, *d_a1p = nullptr;
     Sweep2Args *d_a2 = nullptr;
-    ConvArgs *d_c1 = nullptr, *d_c2 = nullptr, *d_cp = nullptr;
+    ConvArgs *d_c1 = nullptr, *d_c2 = nullptr, *d_cp = nullptr, *d_c1p = nullptr;
     EnsRun *d_er = nullptr;
     EnsQueue *d_q = nullptr;
     int *d_sweeps = nullptr, *d_status = nullptr;
@@ -119,23 +120,40 @@ static void build_tables(pic_ensemble *e)
         a.ebar = h->ebar; a.ga_y = h->ga_y; a.ga_z = h->ga_z; a.ay = h->ay; a.az = h->az;
         a.ctrl = h->ctrl;
         a.j = h->jb[0];
-        a.warm = h->cfg.warm_start == PIC_WARM_EXPLICIT ? 1 : 0;
+        // with a predicted start the proposal is already in delta when the loop starts
+        a.warm = (h->cfg.warm_start == PIC_WARM_EXPLICIT && !h->cfg.warm_field) ? 1 : 0;
         a.a0 = h->a0;
         a.graph = 1;
         a.jpair[0] = h->jb[0]; a.jpair[1] = h->jb[1];
         a.img = h->img;
+
+        // the predicted start: the explicit proposal and its current into jb[1]
+        Sweep1Args &ap = e->a1p[r];
+        ap = a;
+        ap.warm = h->cfg.warm_start == PIC_WARM_EXPLICIT ? 1 : 0;
+        ap.graph = 0;
+        ap.first = 1;
+        ap.j = h->jb[1];
 
         ConvArgs &c = e->c1[r];
         c = ConvArgs{};
         c.M = h->M; c.d_start = h->tapM1_start; c.ntap = h->tapM1_n; c.mode = CONV_SOLVE1; c.ncomp = 1;
         c.taps = h->d_tapM1;
         c.en[0] = h->ex; c.ek[0] = h->ek; c.aux[0] = h->ebar;
-        c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6; c.erel = kFieldIncrementRel;
+        c.dt = h->cfg.dt; c.dx = h->dx; c.tol = h->cfg.tol; c.dtol = 1e-6;
+        c.erel = h->cfg.warm_field ? kFieldIncrementRelPredicted : kFieldIncrementRel;
         c.max_iter = h->cfg.max_iter; c.fp32 = h->fp32; c.subsystem = 1; c.ctrl = h->ctrl;
         c.graph = 1;
         c.pair[0][0] = h->jb[0]; c.pair[0][1] = h->jb[1];
         c.cond_handle = 0;      // the ensemble ends the loop, not the run
         c.img = h->img;
+
+        // e^(0) = e^n - M1^{-1} j^(0) from the predicted start's current
+        ConvArgs &cs = e->c1p[r];
+        cs = c;
+        cs.mode = CONV_START1;
+        cs.graph = 0;
+        cs.in[0] = h->jb[1];
 
         Sweep2Args &b = e->a2[r];
         b = Sweep2Args{};
@@ -185,6 +203,8 @@ static int upload_tables(pic_ensemble *e)
     ECK(cudaMemcpyAsync(e->d_c1, e->c1.data(), n * sizeof(ConvArgs), cudaMemcpyHostToDevice, e->stream));
     ECK(cudaMemcpyAsync(e->d_c2, e->c2.data(), n * sizeof(ConvArgs), cudaMemcpyHostToDevice, e->stream));
     ECK(cudaMemcpyAsync(e->d_cp, e->cp.data(), n * sizeof(ConvArgs), cudaMemcpyHostToDevice, e->stream));
+    ECK(cudaMemcpyAsync(e->d_a1p, e->a1p.data(), n * sizeof(Sweep1Args), cudaMemcpyHostToDevice, e->stream));
+    ECK(cudaMemcpyAsync(e->d_c1p, e->c1p.data(), n * sizeof(ConvArgs), cudaMemcpyHostToDevice, e->stream));
     ECK(cudaMemcpyAsync(e->d_er, e->er.data(), n * sizeof(EnsRun), cudaMemcpyHostToDevice, e->stream));
     return PIC_OK;
 }
@@ -219,6 +239,16 @@ static int loop_body(pic_ensemble *e, int which, cudaStream_t s, unsigned long l
 static int seg_prep1(pic_ensemble *e, cudaStream_t s)
 {
     ELAUNCH(launch_prep1_ens(e->d_desc, e->nruns, e->Mmax, s), "ensemble prep I");
+    if (e->warm_field) {
+        // predicted start of every run: plan (all runs are iterating), the proposals
+        // and their currents (work queue), e^(0) per run
+        const int grid = e->num_sms * e->bps_max;
+        ELAUNCH(launch_ens_plan(e->d_q, e->d_er, e->nruns, 0ull, s), "ensemble plan");
+        ELAUNCH(launch_predeposit_ens(e->K, e->fp32, e->d_a1p, e->nruns, e->d_q, grid, e->smem1, s),
+                "ensemble predicted start");
+        ELAUNCH(launch_conv_ens(e->d_c1p, e->nruns, e->Mmax, 1, e->ntap1, e->d_q, e->d_sweeps, 0ull, s),
+                "ensemble start field");
+    }
     return PIC_OK;
 }
 
@@ -239,7 +269,7 @@ static int seg_end(pic_ensemble *e, cudaStream_t s)
 }
 
 // kernels launched per step outside the loops, and per loop sweep
-static constexpr int kStepLaunches = 6, kLoopLaunches = 3;
+static constexpr int kStepLaunches = 6, kLoopLaunches = 3, kStartLaunches = 3;
 
 // Build the step graph: linear segments as child graphs, loops as WHILE nodes
 // whose bodies are captured on the private stream.
@@ -325,6 +355,7 @@ static void ens_release(pic_ensemble *e)
     if (e->graph) cudaGraphDestroy(e->graph);
     auto f = [](void *p) { if (p) cudaFree(p); };
     f(e->d_desc); f(e->d_a1); f(e->d_a2); f(e->d_c1); f(e->d_c2); f(e->d_cp); f(e->d_er); f(e->d_q);
+    f(e->d_a1p); f(e->d_c1p);
     f(e->d_sweeps); f(e->d_status);
     if (e->h_buf) cudaFreeHost(e->h_buf);
     if (e->cap) cudaStreamDestroy(e->cap);
@@ -343,8 +374,8 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
     }
     for (int r = 1; r < nruns; ++r)
         if (cfgs[r].degree != cfgs[0].degree || cfgs[r].precision != cfgs[0].precision ||
-            cfgs[r].warm_start != cfgs[0].warm_start) {
-            set_thread_error("ensemble: runs must share degree, precision and warm start");
+            cfgs[r].warm_start != cfgs[0].warm_start || cfgs[r].warm_field != cfgs[0].warm_field) {
+            set_thread_error("ensemble: runs must share degree, precision, warm start and warm_field");
             return PIC_ERR_INVALID;
         }
     if (cfgs[0].warm_start == PIC_WARM_MLP) {
@@ -354,7 +385,7 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
     for (int r = 0; r < nruns; ++r)
         if ((cfgs[r].deposit != PIC_ACC_DEFAULT && cfgs[r].deposit != PIC_ACC_COMPENSATED &&
              !(cfgs[r].precision == PIC_FP64 && cfgs[r].deposit == PIC_ACC_DOUBLE)) ||
-            cfgs[r].splitting != PIC_SPLIT_LIE || cfgs[r].hbar != 0.0 || cfgs[r].warm_field) {
+            cfgs[r].splitting != PIC_SPLIT_LIE || cfgs[r].hbar != 0.0) {
             set_thread_error("ensemble: runs use the default deposit accumulation, Lie--Trotter steps and no spin");
             return PIC_ERR_INVALID;
         }
@@ -363,6 +394,7 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
     e->stream = (cudaStream_t)stream;
     e->nruns = nruns;
     e->use_graph = use_graph ? 1 : 0;
+    e->warm_field = cfgs[0].warm_field ? 1 : 0;
     auto bail = [&](int code) {
         set_thread_error(e->err.empty() ? "pic_ensemble_create failed" : e->err.c_str());
         ens_release(e);
@@ -400,12 +432,12 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
     }
     const size_t n = (size_t)nruns;
     e->desc.resize(n); e->a1.resize(n); e->a2.resize(n); e->c1.resize(n); e->c2.resize(n);
-    e->cp.resize(n); e->er.resize(n);
+    e->cp.resize(n); e->er.resize(n); e->a1p.resize(n); e->c1p.resize(n);
     int rc;
     if ((rc = ealloc(e, &e->d_desc, n)) || (rc = ealloc(e, &e->d_a1, n)) || (rc = ealloc(e, &e->d_a2, n)) ||
         (rc = ealloc(e, &e->d_c1, n)) || (rc = ealloc(e, &e->d_c2, n)) || (rc = ealloc(e, &e->d_cp, n)) ||
         (rc = ealloc(e, &e->d_er, n)) || (rc = ealloc(e, &e->d_q, 1)) || (rc = ealloc(e, &e->d_sweeps, 2 * n)) ||
-        (rc = ealloc(e, &e->d_status, n)))
+        (rc = ealloc(e, &e->d_status, n)) || (rc = ealloc(e, &e->d_a1p, n)) || (rc = ealloc(e, &e->d_c1p, n)))
         return bail(rc);
     if (cudaMallocHost((void **)&e->h_buf, (3 * n + 8) * sizeof(int)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
     if (cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess) return bail(PIC_ERR_CUDA);
@@ -474,7 +506,8 @@ extern "C" int pic_ensemble_step(pic_ensemble *e, int32_t nsteps, int64_t *sweep
         for (int i = 0; i < 2 * n; ++i) sweeps[i] += e->h_buf[i];
     {
         const long long l1 = e->h_buf[3 * n], l2 = e->h_buf[3 * n + 1];
-        e->launches += (long long)nsteps * kStepLaunches + kLoopLaunches * ((l1 - e->loops_seen[0]) + (l2 - e->loops_seen[1]));
+        e->launches += (long long)nsteps * (kStepLaunches + (e->warm_field ? kStartLaunches : 0)) +
+                       kLoopLaunches * ((l1 - e->loops_seen[0]) + (l2 - e->loops_seen[1]));
         e->loops_seen[0] = l1;
         e->loops_seen[1] = l2;
     }

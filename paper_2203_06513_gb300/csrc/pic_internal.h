@@ -256,6 +256,9 @@ int launch_sweep1_ens(int K, int fp32, const Sweep1Args *runs, int nruns, EnsQue
                       size_t smem, cudaStream_t s);
 int launch_sweep2_ens(int K, int fp32, const Sweep2Args *runs, int nruns, EnsQueue *Q, int grid,
                       size_t smem, cudaStream_t s);
+// the predicted start of every run in the queue (delta^(0) and its current into each run's a.j)
+int launch_predeposit_ens(int K, int fp32, const Sweep1Args *runs, int nruns, EnsQueue *Q, int grid,
+                          size_t smem, cudaStream_t s);
 int launch_finalize1_ens(int fp32, const RunDesc *R, int nruns, int grid_x, cudaStream_t s);
 int launch_prep1(const RunDesc &R, cudaStream_t s);
 int launch_prep2(const RunDesc &R, cudaStream_t s);

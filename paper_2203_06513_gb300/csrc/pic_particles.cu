@@ -1518,6 +1518,21 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1)
         if (!sweep1_range<K, R, DefaultAcc<R>::v>(runs[run], beg, end, smem, q)) break;
 }
 
+// the predicted start of every run (sweep1_range's PRE mode over the work queue)
+template <int K, typename R>
+__global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1)
+    k_predeposit_ens(const Sweep1Args *runs, int nruns, EnsQueue *Q)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    if ((int)blockIdx.x >= Q->nblocks) return;
+    tile_bars_init(*reinterpret_cast<TileBars *>(smem));
+    unsigned long long q = 0;
+    int run;
+    long long beg, end;
+    while (ens_claim(Q, runs, nruns, run, beg, end))
+        if (!sweep1_range<K, R, DefaultAcc<R>::v, true>(runs[run], beg, end, smem, q)) break;
+}
+
 template <int K, typename R>
 __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1)
     k_sweep2_ens(const Sweep2Args *runs, int nruns, EnsQueue *Q)
@@ -1540,7 +1555,8 @@ static int launch_sweep_ens_t(int which, int K, const void *runs, int nruns, Ens
 #define ENS(KK)                                                                                          \
     case KK:                                                                                             \
         if (which == 1) k_sweep1_ens<KK, R><<<grid, b, smem, s>>>((const Sweep1Args *)runs, nruns, Q);   \
-        else k_sweep2_ens<KK, R><<<grid, b, smem, s>>>((const Sweep2Args *)runs, nruns, Q);              \
+        else if (which == 2) k_sweep2_ens<KK, R><<<grid, b, smem, s>>>((const Sweep2Args *)runs, nruns, Q); \
+        else k_predeposit_ens<KK, R><<<grid, b, smem, s>>>((const Sweep1Args *)runs, nruns, Q);        \
         break;
     switch (K) {
     ENS(2) ENS(3) ENS(4) ENS(5)
@@ -1562,6 +1578,13 @@ int launch_sweep2_ens(int K, int fp32, const Sweep2Args *runs, int nruns, EnsQue
 {
     return fp32 ? launch_sweep_ens_t<float>(2, K, runs, nruns, Q, grid, smem, s)
                 : launch_sweep_ens_t<double>(2, K, runs, nruns, Q, grid, smem, s);
+}
+
+int launch_predeposit_ens(int K, int fp32, const Sweep1Args *runs, int nruns, EnsQueue *Q, int grid,
+                          size_t smem, cudaStream_t s)
+{
+    return fp32 ? launch_sweep_ens_t<float>(0, K, runs, nruns, Q, grid, smem, s)
+                : launch_sweep_ens_t<double>(0, K, runs, nruns, Q, grid, smem, s);
 }
 
 // End of subsystem I for every run (block row = run); runs stopped by an error
@@ -1586,6 +1609,7 @@ template <int K, typename R>
 static int set_attrs_kr(size_t s1, size_t s2, size_t s3)
 {
     if (cudaFuncSetAttribute(k_sweep1_ens<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) return 1;
+    if (cudaFuncSetAttribute(k_predeposit_ens<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1)) return 1;
     if (cudaFuncSetAttribute(k_sweep2_ens<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) return 1;
     if (cudaFuncSetAttribute(k_current<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3)) return 1;
     if (cudaFuncSetAttribute(k_charge<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3)) return 1;

@@ -79,13 +79,16 @@ def test_ensemble_fp64_against_oracle():
     ens.close()
 
 
-@pytest.mark.parametrize("precision", [pic.PIC_FP64, pic.PIC_FP32])
-def test_ensemble_matches_single_runs(precision):
+@pytest.mark.parametrize("precision,warm_field", [(pic.PIC_FP64, 0), (pic.PIC_FP32, 0), (pic.PIC_FP64, 1),
+                                                   (pic.PIC_FP32, 1)])
+def test_ensemble_matches_single_runs(precision, warm_field):
     """Every run of a 6-run ensemble equals the same run stepped alone, sweep
-    counts included (FP64 to rounding order; FP32 to a few float ulps)."""
+    counts included (FP64 to rounding order; FP32 to a few float ulps), with and
+    without the predicted start of subsystem I."""
     ws = members(6, base_np=2000)
     ins = inputs_of(ws)
-    cfgs = [pic.Config.from_workload(w, precision=precision, warm_start=pic.PIC_WARM_EXPLICIT, sort_every=2)
+    cfgs = [pic.Config.from_workload(w, precision=precision, warm_start=pic.PIC_WARM_EXPLICIT, sort_every=2,
+                                     warm_field=warm_field)
             for w in ws]
     ens = pic.Ensemble(cfgs, ins)
     steps = 4
@@ -97,11 +100,11 @@ def test_ensemble_matches_single_runs(precision):
         g = pic.Pic(cfgs[r], x, p, ay, az, ey, ez)
         i1, i2 = g.step(steps)
         compare(ens.run(r).state_numpy(), g.state_numpy(), w.L, tol)
-        # a decision right at the tolerance may flip with the order of atomics.  In
-        # float, runs this small stop at the noise floor of the increments, where
-        # the stagnation test waits for an increment that no longer shrinks, and
-        # which sweep shows one depends on the rounding: up to two sweeps a step.
-        slack = 1 if precision == pic.PIC_FP64 else 2 * steps
+        # a decision right at the tolerance may flip with the order of atomics, in
+        # float more often (increments near the noise floor): measured at most one
+        # sweep apart over the four steps
+        slack = 1 if precision == pic.PIC_FP64 else 2
+        print(f"run {r}: ensemble sweeps {tuple(sw[r])}, alone ({i1}, {i2})")
         assert abs(sw[r, 0] - i1) <= slack and abs(sw[r, 1] - i2) <= slack, (r, sw[r], i1, i2)
         g.close()
     ens.close()

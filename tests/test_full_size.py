@@ -171,11 +171,12 @@ def test_c2_full_size_fp32_learned(pool):
         d = np.load(WEIGHTS)
         mlp = pic.Mlp(d["norm"], d["params"])
         warm = pic.PIC_WARM_MLP
-    cfg = pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=warm, sort_every=2)
+    cfg = pic.Config.from_workload(w, precision=pic.PIC_FP32, warm_start=warm, sort_every=2, warm_field=1)
     st0, st1, st2, _ = run_one_step(cfg, (x, p, ay, az, ey, ez), mlp)
     del x, p
-    # FP32 stopping rule: position estimate <= 1e-6 cells relative; float state
-    out = check_step(pool, w, st0, st1, st2, tol_sweep=1e-5, tol_energy=1e-10, tol_gauss=1e-6, tol_ii=1e-5)
+    # FP32 stopping rule: position estimate <= 1e-6 cells relative; float state.
+    # Measured: sweep 2.4e-7, Gauss 1.6e-9 max|rho|, subsystem II 1.7e-9, energy 2e-14.
+    out = check_step(pool, w, st0, st1, st2, tol_sweep=1e-6, tol_energy=1e-12, tol_gauss=5e-9, tol_ii=5e-9)
     print("C2 FP32 full size:", out)
 
 
@@ -188,8 +189,9 @@ def test_c3_full_size_fp64_and_fp32(pool):
     arrays = (x, p, ay, az, ey, ez)
     res = {}
     fields = {}
+    # FP32 measured: sweep 4.8e-7, energy 1.6e-12, Gauss 1.4e-9 max|rho|, subsystem II 2.9e-9
     for prec, name, tols in ((pic.PIC_FP64, "fp64", (1e-10, 1e-12, 1e-12, 1e-9)),
-                             (pic.PIC_FP32, "fp32", (1e-5, 1e-10, 1e-6, 1e-5))):
+                             (pic.PIC_FP32, "fp32", (2e-6, 5e-12, 5e-9, 1e-8))):
         cfg = pic.Config.from_workload(w, precision=prec, warm_start=pic.PIC_WARM_EXPLICIT, sort_every=2)
         st0, st1, st2, _ = run_one_step(cfg, arrays)
         res[name] = check_step(pool, w, st0, st1, st2, *tols)
@@ -198,4 +200,4 @@ def test_c3_full_size_fp64_and_fp32(pool):
     diff = max(float(np.max(np.abs(fields["fp32"][k] - fields["fp64"][k])) / np.max(np.abs(fields["fp64"][k])))
                for k in ("ex", "ey", "ay"))
     print("C3 full size:", res, "FP32 vs FP64 fields, relative:", diff)
-    assert diff <= 1e-5
+    assert diff <= 3e-7          # measured 9.9e-8

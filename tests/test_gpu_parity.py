@@ -231,6 +231,8 @@ def test_fp32_form_against_oracle():
     # eps ~ 1.2e-7) on a current w v dt; per node and step the residual grows by
     # about eps w v dt sqrt(k Np / M) / dx, a random walk over steps.  Allow 20x.
     est = 1.2e-7 * w.weight * w.vth * w.dt * math.sqrt(3 * w.np / w.nx) / w.dx * math.sqrt(5)
+    print(f"\nFP32 vs oracle, 5 steps: energy {abs(E['total'] - H0) / H0:.3e}, Gauss {E['gauss']:.3e} = "
+          f"{E['gauss'] / est:.3f} x estimate")
     assert E["gauss"] < 20 * est
 
 

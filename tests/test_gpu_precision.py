@@ -63,11 +63,11 @@ def test_c3_precision_sweep():
     print("\nC3 grid, 1e6 markers, 1000 steps: form | max rel energy err | max Gauss | field err vs FP64 | p err")
     for r in rows:
         print(f"{r[0]} | {r[1]:.2e} | {r[2]:.2e} | {r[3]:.2e} | {r[4]:.2e}")
-    assert e64 < 1e-11 and g64 < 1e-13
-    # the FP32 runs follow the FP64 trajectory to about 1e-4..1e-3 after 1000 steps
-    # (the plasma amplifies rounding differences); their invariants stay near float
-    # resolution
+    assert e64 < 1e-12 and g64 < 3e-15          # measured 3.0e-13, 8.0e-16
+    # the FP32 runs follow the FP64 trajectory to about 3e-4 after 1000 steps (the
+    # plasma amplifies rounding differences); their invariants stay near float
+    # resolution: measured energy 1.2e-10..1.8e-10, fields 3.2e-4..3.4e-4
     for name, e, gs, fe, pe in rows[1:]:
-        assert e < 1e-8, name
-        assert fe < 3e-3, name
+        assert e < 6e-10, name
+        assert fe < 1e-3, name
     assert rows[2][2] < 0.3 * rows[1][2]        # the compensated pair's Gauss residual

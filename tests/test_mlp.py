@@ -84,7 +84,8 @@ def test_gpu_tensor_core_inference_matches_reference():
     y = Y.cpu().numpy()
     # bf16 operands (8-bit mantissa) through four layers: a few 1e-3 of the output scale
     scale = np.max(np.abs(ref))
-    assert np.max(np.abs(y - ref)) <= 3e-2 * scale
+    print(f"\nbf16 tensor-core inference: max error {np.max(np.abs(y - ref)) / scale:.3e} of the output scale")
+    assert np.max(np.abs(y - ref)) <= 2e-2 * scale      # measured 6.3e-3
     assert np.corrcoef(y[:, 0], ref[:, 0])[0, 1] > 0.999
 
 
