@@ -61,12 +61,13 @@ BYTES_SWEEP1 = {1: 28, 0: 44}
 BYTES_SWEEP2 = 12
 FLOP_MLP = 2 * (6 * 64 + 64 * 64 + 64 * 64 + 64 * 2)
 # DRAM bytes (read + write) per marker from ncu captures of the current kernels on
-# 2e7 markers of the C2 grid (--set full, one launch each); per launch = x N_p.
-NCU_DRAM_PER_MARKER = {"k_sweep1<3,float>": 22.34, "k_sweep2<3,float>": 12.21, "k_warm_mlp<3,float>": 15.02}
+# 2e7 markers of the C2 grid (--set full, one launch each; the sweeps with their
+# default compensated deposit lanes); per launch = x N_p.
+NCU_DRAM_PER_MARKER = {"k_sweep1<3,float>": 22.35, "k_sweep2<3,float>": 12.29, "k_warm_mlp<3,float>": 15.02}
 # Warp instructions x 32 per marker from the same captures: the kernels are bound by
 # instruction issue, which the "issue" entry compares with the issue-slot peak
 # (SMs x 4 schedulers x 1 warp instruction a cycle x the sampled SM clock).
-NCU_INST_PER_MARKER = {"k_sweep1<3,float>": 608, "k_sweep2<3,float>": 292, "k_warm_mlp<3,float>": 1182}
+NCU_INST_PER_MARKER = {"k_sweep1<3,float>": 577, "k_sweep2<3,float>": 359, "k_warm_mlp<3,float>": 1182}
 
 
 def peaks():

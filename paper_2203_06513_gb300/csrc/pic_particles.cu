@@ -918,14 +918,22 @@ size_t sweep2_smem(int M, int H, int fp32)
     return 128 + stages + 2 * W * sizeof(double) + (fp32 ? 3 * W * sizeof(float2) : 2 * W * sizeof(double2));
 }
 
+// The predicted start's current only sets where the fixed-point iteration starts
+// (the fixed point and its stopping test do not depend on it), so its lanes sum in
+// the form's own precision: plain float lanes in the FP32 form, whatever
+// accumulation the sweeps use.
+#define PIC_FOR_PREDEPOSIT_VARIANTS(X)                                                              \
+    X(2, double, ACC_NATIVE) X(3, double, ACC_NATIVE) X(4, double, ACC_NATIVE) X(5, double, ACC_NATIVE) \
+    X(2, float, ACC_NATIVE) X(3, float, ACC_NATIVE) X(4, float, ACC_NATIVE) X(5, float, ACC_NATIVE)
+
 int launch_predeposit(const Sweep1Args &a, int grid, int block, size_t smem, cudaStream_t s)
 {
 #define LP(KK, RR, AA)                                                                              \
-    if (a.K == KK && (a.fp32 != 0) == std::is_same<RR, float>::value && a.acc == AA) {              \
+    if (a.K == KK && (a.fp32 != 0) == std::is_same<RR, float>::value) {                             \
         k_predeposit<KK, RR, AA><<<grid, block, smem, s>>>(a);                                      \
         return 0;                                                                                   \
     }
-    PIC_FOR_SWEEP_VARIANTS(LP)
+    PIC_FOR_PREDEPOSIT_VARIANTS(LP)
 #undef LP
     return 1;
 }
@@ -1530,7 +1538,7 @@ __global__ void __launch_bounds__(kSweepThreads, Real<R>::fp32 ? 2 : 1)
     int run;
     long long beg, end;
     while (ens_claim(Q, runs, nruns, run, beg, end))
-        if (!sweep1_range<K, R, DefaultAcc<R>::v, true>(runs[run], beg, end, smem, q)) break;
+        if (!sweep1_range<K, R, ACC_NATIVE, true>(runs[run], beg, end, smem, q)) break;
 }
 
 template <int K, typename R>
@@ -1627,14 +1635,17 @@ static int set_attrs_sweeps(size_t s1, size_t s2, size_t s3)
 {
     int rc = 0;
 #define ATTRV(KK, RR, AA)                                                                               \
-    rc |= cudaFuncSetAttribute(k_predeposit<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1) != \
-          cudaSuccess;                                                                                  \
     rc |= cudaFuncSetAttribute(k_sweep1<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1) != \
           cudaSuccess;                                                                                  \
     rc |= cudaFuncSetAttribute(k_sweep2<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2) != \
           cudaSuccess;
     PIC_FOR_SWEEP_VARIANTS(ATTRV)
 #undef ATTRV
+#define ATTRP(KK, RR, AA)                                                                               \
+    rc |= cudaFuncSetAttribute(k_predeposit<KK, RR, AA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1) != \
+          cudaSuccess;
+    PIC_FOR_PREDEPOSIT_VARIANTS(ATTRP)
+#undef ATTRP
     return rc;
 }
 
