@@ -233,8 +233,8 @@ static int sort_markers(pic_handle *h)
     PartPtrs dst = h->P[1 - h->cur];
     dst.delta = h->delta;
     dst.pnew = h->pnew;
-    if (launch_sort(h->fp32, h->np, h->M, h->cfg.dt / h->dx, src, dst, h->counts, particle_grid(h), 256,
-                    h->stream))
+    if (launch_sort(h->fp32, h->np, h->M, h->cfg.dt / h->dx, bins_per_cell(h->np, h->M), src, dst, h->counts,
+                    particle_grid(h), 256, h->stream))
         return fail(h, PIC_ERR_CUDA, "sort launch failed");
     CKL_N("launch_sort");
     h->cur = 1 - h->cur;
@@ -441,7 +441,7 @@ extern "C" int pic_init_split(const pic_config *cfg, const pic_arrays *in, int32
         h->img.inv_fact = 1.0 / fact;
         h->img.escale = dx / (double)mean_scale(c.degree - 1);
     }
-    if ((rc = dalloc(h, &h->counts, 2 * M * kVelBins))) return bail(rc);
+    if ((rc = dalloc(h, &h->counts, 2 * M * kVelBinsBase * bins_per_cell((long long)np, (int)M)))) return bail(rc);
     if ((rc = dalloc(h, &h->ctrl, 1))) return bail(rc);
     if (cudaMallocHost((void **)&h->h_flag, sizeof(int)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
     if (cudaMallocHost((void **)&h->h_ctrl, sizeof(DevCtrl)) != cudaSuccess) return bail(PIC_ERR_NOMEM);

@@ -1365,20 +1365,20 @@ int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Counting sort of the markers by key = cell * kVelBins + velocity bin, the
-// bin being the expected displacement tau p in whole cells (clamped), so that a
-// warp's markers share cells and piece counts.  Runs between steps; delta and
+// Counting sort of the markers by key = cell * nbins + velocity bin, the bin being
+// the expected displacement tau p in units of 1/per cell (nbins = 16 per, clamped),
+// so that a warp's markers share cells and piece counts.  Runs between steps; delta and
 // p_new are not carried (each step's first sweep or warm start writes them
 // before they are read, and delta is all zero where the iteration starts from
 // it).  Atomics are aggregated per warp over equal keys.
 // counts: 2 * nkeys int32 (histogram, then cursors).
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ int sort_key(int c, R p, float tau)
+__device__ __forceinline__ int sort_key(int c, R p, float taup, int nbins)
 {
-    int b = (int)floorf((float)p * tau) + kVelBins / 2;
-    b = b < 0 ? 0 : (b >= kVelBins ? kVelBins - 1 : b);
-    return c * kVelBins + b;
+    int b = (int)floorf((float)p * taup) + nbins / 2;
+    b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+    return c * nbins + b;
 }
 
 // Both passes give each block a contiguous chunk of the markers.  The markers are
@@ -1386,7 +1386,7 @@ __device__ __forceinline__ int sort_key(int c, R p, float tau)
 // same time then touch different keys' counters; in a grid-stride order every
 // block would work on the same few cells at once and serialise on their counters.
 template <typename R>
-__global__ void __launch_bounds__(256) k_hist(long long np, float tau, PartPtrs S, int32_t *counts)
+__global__ void __launch_bounds__(256) k_hist(long long np, float tau, int nbins, PartPtrs S, int32_t *counts)
 {
     const R *ps = static_cast<const R *>(S.p);
     long long beg, end;
@@ -1395,7 +1395,7 @@ __global__ void __launch_bounds__(256) k_hist(long long np, float tau, PartPtrs 
     for (long long base = beg; base < end; base += blockDim.x) {
         const long long a = base + threadIdx.x;
         const bool act = a < end;
-        const int key = act ? sort_key(S.cell[a], ps[a], tau) : -1;
+        const int key = act ? sort_key(S.cell[a], ps[a], tau, nbins) : -1;
         const unsigned grp = __match_any_sync(0xffffffffu, key);
         if (act && lane == __ffs(grp) - 1) atomicAdd(&counts[key], __popc(grp));
     }
@@ -1422,7 +1422,7 @@ __global__ void __launch_bounds__(1024) k_scan(int nkeys, int32_t *counts)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_scatter(long long np, float tau, PartPtrs S, PartPtrs D,
+__global__ void __launch_bounds__(256) k_scatter(long long np, float tau, int nbins, PartPtrs S, PartPtrs D,
                                                  int32_t *cursor)
 {
     const R *ts = static_cast<const R *>(S.t);
@@ -1445,7 +1445,7 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, float tau, PartPt
             const bool act = a < end;
             c[u] = act ? S.cell[a] : 0;
             p[u] = act ? ps[a] : R(0);
-            key[u] = act ? sort_key(c[u], p[u], tau) : -1;
+            key[u] = act ? sort_key(c[u], p[u], tau, nbins) : -1;
         }
 #pragma unroll
         for (int u = 0; u < kSortU; ++u) {
@@ -1467,16 +1467,18 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, float tau, PartPt
     }
 }
 
-int launch_sort(int fp32, long long np, int M, double tau, PartPtrs src, PartPtrs dst,
+int launch_sort(int fp32, long long np, int M, double tau, int per, PartPtrs src, PartPtrs dst,
                 int32_t *counts, int grid, int block, cudaStream_t s)
 {
-    const int nkeys = M * kVelBins;
+    const int nbins = kVelBinsBase * per;
+    const int nkeys = M * nbins;
+    const float taup = (float)(tau * per);
     if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * (size_t)nkeys, s) != cudaSuccess) return 1;
-    if (fp32) k_hist<float><<<grid, block, 0, s>>>(np, (float)tau, src, counts);
-    else k_hist<double><<<grid, block, 0, s>>>(np, (float)tau, src, counts);
+    if (fp32) k_hist<float><<<grid, block, 0, s>>>(np, taup, nbins, src, counts);
+    else k_hist<double><<<grid, block, 0, s>>>(np, taup, nbins, src, counts);
     k_scan<<<1, 1024, 0, s>>>(nkeys, counts);
-    if (fp32) k_scatter<float><<<grid, block, 0, s>>>(np, (float)tau, src, dst, counts + nkeys);
-    else k_scatter<double><<<grid, block, 0, s>>>(np, (float)tau, src, dst, counts + nkeys);
+    if (fp32) k_scatter<float><<<grid, block, 0, s>>>(np, taup, nbins, src, dst, counts + nkeys);
+    else k_scatter<double><<<grid, block, 0, s>>>(np, taup, nbins, src, dst, counts + nkeys);
     return 0;
 }
 
