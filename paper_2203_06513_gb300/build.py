@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpic.so")
-SOURCES = ["pic_particles.cu", "pic_grid.cu", "pic_api.cu", "pic_noalloc.cu", "pic_mlp.cu", "pic_ensemble.cu"]
+SOURCES = ["pic_particles.cu", "pic_grid.cu", "pic_api.cu", "pic_noalloc.cu", "pic_mlp.cu", "pic_ensemble.cu", "pic2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,691 @@
+// pic2d.cu -- subsystem I of the two-dimensional scheme (Sec. 4.3) on the GPU, FP64.
+//
+// Spaces (Sec. 3.2): tensor-product B-splines on a uniform periodic M1 x M2 grid,
+// node i = i1 * M2 + i2; A_z on N^k x N^k, the 1-form e_xy as e_x on N^{k-1} x N^k
+// and e_y on N^k x N^{k-1}.  One thread per marker and sweep:
+//   * the path means of both V1 components along x^n -> x^(k) (the straight path
+//     split at every knot crossing of either coordinate, k-point Gauss--Legendre on
+//     each piece: the integrand is a polynomial of degree 2k - 1 there), gathered
+//     against e_bar;
+//   * the coordinate-increment difference quotients D of A_z as exact path means of
+//     dA/dx1 along x1 (at x2^(k)) and of dA/dx2 along x2 (at x1^n);
+//   * the momentum and position updates of the discrete-gradient scheme;
+//   * the current of the new path x^n -> x^(k+1), accumulated per block in shared
+//     memory over the whole grid and added to the global deposit once per node.
+// The grid side applies M1^{-1} = diag(M1_x^{-1} (x) M0_y^{-1}, M0_x^{-1} (x) M1_y^{-1})
+// as two circulant passes with the exact inverse rows of the 1D mass matrices.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pic2d.h"
+#include "pic_internal.h"
+
+namespace pic {
+namespace {
+
+constexpr int kMax2DNodes = 4096;     // M1 * M2: the block's shared-memory deposit rows
+constexpr int kMaxCross = 16;         // knot crossings per coordinate and path
+
+struct Args2D {
+    int M1, M2;
+    long long np;
+    double dx1, dx2, dt, w;
+    const double *x;        // np x 2, in the box
+    const double *pn;       // np x 2
+    double *d;              // np x 2 displacement iterate (length units), in/out
+    double *pk;             // np x 2 momentum iterate, in/out
+    const double *ebx, *eby;
+    const double *az, *gax, *gay;
+    double *jx, *jy;        // deposits of this sweep (zeroed before)
+    unsigned long long *dmax_bits, *pmax_bits;
+    int *status;
+    double glx[5], glw[5];  // K-point Gauss--Legendre on [-1, 1]
+};
+
+__device__ __forceinline__ int wrapi(int i, int M)
+{
+    int r = i % M;
+    return r < 0 ? r + M : r;
+}
+
+// [N^D(r + t)], r = 0..D: the normalised B-spline values of one cell
+template <int D>
+__device__ __forceinline__ void bsp(double t, double *v)
+{
+    bspline_scaled<D, double>(t, v);
+    const double s = 1.0 / (double)Fact<D>::v;
+#pragma unroll
+    for (int r = 0; r <= D; ++r) v[r] *= s;
+}
+
+// Pieces of the path u0 -> u0 + du (cell units, both coordinates) between knot
+// crossings: f(sa, sb) for consecutive parameter values 0 = s_0 < ... = 1.
+// Returns false when a coordinate crosses more than kMaxCross knots.
+template <class F>
+__device__ __forceinline__ bool walk2(double u0x, double u0y, double dux, double duy, F &&f)
+{
+    const double ex = u0x + dux, ey = u0y + duy;
+    // next knot index and its step in each coordinate
+    int nx, ny, cx = 0, cy = 0;
+    const int tx = dux > 0.0 ? (int)ceil(ex) - 1 - (int)floor(u0x) : (dux < 0.0 ? (int)ceil(u0x) - 1 - (int)floor(ex) : 0);
+    const int ty = duy > 0.0 ? (int)ceil(ey) - 1 - (int)floor(u0y) : (duy < 0.0 ? (int)ceil(u0y) - 1 - (int)floor(ey) : 0);
+    if (tx > kMaxCross || ty > kMaxCross) return false;
+    nx = dux > 0.0 ? (int)floor(u0x) + 1 : (int)ceil(u0x) - 1;
+    ny = duy > 0.0 ? (int)floor(u0y) + 1 : (int)ceil(u0y) - 1;
+    const int sx = dux > 0.0 ? 1 : -1, sy = duy > 0.0 ? 1 : -1;
+    double sa = 0.0;
+    for (int guard = 0; guard < 2 * kMaxCross + 2; ++guard) {
+        const double bx = cx < tx ? ((double)nx - u0x) / dux : 2.0;
+        const double by = cy < ty ? ((double)ny - u0y) / duy : 2.0;
+        double sb = fmin(fmin(bx, by), 1.0);
+        if (sb > sa) f(sa, sb);
+        if (sb >= 1.0) return true;
+        if (bx <= sb) { nx += sx; ++cx; }
+        if (by <= sb) { ny += sy; ++cy; }
+        sa = sb;
+    }
+    return true;
+}
+
+// 1D pieces of u0 -> u0 + du
+template <class F>
+__device__ __forceinline__ bool walk1(double u0, double du, F &&f)
+{
+    return walk2(u0, 0.0, du, 0.0, [&](double sa, double sb) { f(sa, sb); });
+}
+
+template <int K>
+__device__ __forceinline__ double value0(const double *a, int M1, int M2, double u1, double u2)
+{
+    const double c1 = floor(u1), c2 = floor(u2);
+    double v1[K + 1], v2[K + 1];
+    bsp<K>(u1 - c1, v1);
+    bsp<K>(u2 - c2, v2);
+    double s = 0.0;
+#pragma unroll
+    for (int r1 = 0; r1 <= K; ++r1) {
+        const int i1 = wrapi((int)c1 - r1, M1);
+#pragma unroll
+        for (int r2 = 0; r2 <= K; ++r2) s += a[i1 * M2 + wrapi((int)c2 - r2, M2)] * v1[r1] * v2[r2];
+    }
+    return s;
+}
+
+// visit(i_x, v_x, i_y, v_y) per quadrature node and basis pair: the x-component
+// value N^{K-1} x N^K at node i_x and the y-component value N^K x N^{K-1} at i_y,
+// already multiplied by the quadrature weight (path means over s in [0, 1])
+template <int K, class V>
+__device__ __forceinline__ bool path_means(const Args2D &A, double u0x, double u0y, double dux, double duy,
+                                           V &&visit)
+{
+    return walk2(u0x, u0y, dux, duy, [&](double sa, double sb) {
+        const double sm = 0.5 * (sa + sb), hs = 0.5 * (sb - sa);
+        const double c1 = floor(u0x + sm * dux), c2 = floor(u0y + sm * duy);
+#pragma unroll
+        for (int g = 0; g < K; ++g) {
+            const double s = sm + hs * A.glx[g];
+            const double wq = hs * A.glw[g];
+            const double t1 = u0x + s * dux - c1, t2 = u0y + s * duy - c2;
+            double b1k[K + 1], b1m[K], b2k[K + 1], b2m[K];
+            bsp<K>(t1, b1k);
+            bsp<K - 1>(t1, b1m);
+            bsp<K>(t2, b2k);
+            bsp<K - 1>(t2, b2m);
+#pragma unroll
+            for (int r1 = 0; r1 <= K; ++r1) {
+                const int i1 = wrapi((int)c1 - r1, A.M1);
+#pragma unroll
+                for (int r2 = 0; r2 <= K; ++r2) {
+                    const int i = i1 * A.M2 + wrapi((int)c2 - r2, A.M2);
+                    const double vx = (r1 < K) ? wq * b1m[r1 < K ? r1 : 0] * b2k[r2] : 0.0;
+                    const double vy = (r2 < K) ? wq * b1k[r1] * b2m[r2 < K ? r2 : 0] : 0.0;
+                    visit(i, vx, vy);
+                }
+            }
+        }
+    });
+}
+
+// mean of dA/dx1 along x1 from u0 to u0 + du at fixed x2 (cell coordinate u2):
+// sum (G_x a)_i (mean of N^{K-1}(x1 - i1)) N^K(x2 - i2); and the same along x2
+template <int K>
+__device__ __forceinline__ double dA_mean(const Args2D &A, int axis, double u0, double du, double uo)
+{
+    const double co = floor(uo);
+    double vo[K + 1];
+    bsp<K>(uo - co, vo);
+    const double *ga = axis == 0 ? A.gax : A.gay;
+    double s = 0.0;
+    walk1(u0, du, [&](double sa, double sb) {
+        const double sm = 0.5 * (sa + sb), hs = 0.5 * (sb - sa);
+        const double c = floor(u0 + sm * du);
+#pragma unroll
+        for (int g = 0; g < K; ++g) {
+            const double t = u0 + (sm + hs * A.glx[g]) * du - c;
+            double bm[K];
+            bsp<K - 1>(t, bm);
+            const double wq = hs * A.glw[g];
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                double acc = 0.0;
+#pragma unroll
+                for (int ro = 0; ro <= K; ++ro) {
+                    const int i = axis == 0 ? wrapi((int)c - r, A.M1) * A.M2 + wrapi((int)co - ro, A.M2)
+                                            : wrapi((int)co - ro, A.M1) * A.M2 + wrapi((int)c - r, A.M2);
+                    acc += ga[i] * vo[ro];
+                }
+                s += wq * bm[r] * acc;
+            }
+        }
+    });
+    return s;
+}
+
+__device__ __forceinline__ void max_bits(unsigned long long *dst, double v)
+{
+    // non-negative doubles order like their bit patterns; NaN maps to the largest
+    const unsigned long long b = (v == v) ? (unsigned long long)__double_as_longlong(v) : 0x7ff8000000000000ull;
+    atomicMax(dst, b);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k2_sweep(Args2D A)
+{
+    extern __shared__ double s_j[];     // 2 * M1 * M2: x then y
+    const int N = A.M1 * A.M2;
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) s_j[i] = 0.0;
+    __syncthreads();
+    double dm = 0.0, pm = 0.0;
+    bool bad = false;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < A.np;
+         a += (long long)gridDim.x * blockDim.x) {
+        const double u0x = A.x[2 * a] / A.dx1, u0y = A.x[2 * a + 1] / A.dx2;
+        const double d0 = A.d[2 * a], d1 = A.d[2 * a + 1];
+        const double p0 = A.pn[2 * a], p1 = A.pn[2 * a + 1];
+        const double dux = d0 / A.dx1, duy = d1 / A.dx2;
+        const double A0 = value0<K>(A.az, A.M1, A.M2, u0x, u0y);
+        const double A1 = value0<K>(A.az, A.M1, A.M2, u0x + dux, u0y + duy);
+        double Ex = 0.0, Ey = 0.0;
+        bool ok = path_means<K>(A, u0x, u0y, dux, duy, [&](int i, double vx, double vy) {
+            Ex += vx * A.ebx[i];
+            Ey += vy * A.eby[i];
+        });
+        const double D1 = dA_mean<K>(A, 0, u0x, dux, u0y + duy);
+        const double D2 = dA_mean<K>(A, 1, u0y, duy, u0x);
+        const double pp = p0 * p0 + p1 * p1;
+        const double g0 = sqrt(1.0 + pp + A0 * A0);
+        const double g1 = sqrt(1.0 + pp + A1 * A1);
+        const double f = A.dt * (A1 + A0) / (g1 + g0);
+        const double q0 = p0 + A.dt * Ex - f * D1;
+        const double q1 = p1 + A.dt * Ey - f * D2;
+        const double g2 = sqrt(1.0 + q0 * q0 + q1 * q1 + A1 * A1);
+        const double n0 = A.dt * (p0 + q0) / (g1 + g2);
+        const double n1 = A.dt * (p1 + q1) / (g1 + g2);
+        if (!(isfinite(n0) && isfinite(n1))) { bad = true; continue; }
+        // the current of the new path
+        const double wx = A.w * n0, wy = A.w * n1;
+        ok = ok && path_means<K>(A, u0x, u0y, n0 / A.dx1, n1 / A.dx2, [&](int i, double vx, double vy) {
+            if (vx != 0.0) atomicAdd(&s_j[i], wx * vx);
+            if (vy != 0.0) atomicAdd(&s_j[N + i], wy * vy);
+        });
+        if (!ok) bad = true;
+        dm = fmax(dm, fmax(fabs(n0 - d0), fabs(n1 - d1)));
+        pm = fmax(pm, fmax(fabs(q0 - A.pk[2 * a]), fabs(q1 - A.pk[2 * a + 1])));
+        A.d[2 * a] = n0;
+        A.d[2 * a + 1] = n1;
+        A.pk[2 * a] = q0;
+        A.pk[2 * a + 1] = q1;
+    }
+    if (bad) atomicOr(A.status, STATUS_NUMERIC);
+    // block maxima of the increments
+    __shared__ double s_m[2][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        pm = fmax(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_m[0][threadIdx.x >> 5] = dm;
+        s_m[1][threadIdx.x >> 5] = pm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = fmax(a, s_m[0][w]);
+            b = fmax(b, s_m[1][w]);
+        }
+        max_bits(A.dmax_bits, a);
+        max_bits(A.pmax_bits, b);
+    }
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+        const double v = s_j[i];
+        if (v != 0.0) atomicAdd(i < N ? &A.jx[i] : &A.jy[i - N], v);
+    }
+}
+
+// out[i1, i2] = sum_q g[(i_axis - q) mod M_axis] in[.. q ..] along one axis
+__global__ void k2_circ(int M1, int M2, int axis, const double *g, const double *in, double *out)
+{
+    const int N = M1 * M2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const int i1 = i / M2, i2 = i % M2;
+        double s = 0.0;
+        if (axis == 0) {
+            for (int q = 0; q < M1; ++q) s += g[wrapi(i1 - q, M1)] * in[q * M2 + i2];
+        } else {
+            for (int q = 0; q < M2; ++q) s += g[wrapi(i2 - q, M2)] * in[i1 * M2 + q];
+        }
+        out[i] = s;
+    }
+}
+
+// e^(k+1) = e^n - sol (sol = M1^{-1} j); increment max-norm; e_bar for the next sweep
+__global__ void k2_update(int N, const double *en, const double *sol, double *ek, double *eb,
+                          unsigned long long *emax_bits)
+{
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const double v = en[i] - sol[i];
+        m = fmax(m, fabs(v - ek[i]));
+        if (!(v == v)) m = v;
+        ek[i] = v;
+        eb[i] = 0.5 * (en[i] + v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = (t > m || t != t) ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) max_bits(emax_bits, m);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k2_kinetic(long long np, int M1, int M2, double dx1, double dx2, double w,
+                                                   const double *x, const double *p, const double *az, double *acc)
+{
+    double s = 0.0;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < np;
+         a += (long long)gridDim.x * blockDim.x) {
+        const double A = value0<K>(az, M1, M2, x[2 * a] / dx1, x[2 * a + 1] / dx2);
+        s += w * (sqrt(1.0 + p[2 * a] * p[2 * a] + p[2 * a + 1] * p[2 * a + 1] + A * A) - 1.0);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+
+// x^{n+1} = x^n + delta wrapped into the box, p^{n+1} = p^(k)
+__global__ void k2_finalize(long long np, double L1, double L2, double *x, double *p, const double *d,
+                            const double *pk)
+{
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < np;
+         a += (long long)gridDim.x * blockDim.x) {
+        for (int q = 0; q < 2; ++q) {
+            const double L = q == 0 ? L1 : L2;
+            double v = x[2 * a + q] + d[2 * a + q];
+            v -= L * floor(v / L);
+            if (v >= L) v -= L;
+            if (v < 0.0) v = 0.0;
+            x[2 * a + q] = v;
+            p[2 * a + q] = pk[2 * a + q];
+        }
+    }
+}
+
+// K-point Gauss--Legendre nodes and weights on [-1, 1] by Newton's method on the
+// three-term recurrence of the Legendre polynomials
+void gauss_legendre(int n, double *x, double *w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int j = 1; j < n; ++j) {
+                const double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            double pn = n == 0 ? 1.0 : p1, pm = n == 0 ? 0.0 : p0;
+            if (n == 1) { pn = z; pm = 1.0; }
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+}  // namespace
+}  // namespace pic
+
+using namespace pic;
+
+struct pic2d_handle {
+    pic2d_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    double dx1 = 0.0, dx2 = 0.0;
+    int N = 0;
+    double *x = nullptr, *p = nullptr, *d = nullptr, *pk = nullptr;
+    double *ex = nullptr, *ey = nullptr, *exk = nullptr, *eyk = nullptr, *ebx = nullptr, *eby = nullptr;
+    double *az = nullptr, *gax = nullptr, *gay = nullptr;
+    double *jx = nullptr, *jy = nullptr, *tmp = nullptr, *sol = nullptr;
+    double *g1x = nullptr, *g0y = nullptr, *g0x = nullptr, *g1y = nullptr;   // inverse rows
+    unsigned long long *bits = nullptr;      // dmax, pmax, emax
+    int *status = nullptr;
+    double *acc = nullptr;
+    std::vector<double> m0x, m1x, m0y, m1y;  // 1D mass rows (host) for the field energy
+    double glx[5] = {0, 0, 0, 0, 0}, glw[5] = {0, 0, 0, 0, 0};
+    std::string err;
+};
+
+static thread_local std::string g_err2d;
+
+static int fail2d(pic2d_handle *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_err2d = buf;
+    return code;
+}
+
+#define CK2(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return fail2d(h, PIC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static void free2d(pic2d_handle *h)
+{
+    double **arrs[] = {&h->x, &h->p, &h->d, &h->pk, &h->ex, &h->ey, &h->exk, &h->eyk, &h->ebx, &h->eby,
+                       &h->az, &h->gax, &h->gay, &h->jx, &h->jy, &h->tmp, &h->sol, &h->g1x, &h->g0y,
+                       &h->g0x, &h->g1y, &h->acc};
+    for (double **a : arrs)
+        if (*a) { cudaFree(*a); *a = nullptr; }
+    if (h->bits) cudaFree(h->bits);
+    if (h->status) cudaFree(h->status);
+    h->bits = nullptr;
+    h->status = nullptr;
+}
+
+// full periodic circulant row of the degree-d mass matrix (band folded onto M nodes)
+static std::vector<double> mass_row_full(int d, int M, double dx)
+{
+    std::vector<double> band(d + 1), row(M, 0.0);
+    mass_band(d, dx, band.data());
+    for (int r = -d; r <= d; ++r) row[((r % M) + M) % M] += band[r < 0 ? -r : r];
+    return row;
+}
+
+static std::vector<double> inverse_row(int d, int M, double dx)
+{
+    std::vector<double> band(d + 1), g(M), taps(M);
+    mass_band(d, dx, band.data());
+    int start = 0, n = 0;
+    inverse_taps(band.data(), d, M, 0.0, g.data(), &start, &n, taps.data());
+    return g;
+}
+
+template <int K>
+static int launch_sweep2d(const Args2D &a, int grid, size_t smem, cudaStream_t s)
+{
+    k2_sweep<K><<<grid, 256, smem, s>>>(a);
+    return 0;
+}
+
+extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double *p, const double *ex,
+                          const double *ey, const double *az, int32_t mem, void *stream, pic2d_handle **out)
+{
+    if (!cfg || !x || !p || !ex || !ey || !az || !out) return fail2d(nullptr, PIC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    const pic2d_config &c = *cfg;
+    if (!(c.L1 > 0.0) || !(c.L2 > 0.0) || c.M1 < 1 || c.M2 < 1 || (long long)c.M1 * c.M2 > kMax2DNodes ||
+        c.degree < 2 || c.degree > 5 || c.np < 1 || !(c.dt > 0.0) || !(c.tol > 0.0) || c.max_iter < 1 ||
+        !std::isfinite(c.weight) || (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE))
+        return fail2d(nullptr, PIC_ERR_INVALID, "bad 2D configuration");
+    pic2d_handle *h = new (std::nothrow) pic2d_handle();
+    if (!h) return fail2d(nullptr, PIC_ERR_NOMEM, "handle");
+    h->cfg = c;
+    h->stream = (cudaStream_t)stream;
+    cudaGetDevice(&h->device);
+    h->dx1 = c.L1 / c.M1;
+    h->dx2 = c.L2 / c.M2;
+    h->N = c.M1 * c.M2;
+    const size_t np2 = 2 * (size_t)c.np, N = (size_t)h->N;
+    auto bail = [&](int rc) {
+        g_err2d = h->err.empty() ? "pic2d_init failed" : h->err;
+        free2d(h);
+        delete h;
+        return rc;
+    };
+    double **parts[] = {&h->x, &h->p, &h->d, &h->pk};
+    for (double **a : parts)
+        if (cudaMalloc((void **)a, np2 * sizeof(double)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
+    double **grids[] = {&h->ex, &h->ey, &h->exk, &h->eyk, &h->ebx, &h->eby, &h->az, &h->gax, &h->gay,
+                        &h->jx, &h->jy, &h->tmp, &h->sol};
+    for (double **a : grids)
+        if (cudaMalloc((void **)a, N * sizeof(double)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
+    if (cudaMalloc((void **)&h->g1x, c.M1 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&h->g0x, c.M1 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&h->g0y, c.M2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&h->g1y, c.M2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&h->bits, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void **)&h->status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void **)&h->acc, sizeof(double)) != cudaSuccess)
+        return bail(PIC_ERR_NOMEM);
+    // positions must lie in the box
+    const cudaMemcpyKind kind = mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (mem == PIC_MEM_HOST) {
+        for (size_t a = 0; a < (size_t)c.np; ++a)
+            if (!(x[2 * a] >= 0.0 && x[2 * a] < c.L1 && x[2 * a + 1] >= 0.0 && x[2 * a + 1] < c.L2) ||
+                !std::isfinite(p[2 * a]) || !std::isfinite(p[2 * a + 1])) {
+                fail2d(h, PIC_ERR_INVALID, "marker %zu outside the box or not finite", a);
+                return bail(PIC_ERR_INVALID);
+            }
+    }
+    if (cudaMemcpyAsync(h->x, x, np2 * sizeof(double), kind, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->p, p, np2 * sizeof(double), kind, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->ex, ex, N * sizeof(double), kind, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->ey, ey, N * sizeof(double), kind, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->az, az, N * sizeof(double), kind, h->stream) != cudaSuccess)
+        return bail(fail2d(h, PIC_ERR_CUDA, "input copies"));
+    // gradients of A_z (host: small grids): (G_x a)_{i1,i2} = (a_{i1,i2} - a_{i1-1,i2}) / dx1
+    {
+        std::vector<double> a(N), gx(N), gy(N);
+        if (cudaMemcpyAsync(a.data(), h->az, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return bail(fail2d(h, PIC_ERR_CUDA, "a_z readback"));
+        for (int i1 = 0; i1 < c.M1; ++i1)
+            for (int i2 = 0; i2 < c.M2; ++i2) {
+                const int i = i1 * c.M2 + i2;
+                gx[i] = (a[i] - a[((i1 - 1 + c.M1) % c.M1) * c.M2 + i2]) / h->dx1;
+                gy[i] = (a[i] - a[i1 * c.M2 + (i2 - 1 + c.M2) % c.M2]) / h->dx2;
+            }
+        std::vector<double> g1x = inverse_row(c.degree - 1, c.M1, h->dx1), g0x = inverse_row(c.degree, c.M1, h->dx1);
+        std::vector<double> g1y = inverse_row(c.degree - 1, c.M2, h->dx2), g0y = inverse_row(c.degree, c.M2, h->dx2);
+        h->m0x = mass_row_full(c.degree, c.M1, h->dx1);
+        h->m1x = mass_row_full(c.degree - 1, c.M1, h->dx1);
+        h->m0y = mass_row_full(c.degree, c.M2, h->dx2);
+        h->m1y = mass_row_full(c.degree - 1, c.M2, h->dx2);
+        if (cudaMemcpy(h->gax, gx.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->gay, gy.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->g1x, g1x.data(), c.M1 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->g0x, g0x.data(), c.M1 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->g1y, g1y.data(), c.M2 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->g0y, g0y.data(), c.M2 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail2d(h, PIC_ERR_CUDA, "grid uploads"));
+    }
+    gauss_legendre(c.degree, h->glx, h->glw);
+    const size_t smem = 2 * N * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    switch (c.degree) {
+    case 2: e = cudaFuncSetAttribute(k2_sweep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    case 3: e = cudaFuncSetAttribute(k2_sweep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    case 4: e = cudaFuncSetAttribute(k2_sweep<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    default: e = cudaFuncSetAttribute(k2_sweep<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    }
+    if (e != cudaSuccess) return bail(fail2d(h, PIC_ERR_CUDA, "shared-memory opt-in: %s", cudaGetErrorString(e)));
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(fail2d(h, PIC_ERR_CUDA, "init sync"));
+    *out = h;
+    return PIC_OK;
+}
+
+static int solve_axis_pair(pic2d_handle *h, const double *ga, const double *gb, const double *in)
+{
+    // sol = (A_1^{-1} (x) B_2^{-1}) in: first along x2 with gb, then along x1 with ga
+    const int grid = (h->N + 255) / 256;
+    k2_circ<<<grid, 256, 0, h->stream>>>(h->cfg.M1, h->cfg.M2, 1, gb, in, h->tmp);
+    k2_circ<<<grid, 256, 0, h->stream>>>(h->cfg.M1, h->cfg.M2, 0, ga, h->tmp, h->sol);
+    CK2(cudaGetLastError());
+    return PIC_OK;
+}
+
+extern "C" int pic2d_substep1(pic2d_handle *h, int32_t *iters)
+{
+    if (!h) return PIC_ERR_INVALID;
+    const pic2d_config &c = h->cfg;
+    const size_t np2 = 2 * (size_t)c.np, N = (size_t)h->N;
+    cudaStream_t s = h->stream;
+    CK2(cudaMemsetAsync(h->d, 0, np2 * sizeof(double), s));
+    CK2(cudaMemcpyAsync(h->pk, h->p, np2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK2(cudaMemcpyAsync(h->exk, h->ex, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK2(cudaMemcpyAsync(h->eyk, h->ey, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK2(cudaMemcpyAsync(h->ebx, h->ex, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK2(cudaMemcpyAsync(h->eby, h->ey, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK2(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+    Args2D a{};
+    a.M1 = c.M1; a.M2 = c.M2; a.np = c.np; a.dx1 = h->dx1; a.dx2 = h->dx2; a.dt = c.dt; a.w = c.weight;
+    a.x = h->x; a.pn = h->p; a.d = h->d; a.pk = h->pk;
+    a.ebx = h->ebx; a.eby = h->eby; a.az = h->az; a.gax = h->gax; a.gay = h->gay;
+    a.jx = h->jx; a.jy = h->jy; a.dmax_bits = h->bits; a.pmax_bits = h->bits + 1; a.status = h->status;
+    for (int g = 0; g < 5; ++g) { a.glx[g] = h->glx[g]; a.glw[g] = h->glw[g]; }
+    int num_sms = 0;
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int grid = (int)std::min<long long>((c.np + 255) / 256, 4LL * (num_sms > 0 ? num_sms : 1));
+    const size_t smem = 2 * N * sizeof(double);
+    unsigned long long hb[3];
+    int hs = 0;
+    int it = 0;
+    for (;;) {
+        CK2(cudaMemsetAsync(h->jx, 0, N * sizeof(double), s));
+        CK2(cudaMemsetAsync(h->jy, 0, N * sizeof(double), s));
+        CK2(cudaMemsetAsync(h->bits, 0, 3 * sizeof(unsigned long long), s));
+        switch (c.degree) {
+        case 2: launch_sweep2d<2>(a, grid, smem, s); break;
+        case 3: launch_sweep2d<3>(a, grid, smem, s); break;
+        case 4: launch_sweep2d<4>(a, grid, smem, s); break;
+        default: launch_sweep2d<5>(a, grid, smem, s); break;
+        }
+        CK2(cudaGetLastError());
+        int rc;
+        if ((rc = solve_axis_pair(h, h->g1x, h->g0y, h->jx))) return rc;
+        k2_update<<<(h->N + 255) / 256, 256, 0, s>>>(h->N, h->ex, h->sol, h->exk, h->ebx, h->bits + 2);
+        if ((rc = solve_axis_pair(h, h->g0x, h->g1y, h->jy))) return rc;
+        k2_update<<<(h->N + 255) / 256, 256, 0, s>>>(h->N, h->ey, h->sol, h->eyk, h->eby, h->bits + 2);
+        CK2(cudaGetLastError());
+        CK2(cudaMemcpyAsync(hb, h->bits, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        CK2(cudaMemcpyAsync(&hs, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK2(cudaStreamSynchronize(s));
+        ++it;
+        double dm, pm, em;
+        std::memcpy(&dm, &hb[0], 8);
+        std::memcpy(&pm, &hb[1], 8);
+        std::memcpy(&em, &hb[2], 8);
+        if (hs & STATUS_NUMERIC) return fail2d(h, PIC_ERR_NUMERIC, "2D subsystem I: non-finite value or a path beyond %d cells", kMaxCross);
+        if (!(dm == dm && pm == pm && em == em)) return fail2d(h, PIC_ERR_NUMERIC, "2D subsystem I: NaN increment");
+        if (dm <= c.tol && pm <= c.tol && em <= c.tol) break;
+        if (it >= c.max_iter) {
+            if (iters) *iters = it;
+            return fail2d(h, PIC_ERR_NOCONVERGE, "2D subsystem I: no convergence in %d sweeps", c.max_iter);
+        }
+    }
+    if (iters) *iters = it;
+    k2_finalize<<<(int)std::min<long long>((c.np + 255) / 256, 1024), 256, 0, s>>>(c.np, c.L1, c.L2, h->x, h->p,
+                                                                                     h->d, h->pk);
+    CK2(cudaMemcpyAsync(h->ex, h->exk, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK2(cudaMemcpyAsync(h->ey, h->eyk, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK2(cudaGetLastError());
+    CK2(cudaStreamSynchronize(s));
+    return PIC_OK;
+}
+
+// e^T (A (x) B) e / 2 with circulant rows a (M1) and b (M2), on the host
+static double kron_quad(const std::vector<double> &e, const std::vector<double> &ra, const std::vector<double> &rb,
+                        int M1, int M2)
+{
+    double s = 0.0;
+    for (int i1 = 0; i1 < M1; ++i1)
+        for (int i2 = 0; i2 < M2; ++i2) {
+            double v = 0.0;
+            for (int q1 = 0; q1 < M1; ++q1) {
+                const double ca = ra[((q1 - i1) % M1 + M1) % M1];
+                if (ca == 0.0) continue;
+                for (int q2 = 0; q2 < M2; ++q2) v += ca * rb[((q2 - i2) % M2 + M2) % M2] * e[q1 * M2 + q2];
+            }
+            s += e[i1 * M2 + i2] * v;
+        }
+    return 0.5 * s;
+}
+
+extern "C" int pic2d_energy(pic2d_handle *h, double out[3])
+{
+    if (!h || !out) return PIC_ERR_INVALID;
+    const pic2d_config &c = h->cfg;
+    CK2(cudaMemsetAsync(h->acc, 0, sizeof(double), h->stream));
+    const int grid = (int)std::min<long long>((c.np + 255) / 256, 1024);
+    switch (c.degree) {
+    case 2: k2_kinetic<2><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, h->acc); break;
+    case 3: k2_kinetic<3><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, h->acc); break;
+    case 4: k2_kinetic<4><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, h->acc); break;
+    default: k2_kinetic<5><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, h->acc); break;
+    }
+    CK2(cudaGetLastError());
+    std::vector<double> ex(h->N), ey(h->N);
+    double kin = 0.0;
+    CK2(cudaMemcpyAsync(&kin, h->acc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK2(cudaMemcpyAsync(ex.data(), h->ex, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK2(cudaMemcpyAsync(ey.data(), h->ey, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK2(cudaStreamSynchronize(h->stream));
+    const double fe = kron_quad(ex, h->m1x, h->m0y, c.M1, c.M2) + kron_quad(ey, h->m0x, h->m1y, c.M1, c.M2);
+    out[0] = kin;
+    out[1] = fe;
+    out[2] = kin + fe;
+    return PIC_OK;
+}
+
+extern "C" int pic2d_get_state(pic2d_handle *h, double *x, double *p, double *ex, double *ey, int32_t mem)
+{
+    if (!h || (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE)) return PIC_ERR_INVALID;
+    const cudaMemcpyKind kind = mem == PIC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const size_t np2 = 2 * (size_t)h->cfg.np, N = (size_t)h->N;
+    if (x) CK2(cudaMemcpyAsync(x, h->x, np2 * sizeof(double), kind, h->stream));
+    if (p) CK2(cudaMemcpyAsync(p, h->p, np2 * sizeof(double), kind, h->stream));
+    if (ex) CK2(cudaMemcpyAsync(ex, h->ex, N * sizeof(double), kind, h->stream));
+    if (ey) CK2(cudaMemcpyAsync(ey, h->ey, N * sizeof(double), kind, h->stream));
+    CK2(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
+extern "C" int pic2d_destroy(pic2d_handle *h)
+{
+    if (!h) return PIC_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free2d(h);
+    delete h;
+    return PIC_OK;
+}
+
+extern "C" const char *pic2d_last_error(const pic2d_handle *h)
+{
+    return h ? h->err.c_str() : g_err2d.c_str();
+}

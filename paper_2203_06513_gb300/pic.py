@@ -60,9 +60,14 @@ _lib = None
 
 
 def declared_symbols() -> list[str]:
-    """Entry points declared in include/pic.h."""
-    txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pic_\w+)\s*\(", txt, re.M)))
+    """Entry points declared in include/*.h (pic.h, pic2d.h)."""
+    names = set()
+    inc = os.path.dirname(HEADER)
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pic(?:2d)?_\w+)\s*\(", txt, re.M))
+    return sorted(names)
 
 
 def load(path: str | None = None):
