@@ -49,6 +49,9 @@ struct pic_ensemble {
     EnsRun *d_er = nullptr;
     EnsQueue *d_q = nullptr;
     int *d_sweeps = nullptr, *d_status = nullptr;
+    std::vector<SortRun> sorts;         // the runs due for their periodic sort (batched)
+    SortRun *d_sorts = nullptr;
+    int sort_grid = 1;
     int *h_buf = nullptr;               // pinned readback: sweeps (2 nruns), status (nruns), Q fields
 
     size_t smem1 = 0, smem2 = 0;
@@ -355,7 +358,7 @@ static void ens_release(pic_ensemble *e)
     if (e->graph) cudaGraphDestroy(e->graph);
     auto f = [](void *p) { if (p) cudaFree(p); };
     f(e->d_desc); f(e->d_a1); f(e->d_a2); f(e->d_c1); f(e->d_c2); f(e->d_cp); f(e->d_er); f(e->d_q);
-    f(e->d_a1p); f(e->d_c1p);
+    f(e->d_a1p); f(e->d_c1p); f(e->d_sorts);
     f(e->d_sweeps); f(e->d_status);
     if (e->h_buf) cudaFreeHost(e->h_buf);
     if (e->cap) cudaStreamDestroy(e->cap);
@@ -430,6 +433,8 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
         e->bps_max = std::max(1, std::min(b1, b2));
         e->bps = e->bps_max;
     }
+    // sort blocks a run: about four sweeps of 256 markers a block for the largest
+    e->sort_grid = (int)std::min<long long>(std::max<long long>((npmax + 1023) / 1024, 1), 4LL * e->num_sms);
     const size_t n = (size_t)nruns;
     e->desc.resize(n); e->a1.resize(n); e->a2.resize(n); e->c1.resize(n); e->c2.resize(n);
     e->cp.resize(n); e->er.resize(n); e->a1p.resize(n); e->c1p.resize(n);
@@ -437,7 +442,8 @@ extern "C" int pic_ensemble_create(const pic_config *cfgs, const pic_arrays *ins
     if ((rc = ealloc(e, &e->d_desc, n)) || (rc = ealloc(e, &e->d_a1, n)) || (rc = ealloc(e, &e->d_a2, n)) ||
         (rc = ealloc(e, &e->d_c1, n)) || (rc = ealloc(e, &e->d_c2, n)) || (rc = ealloc(e, &e->d_cp, n)) ||
         (rc = ealloc(e, &e->d_er, n)) || (rc = ealloc(e, &e->d_q, 1)) || (rc = ealloc(e, &e->d_sweeps, 2 * n)) ||
-        (rc = ealloc(e, &e->d_status, n)) || (rc = ealloc(e, &e->d_a1p, n)) || (rc = ealloc(e, &e->d_c1p, n)))
+        (rc = ealloc(e, &e->d_status, n)) || (rc = ealloc(e, &e->d_a1p, n)) || (rc = ealloc(e, &e->d_c1p, n)) ||
+        (rc = ealloc(e, &e->d_sorts, n)))
         return bail(rc);
     if (cudaMallocHost((void **)&e->h_buf, (3 * n + 8) * sizeof(int)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
     if (cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess) return bail(PIC_ERR_CUDA);
@@ -485,16 +491,33 @@ extern "C" int pic_ensemble_step(pic_ensemble *e, int32_t nsteps, int64_t *sweep
         } else if ((rc = host_step(e))) {
             return rc;
         }
-        // periodic marker sort of each run (ordinary launches, then fresh tables)
-        bool resorted = false;
+        // periodic marker sort of the runs due, all in one batched sort (four
+        // launches instead of four per run), then fresh tables
+        e->sorts.clear();
         for (pic_handle *h : e->runs) {
             ++h->steps_done;
             if (h->cfg.sort_every > 0 && h->steps_done % h->cfg.sort_every == 0) {
-                if ((rc = handle_sort(h))) return efail(e, rc, "sort: %s", pic_last_error(h));
-                resorted = true;
+                SortRun r{};
+                const int per = bins_per_cell(h->np, h->M);
+                r.np = h->np;
+                r.M = h->M;
+                r.nbins = kVelBinsBase * per;
+                r.taup = (float)(h->cfg.dt / h->dx * per);
+                r.src = handle_parts(h);
+                r.dst = h->P[1 - h->cur];
+                r.dst.delta = h->delta;
+                r.dst.pnew = h->pnew;
+                r.counts = h->counts;
+                e->sorts.push_back(r);
+                h->cur = 1 - h->cur;
             }
         }
-        if (resorted) {
+        if (!e->sorts.empty()) {
+            ECK(cudaMemcpyAsync(e->d_sorts, e->sorts.data(), e->sorts.size() * sizeof(SortRun),
+                                cudaMemcpyHostToDevice, e->stream));
+            ELAUNCH(launch_sort_ens(e->fp32, e->d_sorts, (int)e->sorts.size(), e->sort_grid, e->stream),
+                    "ensemble sort");
+            e->launches += 4;
             build_tables(e);
             if ((rc = upload_tables(e))) return rc;
         }

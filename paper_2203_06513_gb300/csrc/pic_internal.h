@@ -130,6 +130,15 @@ int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, doubl
 int sweep_blocks_per_sm(int K, int fp32, int acc, int which, int block, size_t smem);
 // whether the sweep kernels are built for (degree, form, accumulator)
 bool sweep_variant_ok(int K, int fp32, int acc);
+// one run's counting sort in a batched launch (key: cell * nbins + velocity bin)
+struct SortRun {
+    long long np;
+    int M, nbins;
+    float taup;             // dt / dx times the bins per cell
+    PartPtrs src, dst;
+    int32_t *counts;        // 2 M nbins: histogram, then cursors
+};
+int launch_sort_ens(int fp32, const SortRun *runs, int nruns, int grid_x, cudaStream_t s);
 int launch_sort(int fp32, long long np, int M, double tau, int per, PartPtrs src, PartPtrs dst,
                 int32_t *counts, int grid, int block, cudaStream_t s);
 

@@ -1385,12 +1385,20 @@ __device__ __forceinline__ int sort_key(int c, R p, float taup, int nbins)
 // nearly sorted (they were sorted a few steps ago), so the blocks running at the
 // same time then touch different keys' counters; in a grid-stride order every
 // block would work on the same few cells at once and serialise on their counters.
+// chunk [beg, end) of block b among nb blocks (a multiple of 32 markers)
+__device__ __forceinline__ void chunk_of(long long np, int b, int nb, long long &beg, long long &end)
+{
+    long long chunk = (np + nb - 1) / nb;
+    chunk = (chunk + 31) & ~31LL;
+    beg = (long long)b * chunk;
+    end = beg + chunk < np ? beg + chunk : np;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_hist(long long np, float tau, int nbins, PartPtrs S, int32_t *counts)
+__device__ __forceinline__ void hist_range(long long beg, long long end, float tau, int nbins, const PartPtrs &S,
+                                           int32_t *counts)
 {
     const R *ps = static_cast<const R *>(S.p);
-    long long beg, end;
-    block_chunk(np, beg, end);
     const int lane = threadIdx.x & 31;
     for (long long base = beg; base < end; base += blockDim.x) {
         const long long a = base + threadIdx.x;
@@ -1401,7 +1409,15 @@ __global__ void __launch_bounds__(256) k_hist(long long np, float tau, int nbins
     }
 }
 
-__global__ void __launch_bounds__(1024) k_scan(int nkeys, int32_t *counts)
+template <typename R>
+__global__ void __launch_bounds__(256) k_hist(long long np, float tau, int nbins, PartPtrs S, int32_t *counts)
+{
+    long long beg, end;
+    block_chunk(np, beg, end);
+    hist_range<R>(beg, end, tau, nbins, S, counts);
+}
+
+__device__ __forceinline__ void scan_block(int nkeys, int32_t *counts)
 {
     // exclusive scan of nkeys counts into cursors (single block)
     __shared__ int s_part[1024];
@@ -1421,16 +1437,16 @@ __global__ void __launch_bounds__(1024) k_scan(int nkeys, int32_t *counts)
     for (int i = lo; i < hi; ++i) { const int v = counts[i]; counts[nkeys + i] = run; run += v; }
 }
 
+__global__ void __launch_bounds__(1024) k_scan(int nkeys, int32_t *counts) { scan_block(nkeys, counts); }
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_scatter(long long np, float tau, int nbins, PartPtrs S, PartPtrs D,
-                                                 int32_t *cursor)
+__device__ __forceinline__ void scatter_range(long long beg, long long end, float tau, int nbins, const PartPtrs &S,
+                                              const PartPtrs &D, int32_t *cursor)
 {
     const R *ts = static_cast<const R *>(S.t);
     const R *ps = static_cast<const R *>(S.p);
     R *td = static_cast<R *>(D.t);
     R *pd = static_cast<R *>(D.p);
-    long long beg, end;
-    block_chunk(np, beg, end);
     const int lane = threadIdx.x & 31;
     // kSortU markers a thread per pass: their cursor atomics are independent, so
     // the warp waits for the returned slots once per pass instead of once a marker
@@ -1465,6 +1481,61 @@ __global__ void __launch_bounds__(256) k_scatter(long long np, float tau, int nb
             D.id[j] = S.id[a];
         }
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_scatter(long long np, float tau, int nbins, PartPtrs S, PartPtrs D,
+                                                 int32_t *cursor)
+{
+    long long beg, end;
+    block_chunk(np, beg, end);
+    scatter_range<R>(beg, end, tau, nbins, S, D, cursor);
+}
+
+// Batched sorts (ensembles): block row y = run, its counts zeroed, histogrammed,
+// scanned (one block a run) and scattered in four launches for all runs due.
+__global__ void __launch_bounds__(256) k_sort_zero_ens(const SortRun *runs)
+{
+    const SortRun &r = runs[blockIdx.y];
+    const int n = 2 * r.M * r.nbins;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r.counts[i] = 0;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_hist_ens(const SortRun *runs)
+{
+    const SortRun &r = runs[blockIdx.y];
+    long long beg, end;
+    chunk_of(r.np, blockIdx.x, gridDim.x, beg, end);
+    hist_range<R>(beg, end, r.taup, r.nbins, r.src, r.counts);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_ens(const SortRun *runs)
+{
+    const SortRun &r = runs[blockIdx.x];
+    scan_block(r.M * r.nbins, r.counts);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_scatter_ens(const SortRun *runs)
+{
+    const SortRun &r = runs[blockIdx.y];
+    long long beg, end;
+    chunk_of(r.np, blockIdx.x, gridDim.x, beg, end);
+    scatter_range<R>(beg, end, r.taup, r.nbins, r.src, r.dst, r.counts + (size_t)r.M * r.nbins);
+}
+
+int launch_sort_ens(int fp32, const SortRun *runs, int nruns, int grid_x, cudaStream_t s)
+{
+    if (nruns < 1) return 0;
+    const dim3 g(grid_x, nruns);
+    k_sort_zero_ens<<<g, 256, 0, s>>>(runs);
+    if (fp32) k_hist_ens<float><<<g, 256, 0, s>>>(runs);
+    else k_hist_ens<double><<<g, 256, 0, s>>>(runs);
+    k_scan_ens<<<nruns, 1024, 0, s>>>(runs);
+    if (fp32) k_scatter_ens<float><<<g, 256, 0, s>>>(runs);
+    else k_scatter_ens<double><<<g, 256, 0, s>>>(runs);
+    return 0;
 }
 
 int launch_sort(int fp32, long long np, int M, double tau, int per, PartPtrs src, PartPtrs dst,
