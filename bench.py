@@ -271,6 +271,44 @@ def e2e_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None):
     return {"s": t1 - t0, "h2d": h2d, "d2h": d2h}
 
 
+def twod_run(steps: int, np_: int | None = None, oracle_np: int = 100):
+    """Subsystem I of the 2D scheme (FP64, Sec. 4.3) on the 2D workload: wall time
+    of `steps` substeps after one warm-up (each substep synchronises per sweep),
+    marker-substeps/s, sweeps and energy; the 2D oracle timed on a small sample of
+    the same workload on one host thread."""
+    import dataclasses
+    from paper_2203_06513_gb300 import pic2d as P2
+    w = I.Workload2D() if np_ is None else dataclasses.replace(I.Workload2D(), np=int(np_))
+    x, p = I.particles2d(w)
+    ex, ey, az = I.fields2d(w)
+    cfg = P2.Config2D(w.L1, w.L2, w.M1, w.M2, w.degree, w.np, w.weight, w.dt)
+    g = P2.Pic2D(cfg, x, p, ex, ey, az)
+    H0 = g.energy()["total"]
+    g.substep1()
+    t0 = time.perf_counter()
+    sweeps = 0
+    for _ in range(steps):
+        sweeps += g.substep1()
+    dt_s = time.perf_counter() - t0
+    H1 = g.energy()["total"]
+    g.close()
+    out = {"value": w.np * steps / dt_s, "unit": "marker-substeps/s", "ms_per_substep": 1e3 * dt_s / steps,
+           "sweeps_per_substep": sweeps / steps, "rel_energy_err": abs(H1 - H0) / abs(H0),
+           "us_per_marker_sweep": 1e6 * dt_s / (w.np * max(1, sweeps)),
+           "workload": "2D subsystem I: L1=L2=4pi, M1=M2=%d, k=%d, Np=%d, dt=%g, vth %g, A_z %g cos(2 x1) "
+                       "cos(x2 2pi/L2), FP64" % (w.M1, w.degree, w.np, w.dt, w.vth, w.amp)}
+    if oracle_np:
+        from oracle import oracle2d as O2
+        ws = dataclasses.replace(w, np=oracle_np)
+        xs, ps = I.particles2d(ws)
+        orc = O2.Oracle2D(w.L1, w.L2, w.M1, w.M2, w.degree, ws.weight, w.dt)
+        t0 = time.perf_counter()
+        orc.substep1(xs, ps, ex, ey, az)
+        out["cpu_oracle"] = {"value": oracle_np / (time.perf_counter() - t0), "unit": "marker-substeps/s",
+                             "cores": 1, "sample": "%d markers of the same workload, one substep" % oracle_np}
+    return out
+
+
 def _member_inputs(w):
     x, p = I.particles(w)
     ay, az, ey, ez = I.fields(w)
@@ -411,6 +449,7 @@ def main():
     ap.add_argument("--ensemble-scale", type=float, default=1.0, help="scale of the runs' marker counts")
     ap.add_argument("--ensemble-host-loop", action="store_true",
                     help="drive the ensemble's loops from the host (same kernels, no graph; for profiling)")
+    ap.add_argument("--twod-steps", type=int, default=5, help="substeps of the 2D subsystem-I line (0: skip)")
     ap.add_argument("--split", action="store_true",
                     help="with N > 1: one plasma of N x Np markers split over the ranks (an all-reduce of the "
                          "deposits per sweep) instead of N independent replicas; only the timed forms run")
@@ -511,6 +550,9 @@ def main():
                          "sweep2_launch_ms": r["timing"]["sweep2_ms"] / max(1, r["timing"]["sweep2_launches"]),
                          "ms_per_step": r["ms"] / args.deposit_variants}
         barrier()
+    twod = None
+    if args.twod_steps > 0 and not split_mode and rank == 0:
+        twod = twod_run(args.twod_steps, oracle_np=0 if args.no_cpu else 100)
     ens = None
     if ens_in is not None:
         del arrays, x, p
@@ -575,6 +617,7 @@ def main():
                           "solve": tr["solve_ms"], "warm_start": tr["warm_ms"],
                           "ms_per_step_host_loops": tr["ms_per_step_host_loops"]},
             "ensemble": ens,
+            "twod": twod,
             "deposit_accumulation": dep,
             "fp64": {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
                      "rel_energy_err": r64["rel_energy_err"], "gauss_residual": r64["gauss"],

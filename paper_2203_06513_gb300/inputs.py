@@ -194,3 +194,48 @@ def fields(w: Workload):
 def spins(w: Workload):
     """(sx, sy, sz) initial spins of the markers: s = (0, 0, 1) (Sec. 5)."""
     return np.zeros(w.np), np.zeros(w.np), np.ones(w.np)
+
+
+# ---------------------------------------------------------------------------
+# Two-dimensional subsystem I (measurement workload): markers uniform in the box
+# [0, L1) x [0, L2), p ~ N(0, vth^2) in each component, equal weights L1 L2 / Np;
+# A_z = amp cos(k0 x1) cos(x2 2 pi / L2) at the Greville abscissae of the
+# degree-k tensor-product basis; e_x = e_y = 0.
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Workload2D:
+    L1: float = 4.0 * math.pi
+    L2: float = 4.0 * math.pi
+    M1: int = 64
+    M2: int = 64
+    degree: int = 3
+    np: int = 2_000_000
+    dt: float = 0.05
+    vth: float = 0.1
+    amp: float = 0.2
+    k0: float = 2.0
+    seed: int = 0
+
+    @property
+    def weight(self) -> float:
+        return self.L1 * self.L2 / self.np
+
+
+def particles2d(w: Workload2D):
+    """(x, p), each np x 2, seeded."""
+    rng = np.random.default_rng([w.seed, 2])
+    x = np.empty((w.np, 2))
+    x[:, 0] = rng.uniform(0.0, w.L1, w.np)
+    x[:, 1] = rng.uniform(0.0, w.L2, w.np)
+    p = rng.normal(0.0, w.vth, (w.np, 2))
+    return x, p
+
+
+def fields2d(w: Workload2D):
+    """(e_x, e_y, a_z) coefficients, node index i1 * M2 + i2."""
+    g1 = (np.arange(w.M1) + 0.5 * (w.degree + 1)) * (w.L1 / w.M1)
+    g2 = (np.arange(w.M2) + 0.5 * (w.degree + 1)) * (w.L2 / w.M2)
+    az = w.amp * np.outer(np.cos(w.k0 * g1), np.cos(2.0 * math.pi * g2 / w.L2)).ravel()
+    n = w.M1 * w.M2
+    return np.zeros(n), np.zeros(n), az
