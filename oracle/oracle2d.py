@@ -13,7 +13,7 @@ two-dimensional splitting), written with plain numpy and pure-Python marker loop
 * the V1 mass matrix M1 = diag(M1_x (x) M0_y, M0_x (x) M1_y) from the 1D circulant
   mass matrices, and the gradient G = (G_x (x) I; I (x) G_y) with the 1D
   derivative matrices of the one-dimensional oracle;
-* subsystem I with hbar = 0 (markers x, p in R^2, field e_xy; A_z frozen):
+* subsystem I (markers x, p in R^2, field e_xy; A_z, b_z and the spins frozen):
       x^{n+1} - x^n = dt (p^n + p^{n+1}) / (g(p^n, A(x^{n+1})) + g(p^{n+1}, A(x^{n+1}))),
       p^{n+1} - p^n = int Lambda_1^T(x(t)) dt e_bar
                       - dt (A(x^{n+1}) + A(x^n)) D / (g(p^n, A(x^{n+1})) + g(p^n, A(x^n))),
@@ -30,7 +30,9 @@ either coordinate and integrated on each piece by k-point Gauss--Legendre (the
 integrand is a polynomial of degree 2k - 1 in the path parameter, so the rule is
 exact); the fixed point is Picard on the positions from x^(0) = x^n, p^(0) = p^n,
 one global e_xy update per sweep, stopped when the position, momentum and field
-increments are all at most tol.  The spin terms (hbar != 0) are not built here.
+increments are all at most tol.  With hbar != 0 the Zeeman term's discrete gradient
+uses the same coordinate increments, with the sign of the printed 2D Hamiltonian
+(+ hbar s . B, B = (dA_z/dx2, -dA_z/dx1, B_z)).
 Parity status: every function here is pinned by tests/test_oracle_2d.py.
 """
 from __future__ import annotations
@@ -154,6 +156,39 @@ class Grid2D:
                 D2 += ga_y[self.idx(c1 - r1, i2)] * v1[r1] * m2[i2]
         return D1, D2
 
+    # ---------------- any tensor-product spline ----------------
+    def value(self, c: np.ndarray, d1: int, d2: int, x1: float, x2: float) -> float:
+        """f(x) = sum_i c_i N^{d1}(x1/dx1 - i1) N^{d2}(x2/dx2 - i2)."""
+        c1, v1 = bvals(d1, x1 / self.dx[0])
+        c2, v2 = bvals(d2, x2 / self.dx[1])
+        s = 0.0
+        for r1 in range(d1 + 1):
+            for r2 in range(d2 + 1):
+                s += c[self.idx(c1 - r1, c2 - r2)] * v1[r1] * v2[r2]
+        return s
+
+    def quotients(self, c: np.ndarray, d1: int, d2: int, P0, P1):
+        """Coordinate-increment difference quotients of f (degrees d1, d2), as exact
+        path means: (mean of df/dx1 along x1 at x2 = x2^1, mean of df/dx2 along x2 at
+        x1 = x1^0).  df/dx1 has coefficients G_x c on degrees (d1 - 1, d2)."""
+        fx = self.Gx @ c
+        fy = self.Gy @ c
+        m1 = O.path_mean_deg(d1 - 1, self.M[0], self.dx[0], P0[0], P1[0])
+        c2, v2 = bvals(d2, P1[1] / self.dx[1])
+        Q1 = 0.0
+        for i1 in range(self.M[0]):
+            if m1[i1] != 0.0:
+                for r2 in range(d2 + 1):
+                    Q1 += fx[self.idx(i1, c2 - r2)] * m1[i1] * v2[r2]
+        m2 = O.path_mean_deg(d2 - 1, self.M[1], self.dx[1], P0[1], P1[1])
+        c1, v1 = bvals(d1, P0[0] / self.dx[0])
+        Q2 = 0.0
+        for i2 in range(self.M[1]):
+            if m2[i2] != 0.0:
+                for r1 in range(d1 + 1):
+                    Q2 += fy[self.idx(c1 - r1, i2)] * v1[r1] * m2[i2]
+        return Q1, Q2
+
     # ---------------- grid algebra ----------------
     def solve_M1(self, jx, jy):
         return np.linalg.solve(self.M1x, jx), np.linalg.solve(self.M1y, jy)
@@ -169,12 +204,30 @@ class Grid2D:
 
 
 class Oracle2D:
-    """Subsystem I of the two-dimensional scheme (hbar = 0), plain FP64."""
+    """Subsystem I of the two-dimensional scheme, plain FP64.  With hbar != 0 the
+    markers carry spins s (Np x 3, frozen in this subsystem) and b_z (the 2-form,
+    degrees k-1, k-1) enters through the Zeeman term of the Hamiltonian
+    (Eq. discrete_H2d): hbar sum_a w (s_x dA_z/dx2 - s_y dA_z/dx1 + s_z B_z)(x_a),
+    whose coordinate-increment discrete gradient joins the momentum update."""
 
-    def __init__(self, L1, L2, M1, M2, k, w, dt, tol=1e-13, max_iter=100):
+    def __init__(self, L1, L2, M1, M2, k, w, dt, tol=1e-13, max_iter=100, hbar=0.0):
         self.g = Grid2D(L1, L2, M1, M2, k)
         self.w, self.dt = float(w), float(dt)
         self.tol, self.max_iter = float(tol), int(max_iter)
+        self.hbar = float(hbar)
+
+    def zeeman(self, x, a, s, bz) -> float:
+        """hbar sum_a w (s_x dA/dx2 - s_y dA/dx1 + s_z B_z)(x_a)."""
+        if self.hbar == 0.0 or s is None:
+            return 0.0
+        g, k = self.g, self.g.k
+        ay, ax = g.Gy @ a, g.Gx @ a          # dA/dx2 on (k, k-1), dA/dx1 on (k-1, k)
+        tot = 0.0
+        for q in range(x.shape[0]):
+            x1, x2 = x[q]
+            tot += s[q, 0] * g.value(ay, k, k - 1, x1, x2) - s[q, 1] * g.value(ax, k - 1, k, x1, x2) \
+                + s[q, 2] * g.value(bz, k - 1, k - 1, x1, x2)
+        return self.hbar * self.w * tot
 
     def kinetic(self, x, p, a) -> float:
         s = 0.0
@@ -183,15 +236,21 @@ class Oracle2D:
             s += self.w * (math.sqrt(1.0 + p[q, 0] ** 2 + p[q, 1] ** 2 + A * A) - 1.0)
         return s
 
-    def energy(self, x, p, ex, ey, a) -> dict:
+    def energy(self, x, p, ex, ey, a, s=None, bz=None) -> dict:
         kin = self.kinetic(x, p, a)
         fe = self.g.field_energy(ex, ey)
-        return {"kinetic": kin, "field": fe, "total": kin + fe}
+        ze = self.zeeman(x, a, s, bz)
+        return {"kinetic": kin, "field": fe, "zeeman": ze, "total": kin + fe + ze}
 
-    def substep1(self, x, p, ex, ey, a, dt=None):
-        """One discrete-gradient step of subsystem I.  x, p: (Np, 2); returns
-        (x^{n+1} wrapped into the box, p^{n+1}, e_x^{n+1}, e_y^{n+1}, sweeps)."""
+    def substep1(self, x, p, ex, ey, a, dt=None, s=None, bz=None):
+        """One discrete-gradient step of subsystem I.  x, p: (Np, 2); s (Np, 3) and
+        bz with hbar != 0; returns (x^{n+1} wrapped into the box, p^{n+1}, e_x^{n+1},
+        e_y^{n+1}, sweeps)."""
         g = self.g
+        k = g.k
+        spin = self.hbar != 0.0 and s is not None
+        if spin:
+            ay, ax = g.Gy @ a, g.Gx @ a
         dt = self.dt if dt is None else float(dt)
         x = np.asarray(x, dtype=np.float64)
         pn = np.asarray(p, dtype=np.float64)
@@ -215,6 +274,12 @@ class Oracle2D:
                 g0 = math.sqrt(1.0 + p2 + A0[q] ** 2)
                 g1 = math.sqrt(1.0 + p2 + A1 * A1)
                 pnew = pn[q] + dt * Ebar - dt * (A1 + A0[q]) * D / (g1 + g0)
+                if spin:
+                    # discrete gradient of the Zeeman term (coordinate increments)
+                    Qy = np.array(g.quotients(ay, k, k - 1, P0, Pk))
+                    Qx = np.array(g.quotients(ax, k - 1, k, P0, Pk))
+                    Qb = np.array(g.quotients(bz, k - 1, k - 1, P0, Pk))
+                    pnew = pnew - dt * self.hbar * (s[q, 0] * Qy - s[q, 1] * Qx + s[q, 2] * Qb)
                 g2 = math.sqrt(1.0 + pnew @ pnew + A1 * A1)
                 dnew = dt * (pn[q] + pnew) / (g1 + g2)
                 # current of the new path x^n -> x^n + dnew

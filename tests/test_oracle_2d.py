@@ -195,3 +195,76 @@ def test_reduces_to_one_dimension(axis):
     e2 = ex2 if axis == 0 else ey2
     np.testing.assert_allclose(e2, s1.ex, rtol=0, atol=1e-12)
     assert abs(it1 - it2) <= 1
+
+
+# ---------------- spin terms (hbar != 0) ----------------
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_quotients_telescope_and_match_scipy(k):
+    """Coordinate-increment quotients of the three Zeeman fields (dA/dx2 on degrees
+    (k, k-1), dA/dx1 on (k-1, k), B_z on (k-1, k-1)): Q . (P1 - P0) = f(P1) - f(P0),
+    and each component against scipy's derivative of the periodic B-splines."""
+    g = O2.Grid2D(4.0, 3.0, 6, 5, k)
+    rng = np.random.default_rng(100 + k)
+    a = rng.normal(0, 1, g.N)
+    bz = rng.normal(0, 1, g.N)
+    fields = ((g.Gy @ a, k, k - 1), (g.Gx @ a, k - 1, k), (bz, k - 1, k - 1))
+    for _ in range(4):
+        P0 = np.array([rng.uniform(0, 4.0), rng.uniform(0, 3.0)])
+        P1 = P0 + rng.normal(0, 1.2, 2) * np.array(g.dx)
+        for c, d1, d2 in fields:
+            Q1, Q2 = g.quotients(c, d1, d2, P0, P1)
+            df = g.value(c, d1, d2, P1[0], P1[1]) - g.value(c, d1, d2, P0[0], P0[1])
+            assert abs(Q1 * (P1[0] - P0[0]) + Q2 * (P1[1] - P0[1]) - df) < 1e-12
+            # Q1 = (f(P1) - f(P0[0], P1[1])) / dx1 from scipy's periodic B-splines
+            def f_sc(x1, x2):
+                return sum(c[i] * periodic_basis(d1, g.M[0], g.dx[0], i // g.M[1], x1)
+                           * periodic_basis(d2, g.M[1], g.dx[1], i % g.M[1], x2) for i in range(g.N))
+            r1 = (f_sc(P1[0], P1[1]) - f_sc(P0[0], P1[1])) / (P1[0] - P0[0])
+            r2 = (f_sc(P0[0], P1[1]) - f_sc(P0[0], P0[1])) / (P1[1] - P0[1])
+            assert abs(Q1 - r1) < 1e-11 * max(1.0, abs(r1))
+            assert abs(Q2 - r2) < 1e-11 * max(1.0, abs(r2))
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_energy_conserved_with_spin(k):
+    rng = np.random.default_rng(55 + k)
+    orc, x, p, ex, ey, a = _random_case(9 + k, 6, 5, k, 20)
+    orc.hbar = 0.1
+    s = rng.normal(0, 1, (20, 3))
+    s /= np.linalg.norm(s, axis=1, keepdims=True)
+    bz = 0.3 * rng.normal(0, 1, orc.g.N)
+    E0 = orc.energy(x, p, ex, ey, a, s, bz)
+    assert abs(E0["zeeman"]) > 1e-4 * abs(E0["total"])
+    for _ in range(2):
+        x, p, ex, ey, it = orc.substep1(x, p, ex, ey, a, s=s, bz=bz)
+    E1 = orc.energy(x, p, ex, ey, a, s, bz)
+    assert abs(E1["total"] - E0["total"]) < 1e-12 * abs(E0["total"])
+
+
+def test_spin_reduces_to_one_dimension():
+    """M2 = 1, A_y = 0, B_z = 0: the 2D Zeeman term -hbar s_y dA_z/dx1 is the 1D
+    oracle's hbar s_y dA_z/dx with the spin's y component reversed (the printed 1D
+    and 2D Hamiltonians carry opposite signs of s . B)."""
+    k, M, npart = 3, 8, 20
+    L, Lo = 5.0, 1.7
+    rng = np.random.default_rng(77)
+    xs = rng.uniform(0, L, npart)
+    ps = rng.normal(0, 0.2, npart)
+    az = 0.3 * rng.normal(0, 1, M)
+    e1 = 0.05 * rng.normal(0, 1, M)
+    sp = rng.normal(0, 1, (npart, 3))
+    sp /= np.linalg.norm(sp, axis=1, keepdims=True)
+    w1, dt, hbar = L / npart, 0.1, 0.1
+    orc1 = O.Oracle(L, M, k, w1, dt, hbar=hbar)
+    s0 = O.initial_state(orc1, xs, ps, np.zeros(M), az, None, None, spin=(sp[:, 0], sp[:, 1], sp[:, 2]))
+    s0.ex = e1.copy()
+    s1, _ = orc1.substep1(s0)
+    orc2 = O2.Oracle2D(L, Lo, M, 1, k, w=w1 * Lo, dt=dt, hbar=hbar)
+    x = np.column_stack([xs, rng.uniform(0, Lo, npart)])
+    p = np.column_stack([ps, np.zeros(npart)])
+    s2 = sp * np.array([1.0, -1.0, 1.0])
+    x2, p2, ex2, ey2, _ = orc2.substep1(x, p, e1.copy(), np.zeros(M), az.copy(), s=s2, bz=np.zeros(M))
+    np.testing.assert_allclose(x2[:, 0], s1.x, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(p2[:, 0], s1.p, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(ex2, s1.ex, rtol=0, atol=1e-12)
