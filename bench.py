@@ -450,6 +450,7 @@ def main():
     ap.add_argument("--ensemble-host-loop", action="store_true",
                     help="drive the ensemble's loops from the host (same kernels, no graph; for profiling)")
     ap.add_argument("--twod-steps", type=int, default=5, help="substeps of the 2D subsystem-I line (0: skip)")
+    ap.add_argument("--twod-np", type=float, default=None, help="markers of the 2D line (smaller runs)")
     ap.add_argument("--split", action="store_true",
                     help="with N > 1: one plasma of N x Np markers split over the ranks (an all-reduce of the "
                          "deposits per sweep) instead of N independent replicas; only the timed forms run")
@@ -552,7 +553,7 @@ def main():
         barrier()
     twod = None
     if args.twod_steps > 0 and not split_mode and rank == 0:
-        twod = twod_run(args.twod_steps, oracle_np=0 if args.no_cpu else 100)
+        twod = twod_run(args.twod_steps, np_=args.twod_np, oracle_np=0 if args.no_cpu else 100)
     ens = None
     if ens_in is not None:
         del arrays, x, p
