@@ -9,6 +9,9 @@
 //     against e_bar;
 //   * the coordinate-increment difference quotients D of A_z as exact path means of
 //     dA/dx1 along x1 (at x2^(k)) and of dA/dx2 along x2 (at x1^n);
+//   * with spins (hbar != 0), the quotients of the Zeeman term hbar s . B,
+//     B = (dA/dx2, -dA/dx1, b_z), the same way: path means of the second
+//     differences of A_z and the first differences of b_z along each coordinate;
 //   * the momentum and position updates of the discrete-gradient scheme;
 //   * the current of the new path x^n -> x^(k+1), accumulated per block in shared
 //     memory over the whole grid and added to the global deposit once per node.
@@ -42,6 +45,9 @@ struct Args2D {
     const double *ebx, *eby;
     const double *az, *gax, *gay;
     double *jx, *jy;        // deposits of this sweep (zeroed before)
+    double hbar;            // Zeeman terms on when non-zero (spins given)
+    const double *s;        // np x 3 spins
+    const double *gxy, *gxx, *gyy, *gbx, *gby;   // G_x G_y a, G_x G_x a, G_y G_y a, G_x b_z, G_y b_z
     unsigned long long *dmax_bits, *pmax_bits;
     int *status;
     double glx[5], glw[5];  // K-point Gauss--Legendre on [-1, 1]
@@ -99,21 +105,28 @@ __device__ __forceinline__ bool walk1(double u0, double du, F &&f)
     return walk2(u0, 0.0, du, 0.0, [&](double sa, double sb) { f(sa, sb); });
 }
 
+// sum_i c_i N^{D1}(u1 - i1) N^{D2}(u2 - i2) at one point (cell coordinates)
+template <int D1, int D2>
+__device__ __forceinline__ double value_dd(const double *c, int M1, int M2, double u1, double u2)
+{
+    const double c1 = floor(u1), c2 = floor(u2);
+    double v1[D1 + 1], v2[D2 + 1];
+    bsp<D1>(u1 - c1, v1);
+    bsp<D2>(u2 - c2, v2);
+    double s = 0.0;
+#pragma unroll
+    for (int r1 = 0; r1 <= D1; ++r1) {
+        const int i1 = wrapi((int)c1 - r1, M1);
+#pragma unroll
+        for (int r2 = 0; r2 <= D2; ++r2) s += c[i1 * M2 + wrapi((int)c2 - r2, M2)] * v1[r1] * v2[r2];
+    }
+    return s;
+}
+
 template <int K>
 __device__ __forceinline__ double value0(const double *a, int M1, int M2, double u1, double u2)
 {
-    const double c1 = floor(u1), c2 = floor(u2);
-    double v1[K + 1], v2[K + 1];
-    bsp<K>(u1 - c1, v1);
-    bsp<K>(u2 - c2, v2);
-    double s = 0.0;
-#pragma unroll
-    for (int r1 = 0; r1 <= K; ++r1) {
-        const int i1 = wrapi((int)c1 - r1, M1);
-#pragma unroll
-        for (int r2 = 0; r2 <= K; ++r2) s += a[i1 * M2 + wrapi((int)c2 - r2, M2)] * v1[r1] * v2[r2];
-    }
-    return s;
+    return value_dd<K, K>(a, M1, M2, u1, u2);
 }
 
 // visit(i_x, v_x, i_y, v_y) per quadrature node and basis pair: the x-component
@@ -186,6 +199,59 @@ __device__ __forceinline__ double dA_mean(const Args2D &A, int axis, double u0, 
     return s;
 }
 
+// One coordinate-increment quotient of the Zeeman term along `axis`: the mean over
+// u_axis in [u0, u0 + du] (the other coordinate fixed at uo) of
+//   wm dF_m/du + wp dF_p/du + wb dF_b/du,
+// given the derivative coefficients on their own degrees (along, across):
+// cm on (K-1, K-1), cp on (K-2, K), cb on (K-2, K-1).  Along x1 these are
+// G_x G_y a, G_x G_x a and G_x b_z; along x2, G_x G_y a, G_y G_y a and G_y b_z.
+template <int K>
+__device__ __forceinline__ double zee_mean(const Args2D &A, int axis, double u0, double du, double uo,
+                                           const double *cm, double wm, const double *cp, double wp,
+                                           const double *cb, double wb)
+{
+    const double co = floor(uo);
+    double vk[K + 1], vm[K];
+    bsp<K>(uo - co, vk);
+    bsp<K - 1>(uo - co, vm);
+    const int Ma = axis == 0 ? A.M1 : A.M2, Mo = axis == 0 ? A.M2 : A.M1;
+    const int sa = axis == 0 ? A.M2 : 1, so = axis == 0 ? 1 : A.M2;
+    int io[K + 1];
+#pragma unroll
+    for (int ro = 0; ro <= K; ++ro) io[ro] = wrapi((int)co - ro, Mo) * so;
+    double s = 0.0;
+    walk1(u0, du, [&](double pa, double pb) {
+        const double sm = 0.5 * (pa + pb), hs = 0.5 * (pb - pa);
+        const double c = floor(u0 + sm * du);
+#pragma unroll
+        for (int g = 0; g < K; ++g) {
+            const double t = u0 + (sm + hs * A.glx[g]) * du - c;
+            double b1[K], b2[K - 1];
+            bsp<K - 1>(t, b1);
+            bsp<K - 2>(t, b2);
+            const double wq = hs * A.glw[g];
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                const int ia = wrapi((int)c - r, Ma) * sa;
+                double am = 0.0;
+#pragma unroll
+                for (int ro = 0; ro < K; ++ro) am += cm[ia + io[ro]] * vm[ro];
+                double v = wm * b1[r] * am;
+                if (r < K - 1) {
+                    double ap = 0.0, ab = 0.0;
+#pragma unroll
+                    for (int ro = 0; ro <= K; ++ro) ap += cp[ia + io[ro]] * vk[ro];
+#pragma unroll
+                    for (int ro = 0; ro < K; ++ro) ab += cb[ia + io[ro]] * vm[ro];
+                    v += b2[r < K - 1 ? r : 0] * (wp * ap + wb * ab);
+                }
+                s += wq * v;
+            }
+        }
+    });
+    return s;
+}
+
 __device__ __forceinline__ void max_bits(unsigned long long *dst, double v)
 {
     // non-negative doubles order like their bit patterns; NaN maps to the largest
@@ -221,8 +287,16 @@ __global__ void __launch_bounds__(256) k2_sweep(Args2D A)
         const double g0 = sqrt(1.0 + pp + A0 * A0);
         const double g1 = sqrt(1.0 + pp + A1 * A1);
         const double f = A.dt * (A1 + A0) / (g1 + g0);
-        const double q0 = p0 + A.dt * Ex - f * D1;
-        const double q1 = p1 + A.dt * Ey - f * D2;
+        double q0 = p0 + A.dt * Ex - f * D1;
+        double q1 = p1 + A.dt * Ey - f * D2;
+        if (A.hbar != 0.0) {
+            // discrete gradient of hbar s . B, B = (dA/dx2, -dA/dx1, b_z)
+            const double sx = A.s[3 * a], sy = A.s[3 * a + 1], sz = A.s[3 * a + 2];
+            const double Z1 = zee_mean<K>(A, 0, u0x, dux, u0y + duy, A.gxy, sx, A.gxx, -sy, A.gbx, sz);
+            const double Z2 = zee_mean<K>(A, 1, u0y, duy, u0x, A.gxy, -sy, A.gyy, sx, A.gby, sz);
+            q0 -= A.dt * A.hbar * Z1;
+            q1 -= A.dt * A.hbar * Z2;
+        }
         const double g2 = sqrt(1.0 + q0 * q0 + q1 * q1 + A1 * A1);
         const double n0 = A.dt * (p0 + q0) / (g1 + g2);
         const double n1 = A.dt * (p1 + q1) / (g1 + g2);
@@ -303,18 +377,34 @@ __global__ void k2_update(int N, const double *en, const double *sol, double *ek
     if ((threadIdx.x & 31) == 0) max_bits(emax_bits, m);
 }
 
+// acc[0] += sum_a w (g(p_a, A(x_a)) - 1); with spins, acc[1] += sum_a w hbar
+// (s_x dA/dx2 - s_y dA/dx1 + s_z b_z)(x_a) (G_y a on (K, K-1), G_x a on (K-1, K),
+// b_z on (K-1, K-1))
 template <int K>
-__global__ void __launch_bounds__(256) k2_kinetic(long long np, int M1, int M2, double dx1, double dx2, double w,
-                                                   const double *x, const double *p, const double *az, double *acc)
+__global__ void __launch_bounds__(256) k2_energy(long long np, int M1, int M2, double dx1, double dx2, double w,
+                                                  const double *x, const double *p, const double *az, double hbar,
+                                                  const double *sp, const double *gax, const double *gay,
+                                                  const double *bz, double *acc)
 {
-    double s = 0.0;
+    double s = 0.0, z = 0.0;
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < np;
          a += (long long)gridDim.x * blockDim.x) {
-        const double A = value0<K>(az, M1, M2, x[2 * a] / dx1, x[2 * a + 1] / dx2);
+        const double u1 = x[2 * a] / dx1, u2 = x[2 * a + 1] / dx2;
+        const double A = value0<K>(az, M1, M2, u1, u2);
         s += w * (sqrt(1.0 + p[2 * a] * p[2 * a] + p[2 * a + 1] * p[2 * a + 1] + A * A) - 1.0);
+        if (hbar != 0.0)
+            z += w * hbar * (sp[3 * a] * value_dd<K, K - 1>(gay, M1, M2, u1, u2) -
+                             sp[3 * a + 1] * value_dd<K - 1, K>(gax, M1, M2, u1, u2) +
+                             sp[3 * a + 2] * value_dd<K - 1, K - 1>(bz, M1, M2, u1, u2));
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc, s);
+        if (hbar != 0.0) atomicAdd(acc + 1, z);
+    }
 }
 
 // x^{n+1} = x^n + delta wrapped into the box, p^{n+1} = p^(k)
@@ -375,6 +465,8 @@ struct pic2d_handle {
     double *x = nullptr, *p = nullptr, *d = nullptr, *pk = nullptr;
     double *ex = nullptr, *ey = nullptr, *exk = nullptr, *eyk = nullptr, *ebx = nullptr, *eby = nullptr;
     double *az = nullptr, *gax = nullptr, *gay = nullptr;
+    double *gxy = nullptr, *gxx = nullptr, *gyy = nullptr;       // second differences of a_z
+    double *spin = nullptr, *bz = nullptr, *gbx = nullptr, *gby = nullptr;   // pic2d_set_spin
     double *jx = nullptr, *jy = nullptr, *tmp = nullptr, *sol = nullptr;
     double *g1x = nullptr, *g0y = nullptr, *g0x = nullptr, *g1y = nullptr;   // inverse rows
     unsigned long long *bits = nullptr;      // dmax, pmax, emax
@@ -409,13 +501,27 @@ static void free2d(pic2d_handle *h)
 {
     double **arrs[] = {&h->x, &h->p, &h->d, &h->pk, &h->ex, &h->ey, &h->exk, &h->eyk, &h->ebx, &h->eby,
                        &h->az, &h->gax, &h->gay, &h->jx, &h->jy, &h->tmp, &h->sol, &h->g1x, &h->g0y,
-                       &h->g0x, &h->g1y, &h->acc};
+                       &h->g0x, &h->g1y, &h->acc,
+                       &h->gxy, &h->gxx, &h->gyy, &h->spin, &h->bz, &h->gbx, &h->gby};
     for (double **a : arrs)
         if (*a) { cudaFree(*a); *a = nullptr; }
     if (h->bits) cudaFree(h->bits);
     if (h->status) cudaFree(h->status);
     h->bits = nullptr;
     h->status = nullptr;
+}
+
+// backward difference of a grid array along one axis, divided by the cell size
+static std::vector<double> grid_diff(const std::vector<double> &c, int M1, int M2, int axis, double dx)
+{
+    std::vector<double> out(c.size());
+    for (int i1 = 0; i1 < M1; ++i1)
+        for (int i2 = 0; i2 < M2; ++i2) {
+            const int i = i1 * M2 + i2;
+            const int j = axis == 0 ? ((i1 - 1 + M1) % M1) * M2 + i2 : i1 * M2 + (i2 - 1 + M2) % M2;
+            out[i] = (c[i] - c[j]) / dx;
+        }
+    return out;
 }
 
 // full periodic circulant row of the degree-d mass matrix (band folded onto M nodes)
@@ -451,7 +557,7 @@ extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double
     const pic2d_config &c = *cfg;
     if (!(c.L1 > 0.0) || !(c.L2 > 0.0) || c.M1 < 1 || c.M2 < 1 || (long long)c.M1 * c.M2 > kMax2DNodes ||
         c.degree < 2 || c.degree > 5 || c.np < 1 || !(c.dt > 0.0) || !(c.tol > 0.0) || c.max_iter < 1 ||
-        !std::isfinite(c.weight) || (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE))
+        !std::isfinite(c.weight) || !std::isfinite(c.hbar) || (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE))
         return fail2d(nullptr, PIC_ERR_INVALID, "bad 2D configuration");
     pic2d_handle *h = new (std::nothrow) pic2d_handle();
     if (!h) return fail2d(nullptr, PIC_ERR_NOMEM, "handle");
@@ -472,7 +578,7 @@ extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double
     for (double **a : parts)
         if (cudaMalloc((void **)a, np2 * sizeof(double)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
     double **grids[] = {&h->ex, &h->ey, &h->exk, &h->eyk, &h->ebx, &h->eby, &h->az, &h->gax, &h->gay,
-                        &h->jx, &h->jy, &h->tmp, &h->sol};
+                        &h->gxy, &h->gxx, &h->gyy, &h->jx, &h->jy, &h->tmp, &h->sol};
     for (double **a : grids)
         if (cudaMalloc((void **)a, N * sizeof(double)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
     if (cudaMalloc((void **)&h->g1x, c.M1 * sizeof(double)) != cudaSuccess ||
@@ -481,7 +587,7 @@ extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double
         cudaMalloc((void **)&h->g1y, c.M2 * sizeof(double)) != cudaSuccess ||
         cudaMalloc((void **)&h->bits, 3 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void **)&h->status, sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void **)&h->acc, sizeof(double)) != cudaSuccess)
+        cudaMalloc((void **)&h->acc, 2 * sizeof(double)) != cudaSuccess)
         return bail(PIC_ERR_NOMEM);
     // positions must lie in the box
     const cudaMemcpyKind kind = mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -499,18 +605,18 @@ extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double
         cudaMemcpyAsync(h->ey, ey, N * sizeof(double), kind, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->az, az, N * sizeof(double), kind, h->stream) != cudaSuccess)
         return bail(fail2d(h, PIC_ERR_CUDA, "input copies"));
-    // gradients of A_z (host: small grids): (G_x a)_{i1,i2} = (a_{i1,i2} - a_{i1-1,i2}) / dx1
+    // differences of A_z (host: small grids): (G_x a)_{i1,i2} = (a_{i1,i2} - a_{i1-1,i2}) / dx1,
+    // (G_y a)_{i1,i2} = (a_{i1,i2} - a_{i1,i2-1}) / dx2, and the second differences of the
+    // Zeeman term's quotients
     {
-        std::vector<double> a(N), gx(N), gy(N);
+        std::vector<double> a(N);
         if (cudaMemcpyAsync(a.data(), h->az, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
             cudaStreamSynchronize(h->stream) != cudaSuccess)
             return bail(fail2d(h, PIC_ERR_CUDA, "a_z readback"));
-        for (int i1 = 0; i1 < c.M1; ++i1)
-            for (int i2 = 0; i2 < c.M2; ++i2) {
-                const int i = i1 * c.M2 + i2;
-                gx[i] = (a[i] - a[((i1 - 1 + c.M1) % c.M1) * c.M2 + i2]) / h->dx1;
-                gy[i] = (a[i] - a[i1 * c.M2 + (i2 - 1 + c.M2) % c.M2]) / h->dx2;
-            }
+        const std::vector<double> gx = grid_diff(a, c.M1, c.M2, 0, h->dx1), gy = grid_diff(a, c.M1, c.M2, 1, h->dx2);
+        const std::vector<double> gxy = grid_diff(gy, c.M1, c.M2, 0, h->dx1);
+        const std::vector<double> gxx = grid_diff(gx, c.M1, c.M2, 0, h->dx1);
+        const std::vector<double> gyy = grid_diff(gy, c.M1, c.M2, 1, h->dx2);
         std::vector<double> g1x = inverse_row(c.degree - 1, c.M1, h->dx1), g0x = inverse_row(c.degree, c.M1, h->dx1);
         std::vector<double> g1y = inverse_row(c.degree - 1, c.M2, h->dx2), g0y = inverse_row(c.degree, c.M2, h->dx2);
         h->m0x = mass_row_full(c.degree, c.M1, h->dx1);
@@ -518,6 +624,9 @@ extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double
         h->m0y = mass_row_full(c.degree, c.M2, h->dx2);
         h->m1y = mass_row_full(c.degree - 1, c.M2, h->dx2);
         if (cudaMemcpy(h->gax, gx.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->gxy, gxy.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->gxx, gxx.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->gyy, gyy.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(h->gay, gy.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(h->g1x, g1x.data(), c.M1 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(h->g0x, g0x.data(), c.M1 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -554,6 +663,8 @@ extern "C" int pic2d_substep1(pic2d_handle *h, int32_t *iters)
 {
     if (!h) return PIC_ERR_INVALID;
     const pic2d_config &c = h->cfg;
+    if (c.hbar != 0.0 && !h->spin)
+        return fail2d(h, PIC_ERR_INVALID, "hbar != 0: pic2d_set_spin must give the spins and b_z first");
     const size_t np2 = 2 * (size_t)c.np, N = (size_t)h->N;
     cudaStream_t s = h->stream;
     CK2(cudaMemsetAsync(h->d, 0, np2 * sizeof(double), s));
@@ -567,6 +678,8 @@ extern "C" int pic2d_substep1(pic2d_handle *h, int32_t *iters)
     a.M1 = c.M1; a.M2 = c.M2; a.np = c.np; a.dx1 = h->dx1; a.dx2 = h->dx2; a.dt = c.dt; a.w = c.weight;
     a.x = h->x; a.pn = h->p; a.d = h->d; a.pk = h->pk;
     a.ebx = h->ebx; a.eby = h->eby; a.az = h->az; a.gax = h->gax; a.gay = h->gay;
+    a.hbar = h->spin ? c.hbar : 0.0;
+    a.s = h->spin; a.gxy = h->gxy; a.gxx = h->gxx; a.gyy = h->gyy; a.gbx = h->gbx; a.gby = h->gby;
     a.jx = h->jx; a.jy = h->jy; a.dmax_bits = h->bits; a.pmax_bits = h->bits + 1; a.status = h->status;
     for (int g = 0; g < 5; ++g) { a.glx[g] = h->glx[g]; a.glw[g] = h->glw[g]; }
     int num_sms = 0;
@@ -637,29 +750,70 @@ static double kron_quad(const std::vector<double> &e, const std::vector<double> 
     return 0.5 * s;
 }
 
-extern "C" int pic2d_energy(pic2d_handle *h, double out[3])
+extern "C" int pic2d_energy(pic2d_handle *h, double out[4])
 {
     if (!h || !out) return PIC_ERR_INVALID;
     const pic2d_config &c = h->cfg;
-    CK2(cudaMemsetAsync(h->acc, 0, sizeof(double), h->stream));
+    CK2(cudaMemsetAsync(h->acc, 0, 2 * sizeof(double), h->stream));
     const int grid = (int)std::min<long long>((c.np + 255) / 256, 1024);
+    const double hb = h->spin ? c.hbar : 0.0;
+#define PIC2D_ENERGY(K)                                                                                     \
+    k2_energy<K><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, hb, \
+                                              h->spin, h->gax, h->gay, h->bz, h->acc)
     switch (c.degree) {
-    case 2: k2_kinetic<2><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, h->acc); break;
-    case 3: k2_kinetic<3><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, h->acc); break;
-    case 4: k2_kinetic<4><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, h->acc); break;
-    default: k2_kinetic<5><<<grid, 256, 0, h->stream>>>(c.np, c.M1, c.M2, h->dx1, h->dx2, c.weight, h->x, h->p, h->az, h->acc); break;
+    case 2: PIC2D_ENERGY(2); break;
+    case 3: PIC2D_ENERGY(3); break;
+    case 4: PIC2D_ENERGY(4); break;
+    default: PIC2D_ENERGY(5); break;
     }
+#undef PIC2D_ENERGY
     CK2(cudaGetLastError());
     std::vector<double> ex(h->N), ey(h->N);
-    double kin = 0.0;
-    CK2(cudaMemcpyAsync(&kin, h->acc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    double acc[2] = {0.0, 0.0};
+    CK2(cudaMemcpyAsync(acc, h->acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
     CK2(cudaMemcpyAsync(ex.data(), h->ex, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK2(cudaMemcpyAsync(ey.data(), h->ey, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK2(cudaStreamSynchronize(h->stream));
     const double fe = kron_quad(ex, h->m1x, h->m0y, c.M1, c.M2) + kron_quad(ey, h->m0x, h->m1y, c.M1, c.M2);
-    out[0] = kin;
+    out[0] = acc[0];
     out[1] = fe;
-    out[2] = kin + fe;
+    out[2] = acc[1];
+    out[3] = acc[0] + fe + acc[1];
+    return PIC_OK;
+}
+
+extern "C" int pic2d_set_spin(pic2d_handle *h, const double *s, const double *bz, int32_t mem)
+{
+    if (!h || !s || !bz || (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE)) return PIC_ERR_INVALID;
+    const pic2d_config &c = h->cfg;
+    const size_t N = (size_t)h->N, n3 = 3 * (size_t)c.np;
+    if (!h->spin) {
+        double *sp = nullptr, *b0 = nullptr, *b1 = nullptr, *b2 = nullptr;
+        if (cudaMalloc((void **)&sp, n3 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&b0, N * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&b1, N * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&b2, N * sizeof(double)) != cudaSuccess) {
+            for (double *q : {sp, b0, b1, b2})
+                if (q) cudaFree(q);
+            return fail2d(h, PIC_ERR_NOMEM, "spin and b_z arrays");
+        }
+        h->spin = sp;
+        h->bz = b0;
+        h->gbx = b1;
+        h->gby = b2;
+    }
+    const cudaMemcpyKind kind = mem == PIC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    std::vector<double> b(N);
+    CK2(cudaMemcpyAsync(h->spin, s, n3 * sizeof(double), kind, h->stream));
+    CK2(cudaMemcpyAsync(h->bz, bz, N * sizeof(double), kind, h->stream));
+    CK2(cudaMemcpyAsync(b.data(), h->bz, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK2(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < N; ++i)
+        if (!std::isfinite(b[i])) return fail2d(h, PIC_ERR_INVALID, "b_z not finite at node %zu", i);
+    const std::vector<double> gbx = grid_diff(b, c.M1, c.M2, 0, h->dx1), gby = grid_diff(b, c.M1, c.M2, 1, h->dx2);
+    CK2(cudaMemcpyAsync(h->gbx, gbx.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK2(cudaMemcpyAsync(h->gby, gby.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK2(cudaStreamSynchronize(h->stream));
     return PIC_OK;
 }
 

@@ -15,7 +15,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class pic2d_config(ctypes.Structure):
     _fields_ = [("L1", ctypes.c_double), ("L2", ctypes.c_double), ("M1", ctypes.c_int32), ("M2", ctypes.c_int32),
                 ("degree", ctypes.c_int32), ("np", ctypes.c_int64), ("weight", ctypes.c_double),
-                ("dt", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32)]
+                ("dt", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("hbar", ctypes.c_double)]
 
 
 _ready = False
@@ -27,6 +28,7 @@ def _lib():
     if not _ready:
         L.pic2d_init.argtypes = [ctypes.POINTER(pic2d_config), _dp, _dp, _dp, _dp, _dp, ctypes.c_int32,
                                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        L.pic2d_set_spin.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_int32]
         L.pic2d_substep1.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
         L.pic2d_energy.argtypes = [ctypes.c_void_p, _dp]
         L.pic2d_get_state.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp, ctypes.c_int32]
@@ -49,10 +51,11 @@ class Config2D:
     dt: float
     tol: float = 1e-13
     max_iter: int = 100
+    hbar: float = 0.0
 
     def c(self) -> pic2d_config:
         return pic2d_config(self.L1, self.L2, self.M1, self.M2, self.degree, self.np, self.weight, self.dt,
-                            self.tol, self.max_iter)
+                            self.tol, self.max_iter, self.hbar)
 
 
 def _f64(a) -> np.ndarray:
@@ -83,15 +86,22 @@ class Pic2D:
             msg = self.L.pic2d_last_error(self.h).decode()
             raise (P.NoConvergence if rc == P.PIC_ERR_NOCONVERGE else P.PicError)(rc, msg)
 
+    def set_spin(self, s, bz):
+        """Spins (np x 3) and b_z (M1 * M2) for the Zeeman terms (hbar != 0)."""
+        c = self.cfg
+        s, bz = _f64(s), _f64(bz)
+        assert s.shape == (c.np, 3) and bz.shape == (c.M1 * c.M2,)
+        self._check(self.L.pic2d_set_spin(self.h, s.ctypes.data_as(_dp), bz.ctypes.data_as(_dp), P.PIC_MEM_HOST))
+
     def substep1(self) -> int:
         it = ctypes.c_int32()
         self._check(self.L.pic2d_substep1(self.h, ctypes.byref(it)))
         return it.value
 
     def energy(self) -> dict:
-        out = np.zeros(3)
+        out = np.zeros(4)
         self._check(self.L.pic2d_energy(self.h, out.ctypes.data_as(_dp)))
-        return {"kinetic": out[0], "field": out[1], "total": out[2]}
+        return {"kinetic": out[0], "field": out[1], "zeeman": out[2], "total": out[3]}
 
     def state(self) -> dict:
         c = self.cfg

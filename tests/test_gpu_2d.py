@@ -98,3 +98,65 @@ def test_2d_invalid_configurations():
     xo[0, 0] = cfg.L1 + 1.0                                            # outside the box
     with pytest.raises(pic.PicError):
         P2.Pic2D(cfg, xo, p, ex, ey, a)
+
+
+def _spins(seed, npart, n, amp=0.3):
+    rng = np.random.default_rng(seed)
+    s = rng.normal(0, 1, (npart, 3))
+    s /= np.linalg.norm(s, axis=1, keepdims=True)
+    return s, amp * rng.normal(0, 1, n)
+
+
+@pytest.mark.parametrize("k,M1,M2", [(2, 6, 5), (3, 7, 6), (4, 8, 5)])
+def test_2d_spin_substep_matches_oracle(k, M1, M2):
+    """hbar = 0.1: the Zeeman quotients (second differences of A_z, first of b_z)
+    on the GPU against the oracle; the Zeeman energy and the total likewise."""
+    cfg, orc, x, p, ex, ey, a = _case(60 + k, M1, M2, k, 40)
+    cfg.hbar = orc.hbar = 0.1
+    s, bz = _spins(90 + k, 40, M1 * M2)
+    g = P2.Pic2D(cfg, x, p, ex, ey, a)
+    g.set_spin(s, bz)
+    E0 = g.energy()
+    E0o = orc.energy(x, p, ex, ey, a, s, bz)
+    assert abs(E0["zeeman"] - E0o["zeeman"]) < 1e-12 * abs(E0o["total"])
+    assert abs(E0o["zeeman"]) > 1e-3 * abs(E0o["total"])
+    sx, sp, sex, sey = x, p, ex, ey
+    for step in range(2):
+        sx, sp, sex, sey, it = orc.substep1(sx, sp, sex, sey, a, s=s, bz=bz)
+        it_gpu = g.substep1()
+        assert abs(it_gpu - it) <= 1
+        st = g.state()
+        assert _close(st["x"][:, 0], sx[:, 0], cfg.L1, 1e-10)
+        assert _close(st["x"][:, 1], sx[:, 1], cfg.L2, 1e-10)
+        assert np.max(np.abs(st["p"] - sp)) <= 1e-10 * np.max(np.abs(sp))
+        assert np.max(np.abs(st["ex"] - sex)) <= 1e-10 * np.max(np.abs(sex))
+        assert np.max(np.abs(st["ey"] - sey)) <= 1e-10 * np.max(np.abs(sey))
+    E = g.energy()
+    Eo = orc.energy(sx, sp, sex, sey, a, s, bz)
+    assert abs(E["zeeman"] - Eo["zeeman"]) < 1e-12 * abs(Eo["total"])
+    assert abs(E["total"] - Eo["total"]) < 1e-12 * abs(Eo["total"])
+    g.close()
+
+
+def test_2d_spin_energy_conserved_on_gpu():
+    cfg, orc, x, p, ex, ey, a = _case(78, 12, 10, 3, 4000, L1=6.0, L2=5.0, vth=0.3)
+    cfg.hbar = 0.1
+    s, bz = _spins(79, 4000, 120)
+    g = P2.Pic2D(cfg, x, p, ex, ey, a)
+    g.set_spin(s, bz)
+    E0 = g.energy()
+    for _ in range(5):
+        g.substep1()
+    E1 = g.energy()
+    g.close()
+    assert abs(E1["zeeman"] - E0["zeeman"]) > 1e-6 * abs(E0["total"])     # the term does work
+    assert abs(E1["total"] - E0["total"]) < 1e-12 * abs(E0["total"])
+
+
+def test_2d_spin_required_when_hbar_set():
+    cfg, orc, x, p, ex, ey, a = _case(3, 5, 4, 3, 10)
+    cfg.hbar = 0.1
+    g = P2.Pic2D(cfg, x, p, ex, ey, a)
+    with pytest.raises(pic.PicError):
+        g.substep1()
+    g.close()
