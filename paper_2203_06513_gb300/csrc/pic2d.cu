@@ -38,7 +38,10 @@ struct Args2D {
     int M1, M2;
     long long np;
     double dx1, dx2, dt, w;
+    double idx1, idx2;      // 1 / dx1, 1 / dx2
     const double *x;        // np x 2, in the box
+    double *a0;             // np: A_z(x^n), written by the first sweep of a step
+    int first;              // this is the step's first sweep
     const double *pn;       // np x 2
     double *d;              // np x 2 displacement iterate (length units), in/out
     double *pk;             // np x 2 momentum iterate, in/out
@@ -76,19 +79,21 @@ template <class F>
 __device__ __forceinline__ bool walk2(double u0x, double u0y, double dux, double duy, F &&f)
 {
     const double ex = u0x + dux, ey = u0y + duy;
-    // next knot index and its step in each coordinate
-    int nx, ny, cx = 0, cy = 0;
     const int tx = dux > 0.0 ? (int)ceil(ex) - 1 - (int)floor(u0x) : (dux < 0.0 ? (int)ceil(u0x) - 1 - (int)floor(ex) : 0);
     const int ty = duy > 0.0 ? (int)ceil(ey) - 1 - (int)floor(u0y) : (duy < 0.0 ? (int)ceil(u0y) - 1 - (int)floor(ey) : 0);
     if (tx > kMaxCross || ty > kMaxCross) return false;
-    nx = dux > 0.0 ? (int)floor(u0x) + 1 : (int)ceil(u0x) - 1;
-    ny = duy > 0.0 ? (int)floor(u0y) + 1 : (int)ceil(u0y) - 1;
+    // next knot index and its step in each coordinate; crossing parameters by the
+    // reciprocal of the increment
+    int nx = dux > 0.0 ? (int)floor(u0x) + 1 : (int)ceil(u0x) - 1;
+    int ny = duy > 0.0 ? (int)floor(u0y) + 1 : (int)ceil(u0y) - 1;
     const int sx = dux > 0.0 ? 1 : -1, sy = duy > 0.0 ? 1 : -1;
+    const double rx = tx > 0 ? 1.0 / dux : 0.0, ry = ty > 0 ? 1.0 / duy : 0.0;
+    int cx = 0, cy = 0;
     double sa = 0.0;
     for (int guard = 0; guard < 2 * kMaxCross + 2; ++guard) {
-        const double bx = cx < tx ? ((double)nx - u0x) / dux : 2.0;
-        const double by = cy < ty ? ((double)ny - u0y) / duy : 2.0;
-        double sb = fmin(fmin(bx, by), 1.0);
+        const double bx = cx < tx ? ((double)nx - u0x) * rx : 2.0;
+        const double by = cy < ty ? ((double)ny - u0y) * ry : 2.0;
+        const double sb = fmin(fmin(bx, by), 1.0);
         if (sb > sa) f(sa, sb);
         if (sb >= 1.0) return true;
         if (bx <= sb) { nx += sx; ++cx; }
@@ -105,22 +110,47 @@ __device__ __forceinline__ bool walk1(double u0, double du, F &&f)
     return walk2(u0, 0.0, du, 0.0, [&](double sa, double sb) { f(sa, sb); });
 }
 
+// One triangle for two degrees: vk[r] = D! N^D(r + t) (r = 0..D) and
+// vm[r] = (D-1)! N^{D-1}(r + t) (r = 0..D-1), both left unnormalised
+template <int D>
+__device__ __forceinline__ void bsp_pair(double t, double *vk, double *vm)
+{
+    vk[0] = 1.0;
+    if (D == 1) vm[0] = 1.0;
+#pragma unroll
+    for (int n = 1; n <= D; ++n) {
+        vk[n] = (1.0 - t) * vk[n - 1];
+#pragma unroll
+        for (int r = n - 1; r >= 1; --r) vk[r] = (t + (double)r) * vk[r] + ((double)(n + 1 - r) - t) * vk[r - 1];
+        vk[0] = t * vk[0];
+        if (n == D - 1) {
+#pragma unroll
+            for (int r = 0; r < D; ++r) vm[r] = vk[r];
+        }
+    }
+}
+
 // sum_i c_i N^{D1}(u1 - i1) N^{D2}(u2 - i2) at one point (cell coordinates)
 template <int D1, int D2>
 __device__ __forceinline__ double value_dd(const double *c, int M1, int M2, double u1, double u2)
 {
     const double c1 = floor(u1), c2 = floor(u2);
     double v1[D1 + 1], v2[D2 + 1];
-    bsp<D1>(u1 - c1, v1);
-    bsp<D2>(u2 - c2, v2);
+    bspline_scaled<D1, double>(u1 - c1, v1);
+    bspline_scaled<D2, double>(u2 - c2, v2);
+    int o2[D2 + 1];
+#pragma unroll
+    for (int r2 = 0; r2 <= D2; ++r2) o2[r2] = wrapi((int)c2 - r2, M2);
     double s = 0.0;
 #pragma unroll
     for (int r1 = 0; r1 <= D1; ++r1) {
-        const int i1 = wrapi((int)c1 - r1, M1);
+        const double *row = c + wrapi((int)c1 - r1, M1) * M2;
+        double t = 0.0;
 #pragma unroll
-        for (int r2 = 0; r2 <= D2; ++r2) s += c[i1 * M2 + wrapi((int)c2 - r2, M2)] * v1[r1] * v2[r2];
+        for (int r2 = 0; r2 <= D2; ++r2) t = fma(v2[r2], row[o2[r2]], t);
+        s = fma(v1[r1], t, s);
     }
-    return s;
+    return s * (1.0 / ((double)Fact<D1>::v * (double)Fact<D2>::v));
 }
 
 template <int K>
@@ -129,74 +159,146 @@ __device__ __forceinline__ double value0(const double *a, int M1, int M2, double
     return value_dd<K, K>(a, M1, M2, u1, u2);
 }
 
-// visit(i_x, v_x, i_y, v_y) per quadrature node and basis pair: the x-component
-// value N^{K-1} x N^K at node i_x and the y-component value N^K x N^{K-1} at i_y,
-// already multiplied by the quadrature weight (path means over s in [0, 1])
-template <int K, class V>
-__device__ __forceinline__ bool path_means(const Args2D &A, double u0x, double u0y, double dux, double duy,
-                                           V &&visit)
+// The basis weights of one knot piece [sa, sb] of the path u0 -> u0 + du (inside
+// the cell (c1, c2)): mx[r1][r2] = (sb - sa) x the mean over the piece of the
+// x-component basis N^{K-1} x N^K at node (c1 - r1, c2 - r2), my likewise for the
+// y-component N^K x N^{K-1}, both times (K-1)! K! (unnormalised B-splines).
+// K-point Gauss--Legendre is exact: the integrand is a polynomial of degree
+// 2K - 1 in the path parameter.
+template <int K>
+__device__ __forceinline__ void piece_weights(const Args2D &A, double u0x, double u0y, double dux, double duy,
+                                              double sa, double sb, double c1, double c2, double (&mx)[K][K + 1],
+                                              double (&my)[K + 1][K])
 {
+    const double sm = 0.5 * (sa + sb), hs = 0.5 * (sb - sa);
+#pragma unroll
+    for (int g = 0; g < K; ++g) {
+        const double s = fma(hs, A.glx[g], sm);
+        const double wq = hs * A.glw[g];
+        double b1k[K + 1], b1m[K], b2k[K + 1], b2m[K];
+        bsp_pair<K>(fma(s, dux, u0x) - c1, b1k, b1m);
+        bsp_pair<K>(fma(s, duy, u0y) - c2, b2k, b2m);
+#pragma unroll
+        for (int r1 = 0; r1 < K; ++r1) {
+            const double f = wq * b1m[r1];
+#pragma unroll
+            for (int r2 = 0; r2 <= K; ++r2) mx[r1][r2] = g == 0 ? f * b2k[r2] : fma(f, b2k[r2], mx[r1][r2]);
+        }
+#pragma unroll
+        for (int r1 = 0; r1 <= K; ++r1) {
+            const double f = wq * b1k[r1];
+#pragma unroll
+            for (int r2 = 0; r2 < K; ++r2) my[r1][r2] = g == 0 ? f * b2m[r2] : fma(f, b2m[r2], my[r1][r2]);
+        }
+    }
+}
+
+// node offsets of the cell (c1, c2): o1[r] = ((c1 - r) mod M1) M2, o2[r] = (c2 - r) mod M2
+template <int K>
+__device__ __forceinline__ void cell_offsets(const Args2D &A, double c1, double c2, int *o1, int *o2)
+{
+#pragma unroll
+    for (int r = 0; r <= K; ++r) {
+        o1[r] = wrapi((int)c1 - r, A.M1) * A.M2;
+        o2[r] = wrapi((int)c2 - r, A.M2);
+    }
+}
+
+// (Ex, Ey) = the path means of e_bar's two components along u0 -> u0 + du
+template <int K>
+__device__ __forceinline__ bool gather_path(const Args2D &A, double u0x, double u0y, double dux, double duy,
+                                            double &Ex, double &Ey)
+{
+    double sx = 0.0, sy = 0.0;
+    const bool ok = walk2(u0x, u0y, dux, duy, [&](double sa, double sb) {
+        const double sm = 0.5 * (sa + sb);
+        const double c1 = floor(fma(sm, dux, u0x)), c2 = floor(fma(sm, duy, u0y));
+        double mx[K][K + 1], my[K + 1][K];
+        piece_weights<K>(A, u0x, u0y, dux, duy, sa, sb, c1, c2, mx, my);
+        int o1[K + 1], o2[K + 1];
+        cell_offsets<K>(A, c1, c2, o1, o2);
+#pragma unroll
+        for (int r1 = 0; r1 <= K; ++r1) {
+            const double *rx = A.ebx + o1[r1], *ry = A.eby + o1[r1];
+#pragma unroll
+            for (int r2 = 0; r2 <= K; ++r2) {
+                if (r1 < K) sx = fma(mx[r1 < K ? r1 : 0][r2], rx[o2[r2]], sx);
+                if (r2 < K) sy = fma(my[r1][r2 < K ? r2 : 0], ry[o2[r2]], sy);
+            }
+        }
+    });
+    const double scale = 1.0 / ((double)Fact<K - 1>::v * (double)Fact<K>::v);
+    Ex = sx * scale;
+    Ey = sy * scale;
+    return ok;
+}
+
+// s_j[x | y] += (wx, wy) x the path means of the two basis components along
+// u0 -> u0 + du, one shared-memory add per node and knot piece
+template <int K>
+__device__ __forceinline__ bool deposit_path(const Args2D &A, double *s_j, int N, double u0x, double u0y, double dux,
+                                             double duy, double wx, double wy)
+{
+    const double scale = 1.0 / ((double)Fact<K - 1>::v * (double)Fact<K>::v);
+    const double cx = wx * scale, cy = wy * scale;
     return walk2(u0x, u0y, dux, duy, [&](double sa, double sb) {
-        const double sm = 0.5 * (sa + sb), hs = 0.5 * (sb - sa);
-        const double c1 = floor(u0x + sm * dux), c2 = floor(u0y + sm * duy);
+        const double sm = 0.5 * (sa + sb);
+        const double c1 = floor(fma(sm, dux, u0x)), c2 = floor(fma(sm, duy, u0y));
+        double mx[K][K + 1], my[K + 1][K];
+        piece_weights<K>(A, u0x, u0y, dux, duy, sa, sb, c1, c2, mx, my);
+        int o1[K + 1], o2[K + 1];
+        cell_offsets<K>(A, c1, c2, o1, o2);
 #pragma unroll
-        for (int g = 0; g < K; ++g) {
-            const double s = sm + hs * A.glx[g];
-            const double wq = hs * A.glw[g];
-            const double t1 = u0x + s * dux - c1, t2 = u0y + s * duy - c2;
-            double b1k[K + 1], b1m[K], b2k[K + 1], b2m[K];
-            bsp<K>(t1, b1k);
-            bsp<K - 1>(t1, b1m);
-            bsp<K>(t2, b2k);
-            bsp<K - 1>(t2, b2m);
+        for (int r1 = 0; r1 <= K; ++r1) {
 #pragma unroll
-            for (int r1 = 0; r1 <= K; ++r1) {
-                const int i1 = wrapi((int)c1 - r1, A.M1);
-#pragma unroll
-                for (int r2 = 0; r2 <= K; ++r2) {
-                    const int i = i1 * A.M2 + wrapi((int)c2 - r2, A.M2);
-                    const double vx = (r1 < K) ? wq * b1m[r1 < K ? r1 : 0] * b2k[r2] : 0.0;
-                    const double vy = (r2 < K) ? wq * b1k[r1] * b2m[r2 < K ? r2 : 0] : 0.0;
-                    visit(i, vx, vy);
-                }
+            for (int r2 = 0; r2 <= K; ++r2) {
+                const int i = o1[r1] + o2[r2];
+                if (r1 < K && cx != 0.0) atomicAdd(&s_j[i], cx * mx[r1 < K ? r1 : 0][r2]);
+                if (r2 < K && cy != 0.0) atomicAdd(&s_j[N + i], cy * my[r1][r2 < K ? r2 : 0]);
             }
         }
     });
 }
 
-// mean of dA/dx1 along x1 from u0 to u0 + du at fixed x2 (cell coordinate u2):
-// sum (G_x a)_i (mean of N^{K-1}(x1 - i1)) N^K(x2 - i2); and the same along x2
+// mean of dA/dx1 along x1 from u0 to u0 + du at fixed x2 (cell coordinate uo):
+// sum (G_x a)_i (mean of N^{K-1}(x1 - i1)) N^K(x2 - i2); and the same along x2.
+// The across factor is contracted once per knot piece.
 template <int K>
 __device__ __forceinline__ double dA_mean(const Args2D &A, int axis, double u0, double du, double uo)
 {
     const double co = floor(uo);
     double vo[K + 1];
-    bsp<K>(uo - co, vo);
+    bspline_scaled<K, double>(uo - co, vo);
     const double *ga = axis == 0 ? A.gax : A.gay;
+    const int Ma = axis == 0 ? A.M1 : A.M2, Mo = axis == 0 ? A.M2 : A.M1;
+    const int sa_ = axis == 0 ? A.M2 : 1, so = axis == 0 ? 1 : A.M2;
+    int io[K + 1];
+#pragma unroll
+    for (int ro = 0; ro <= K; ++ro) io[ro] = wrapi((int)co - ro, Mo) * so;
     double s = 0.0;
-    walk1(u0, du, [&](double sa, double sb) {
-        const double sm = 0.5 * (sa + sb), hs = 0.5 * (sb - sa);
-        const double c = floor(u0 + sm * du);
+    walk1(u0, du, [&](double pa, double pb) {
+        const double sm = 0.5 * (pa + pb), hs = 0.5 * (pb - pa);
+        const double c = floor(fma(sm, du, u0));
+        double col[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const double *q = ga + wrapi((int)c - r, Ma) * sa_;
+            double acc = 0.0;
+#pragma unroll
+            for (int ro = 0; ro <= K; ++ro) acc = fma(q[io[ro]], vo[ro], acc);
+            col[r] = acc;
+        }
 #pragma unroll
         for (int g = 0; g < K; ++g) {
-            const double t = u0 + (sm + hs * A.glx[g]) * du - c;
             double bm[K];
-            bsp<K - 1>(t, bm);
-            const double wq = hs * A.glw[g];
+            bspline_scaled<K - 1, double>(fma(fma(hs, A.glx[g], sm), du, u0) - c, bm);
+            double v = 0.0;
 #pragma unroll
-            for (int r = 0; r < K; ++r) {
-                double acc = 0.0;
-#pragma unroll
-                for (int ro = 0; ro <= K; ++ro) {
-                    const int i = axis == 0 ? wrapi((int)c - r, A.M1) * A.M2 + wrapi((int)co - ro, A.M2)
-                                            : wrapi((int)co - ro, A.M1) * A.M2 + wrapi((int)c - r, A.M2);
-                    acc += ga[i] * vo[ro];
-                }
-                s += wq * bm[r] * acc;
-            }
+            for (int r = 0; r < K; ++r) v = fma(bm[r], col[r], v);
+            s = fma(hs * A.glw[g], v, s);
         }
     });
-    return s;
+    return s * (1.0 / ((double)Fact<K - 1>::v * (double)Fact<K>::v));
 }
 
 // One coordinate-increment quotient of the Zeeman term along `axis`: the mean over
@@ -212,8 +314,10 @@ __device__ __forceinline__ double zee_mean(const Args2D &A, int axis, double u0,
 {
     const double co = floor(uo);
     double vk[K + 1], vm[K];
-    bsp<K>(uo - co, vk);
-    bsp<K - 1>(uo - co, vm);
+    bsp_pair<K>(uo - co, vk, vm);
+    // normalisations of the unnormalised values folded into the weights
+    constexpr double fk = (double)Fact<K>::v, fm = (double)Fact<K - 1>::v, f2 = (double)Fact<K - 2>::v;
+    const double em = wm * (1.0 / (fm * fm)), ep = wp * (1.0 / (f2 * fk)), eb = wb * (1.0 / (f2 * fm));
     const int Ma = axis == 0 ? A.M1 : A.M2, Mo = axis == 0 ? A.M2 : A.M1;
     const int sa = axis == 0 ? A.M2 : 1, so = axis == 0 ? 1 : A.M2;
     int io[K + 1];
@@ -222,31 +326,34 @@ __device__ __forceinline__ double zee_mean(const Args2D &A, int axis, double u0,
     double s = 0.0;
     walk1(u0, du, [&](double pa, double pb) {
         const double sm = 0.5 * (pa + pb), hs = 0.5 * (pb - pa);
-        const double c = floor(u0 + sm * du);
+        const double c = floor(fma(sm, du, u0));
+        double colm[K], colq[K - 1];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const int ia = wrapi((int)c - r, Ma) * sa;
+            double am = 0.0;
+#pragma unroll
+            for (int ro = 0; ro < K; ++ro) am = fma(cm[ia + io[ro]], vm[ro], am);
+            colm[r] = em * am;
+            if (r < K - 1) {
+                double ap = 0.0, ab = 0.0;
+#pragma unroll
+                for (int ro = 0; ro <= K; ++ro) ap = fma(cp[ia + io[ro]], vk[ro], ap);
+#pragma unroll
+                for (int ro = 0; ro < K; ++ro) ab = fma(cb[ia + io[ro]], vm[ro], ab);
+                colq[r < K - 1 ? r : 0] = ep * ap + eb * ab;
+            }
+        }
 #pragma unroll
         for (int g = 0; g < K; ++g) {
-            const double t = u0 + (sm + hs * A.glx[g]) * du - c;
             double b1[K], b2[K - 1];
-            bsp<K - 1>(t, b1);
-            bsp<K - 2>(t, b2);
-            const double wq = hs * A.glw[g];
+            bsp_pair<K - 1>(fma(fma(hs, A.glx[g], sm), du, u0) - c, b1, b2);
+            double v = 0.0;
 #pragma unroll
-            for (int r = 0; r < K; ++r) {
-                const int ia = wrapi((int)c - r, Ma) * sa;
-                double am = 0.0;
+            for (int r = 0; r < K; ++r) v = fma(b1[r], colm[r], v);
 #pragma unroll
-                for (int ro = 0; ro < K; ++ro) am += cm[ia + io[ro]] * vm[ro];
-                double v = wm * b1[r] * am;
-                if (r < K - 1) {
-                    double ap = 0.0, ab = 0.0;
-#pragma unroll
-                    for (int ro = 0; ro <= K; ++ro) ap += cp[ia + io[ro]] * vk[ro];
-#pragma unroll
-                    for (int ro = 0; ro < K; ++ro) ab += cb[ia + io[ro]] * vm[ro];
-                    v += b2[r < K - 1 ? r : 0] * (wp * ap + wb * ab);
-                }
-                s += wq * v;
-            }
+            for (int r = 0; r < K - 1; ++r) v = fma(b2[r], colq[r], v);
+            s = fma(hs * A.glw[g], v, s);
         }
     });
     return s;
@@ -263,24 +370,60 @@ template <int K>
 __global__ void __launch_bounds__(256) k2_sweep(Args2D A)
 {
     extern __shared__ double s_j[];     // 2 * M1 * M2: x then y
+    __shared__ int s_perm[256];
+    __shared__ int s_cnt[8];
     const int N = A.M1 * A.M2;
     for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) s_j[i] = 0.0;
     __syncthreads();
     double dm = 0.0, pm = 0.0;
     bool bad = false;
-    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < A.np;
-         a += (long long)gridDim.x * blockDim.x) {
-        const double u0x = A.x[2 * a] / A.dx1, u0y = A.x[2 * a + 1] / A.dx2;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (long long base = blockIdx.x * 256LL; base < A.np; base += gridDim.x * 256LL) {
+        // The block's 256 markers in two groups, paths within one cell first and
+        // paths across a knot last (by the current iterate; the new path mostly
+        // follows it): a warp then runs the extra pieces of a crossing only when
+        // it holds crossing markers, instead of nearly every warp running them
+        // for one lane.
+        {
+            const long long b = base + threadIdx.x;
+            bool multi = true;
+            if (b < A.np) {
+                const double vx = A.x[2 * b] * A.idx1, vy = A.x[2 * b + 1] * A.idx2;
+                multi = floor(vx + A.d[2 * b] * A.idx1) != floor(vx) || floor(vy + A.d[2 * b + 1] * A.idx2) != floor(vy);
+            }
+            const unsigned one = __ballot_sync(0xffffffffu, !multi);
+            if (lane == 0) s_cnt[wid] = __popc(one);
+            __syncthreads();
+            int before = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const int c = s_cnt[w];
+                before += w < wid ? c : 0;
+                total += c;
+            }
+            s_perm[multi ? total + (wid * 32 - before) + __popc(~one & lt) : before + __popc(one & lt)] = threadIdx.x;
+            __syncthreads();
+        }
+        const long long a = base + s_perm[threadIdx.x];
+        __syncthreads();                    // s_perm and s_cnt are free for the next group
+        if (a >= A.np) continue;
+        {
+        const double u0x = A.x[2 * a] * A.idx1, u0y = A.x[2 * a + 1] * A.idx2;
         const double d0 = A.d[2 * a], d1 = A.d[2 * a + 1];
         const double p0 = A.pn[2 * a], p1 = A.pn[2 * a + 1];
-        const double dux = d0 / A.dx1, duy = d1 / A.dx2;
-        const double A0 = value0<K>(A.az, A.M1, A.M2, u0x, u0y);
+        const double dux = d0 * A.idx1, duy = d1 * A.idx2;
+        // A(x^n) is the same in every sweep of the step: evaluated in the first
+        double A0;
+        if (A.first) {
+            A0 = value0<K>(A.az, A.M1, A.M2, u0x, u0y);
+            A.a0[a] = A0;
+        } else {
+            A0 = A.a0[a];
+        }
         const double A1 = value0<K>(A.az, A.M1, A.M2, u0x + dux, u0y + duy);
-        double Ex = 0.0, Ey = 0.0;
-        bool ok = path_means<K>(A, u0x, u0y, dux, duy, [&](int i, double vx, double vy) {
-            Ex += vx * A.ebx[i];
-            Ey += vy * A.eby[i];
-        });
+        double Ex, Ey;
+        bool ok = gather_path<K>(A, u0x, u0y, dux, duy, Ex, Ey);
         const double D1 = dA_mean<K>(A, 0, u0x, dux, u0y + duy);
         const double D2 = dA_mean<K>(A, 1, u0y, duy, u0x);
         const double pp = p0 * p0 + p1 * p1;
@@ -298,15 +441,12 @@ __global__ void __launch_bounds__(256) k2_sweep(Args2D A)
             q1 -= A.dt * A.hbar * Z2;
         }
         const double g2 = sqrt(1.0 + q0 * q0 + q1 * q1 + A1 * A1);
-        const double n0 = A.dt * (p0 + q0) / (g1 + g2);
-        const double n1 = A.dt * (p1 + q1) / (g1 + g2);
+        const double r = A.dt / (g1 + g2);
+        const double n0 = r * (p0 + q0);
+        const double n1 = r * (p1 + q1);
         if (!(isfinite(n0) && isfinite(n1))) { bad = true; continue; }
         // the current of the new path
-        const double wx = A.w * n0, wy = A.w * n1;
-        ok = ok && path_means<K>(A, u0x, u0y, n0 / A.dx1, n1 / A.dx2, [&](int i, double vx, double vy) {
-            if (vx != 0.0) atomicAdd(&s_j[i], wx * vx);
-            if (vy != 0.0) atomicAdd(&s_j[N + i], wy * vy);
-        });
+        ok = ok && deposit_path<K>(A, s_j, N, u0x, u0y, n0 * A.idx1, n1 * A.idx2, A.w * n0, A.w * n1);
         if (!ok) bad = true;
         dm = fmax(dm, fmax(fabs(n0 - d0), fabs(n1 - d1)));
         pm = fmax(pm, fmax(fabs(q0 - A.pk[2 * a]), fabs(q1 - A.pk[2 * a + 1])));
@@ -314,6 +454,7 @@ __global__ void __launch_bounds__(256) k2_sweep(Args2D A)
         A.d[2 * a + 1] = n1;
         A.pk[2 * a] = q0;
         A.pk[2 * a + 1] = q1;
+        }
     }
     if (bad) atomicOr(A.status, STATUS_NUMERIC);
     // block maxima of the increments
@@ -462,7 +603,7 @@ struct pic2d_handle {
     cudaStream_t stream = nullptr;
     double dx1 = 0.0, dx2 = 0.0;
     int N = 0;
-    double *x = nullptr, *p = nullptr, *d = nullptr, *pk = nullptr;
+    double *x = nullptr, *p = nullptr, *d = nullptr, *pk = nullptr, *a0 = nullptr;
     double *ex = nullptr, *ey = nullptr, *exk = nullptr, *eyk = nullptr, *ebx = nullptr, *eby = nullptr;
     double *az = nullptr, *gax = nullptr, *gay = nullptr;
     double *gxy = nullptr, *gxx = nullptr, *gyy = nullptr;       // second differences of a_z
@@ -499,7 +640,7 @@ static int fail2d(pic2d_handle *h, int code, const char *fmt, ...)
 
 static void free2d(pic2d_handle *h)
 {
-    double **arrs[] = {&h->x, &h->p, &h->d, &h->pk, &h->ex, &h->ey, &h->exk, &h->eyk, &h->ebx, &h->eby,
+    double **arrs[] = {&h->x, &h->p, &h->d, &h->pk, &h->a0, &h->ex, &h->ey, &h->exk, &h->eyk, &h->ebx, &h->eby,
                        &h->az, &h->gax, &h->gay, &h->jx, &h->jy, &h->tmp, &h->sol, &h->g1x, &h->g0y,
                        &h->g0x, &h->g1y, &h->acc,
                        &h->gxy, &h->gxx, &h->gyy, &h->spin, &h->bz, &h->gbx, &h->gby};
@@ -577,6 +718,7 @@ extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double
     double **parts[] = {&h->x, &h->p, &h->d, &h->pk};
     for (double **a : parts)
         if (cudaMalloc((void **)a, np2 * sizeof(double)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
+    if (cudaMalloc((void **)&h->a0, (size_t)c.np * sizeof(double)) != cudaSuccess) return bail(PIC_ERR_NOMEM);
     double **grids[] = {&h->ex, &h->ey, &h->exk, &h->eyk, &h->ebx, &h->eby, &h->az, &h->gax, &h->gay,
                         &h->gxy, &h->gxx, &h->gyy, &h->jx, &h->jy, &h->tmp, &h->sol};
     for (double **a : grids)
@@ -676,6 +818,7 @@ extern "C" int pic2d_substep1(pic2d_handle *h, int32_t *iters)
     CK2(cudaMemsetAsync(h->status, 0, sizeof(int), s));
     Args2D a{};
     a.M1 = c.M1; a.M2 = c.M2; a.np = c.np; a.dx1 = h->dx1; a.dx2 = h->dx2; a.dt = c.dt; a.w = c.weight;
+    a.idx1 = 1.0 / h->dx1; a.idx2 = 1.0 / h->dx2; a.a0 = h->a0;
     a.x = h->x; a.pn = h->p; a.d = h->d; a.pk = h->pk;
     a.ebx = h->ebx; a.eby = h->eby; a.az = h->az; a.gax = h->gax; a.gay = h->gay;
     a.hbar = h->spin ? c.hbar : 0.0;
@@ -693,6 +836,7 @@ extern "C" int pic2d_substep1(pic2d_handle *h, int32_t *iters)
         CK2(cudaMemsetAsync(h->jx, 0, N * sizeof(double), s));
         CK2(cudaMemsetAsync(h->jy, 0, N * sizeof(double), s));
         CK2(cudaMemsetAsync(h->bits, 0, 3 * sizeof(unsigned long long), s));
+        a.first = it == 0;
         switch (c.degree) {
         case 2: launch_sweep2d<2>(a, grid, smem, s); break;
         case 3: launch_sweep2d<3>(a, grid, smem, s); break;
