@@ -367,7 +367,7 @@ __device__ __forceinline__ void max_bits(unsigned long long *dst, double v)
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) k2_sweep(Args2D A)
+__global__ void __launch_bounds__(256, K <= 3 ? 2 : 1) k2_sweep(Args2D A)
 {
     extern __shared__ double s_j[];     // 2 * M1 * M2: x then y
     __shared__ int s_perm[256];
