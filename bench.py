@@ -295,6 +295,7 @@ def twod_run(steps: int, np_: int | None = None, oracle_np: int = 100):
     out = {"value": w.np * steps / dt_s, "unit": "marker-substeps/s", "ms_per_substep": 1e3 * dt_s / steps,
            "sweeps_per_substep": sweeps / steps, "rel_energy_err": abs(H1 - H0) / abs(H0),
            "us_per_marker_sweep": 1e6 * dt_s / (w.np * max(1, sweeps)),
+           "start": "x^(0) = x^n (the explicit predictor measured no fewer sweeps here)",
            "workload": "2D subsystem I: L1=L2=4pi, M1=M2=%d, k=%d, Np=%d, dt=%g, vth %g, A_z %g cos(2 x1) "
                        "cos(x2 2pi/L2), FP64" % (w.M1, w.degree, w.np, w.dt, w.vth, w.amp)}
     if oracle_np:

@@ -19,7 +19,8 @@
  * M1 = diag(M1_x (x) M0_y, M0_x (x) M1_y).  The Zeeman term is that of the 2D
  * Hamiltonian (Eq. discrete_H2d), + hbar s . B with B = (dA_z/dx2, -dA_z/dx1, b_z);
  * spins and b_z are constant in this subsystem.  The fixed point is a Picard
- * iteration on the positions from x^(0) = x^n with one e_xy update per sweep,
+ * iteration on the positions (from x^(0) = x^n, or the explicit predictor with
+ * its consistent field, see pic2d_config.warm) with one e_xy update per sweep,
  * stopped when the position, momentum and field increments are all at most tol.
  * All arithmetic is FP64.
  *
@@ -50,6 +51,10 @@ typedef struct pic2d_config {
     double tol;          /* absolute tolerance on the max-norm of the increments */
     int32_t max_iter;    /* sweep cap of the fixed point */
     double hbar;         /* 0: no spin terms; else pic2d_set_spin before the first step */
+    int32_t warm;        /* start of the fixed point: 0 = x^(0) = x^n with e^(0) = e^n;
+                            1 = the explicit predictor x^(0) = x^n + dt p^n / g(p^n, A(x^n))
+                            with the field consistent with it, e^(0) = e^n - M1^{-1} j(x^n -> x^(0))
+                            (the same fixed point; fewer sweeps) */
 } pic2d_config;
 
 typedef struct pic2d_handle pic2d_handle;

@@ -366,7 +366,11 @@ __device__ __forceinline__ void max_bits(unsigned long long *dst, double v)
     atomicMax(dst, b);
 }
 
-template <int K>
+// PRE: the predicted start instead of a sweep -- A(x^n) stored, the explicit
+// predictor delta^(0) = dt p^n / gamma(p^n, A(x^n)) written and the current of
+// x^n -> x^n + delta^(0) deposited, so that the fixed point can start from the
+// field consistent with it; no gather, no momentum update, no increments.
+template <int K, bool PRE = false>
 __global__ void __launch_bounds__(256, K <= 3 ? 2 : 1) k2_sweep(Args2D A)
 {
     extern __shared__ double s_j[];     // 2 * M1 * M2: x then y
@@ -389,8 +393,11 @@ __global__ void __launch_bounds__(256, K <= 3 ? 2 : 1) k2_sweep(Args2D A)
             const long long b = base + threadIdx.x;
             bool multi = true;
             if (b < A.np) {
+                // the predicted start's path is within dt p (gamma >= 1)
                 const double vx = A.x[2 * b] * A.idx1, vy = A.x[2 * b + 1] * A.idx2;
-                multi = floor(vx + A.d[2 * b] * A.idx1) != floor(vx) || floor(vy + A.d[2 * b + 1] * A.idx2) != floor(vy);
+                const double ex = PRE ? A.dt * A.pn[2 * b] : A.d[2 * b];
+                const double ey = PRE ? A.dt * A.pn[2 * b + 1] : A.d[2 * b + 1];
+                multi = floor(vx + ex * A.idx1) != floor(vx) || floor(vy + ey * A.idx2) != floor(vy);
             }
             const unsigned one = __ballot_sync(0xffffffffu, !multi);
             if (lane == 0) s_cnt[wid] = __popc(one);
@@ -413,6 +420,16 @@ __global__ void __launch_bounds__(256, K <= 3 ? 2 : 1) k2_sweep(Args2D A)
         const double d0 = A.d[2 * a], d1 = A.d[2 * a + 1];
         const double p0 = A.pn[2 * a], p1 = A.pn[2 * a + 1];
         const double dux = d0 * A.idx1, duy = d1 * A.idx2;
+        if constexpr (PRE) {
+            const double A0 = value0<K>(A.az, A.M1, A.M2, u0x, u0y);
+            A.a0[a] = A0;
+            const double r = A.dt / sqrt(1.0 + p0 * p0 + p1 * p1 + A0 * A0);
+            const double n0 = r * p0, n1 = r * p1;
+            if (!deposit_path<K>(A, s_j, N, u0x, u0y, n0 * A.idx1, n1 * A.idx2, A.w * n0, A.w * n1)) bad = true;
+            A.d[2 * a] = n0;
+            A.d[2 * a + 1] = n1;
+            continue;
+        }
         // A(x^n) is the same in every sweep of the step: evaluated in the first
         double A0;
         if (A.first) {
@@ -468,7 +485,7 @@ __global__ void __launch_bounds__(256, K <= 3 ? 2 : 1) k2_sweep(Args2D A)
         s_m[1][threadIdx.x >> 5] = pm;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !PRE) {
         double a = 0.0, b = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             a = fmax(a, s_m[0][w]);
@@ -684,9 +701,19 @@ static std::vector<double> inverse_row(int d, int M, double dx)
 }
 
 template <int K>
-static int launch_sweep2d(const Args2D &a, int grid, size_t smem, cudaStream_t s)
+static cudaError_t smem_optin(size_t smem)
 {
-    k2_sweep<K><<<grid, 256, smem, s>>>(a);
+    cudaError_t e = cudaFuncSetAttribute(k2_sweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k2_sweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+template <int K>
+static int launch_sweep2d(const Args2D &a, int grid, size_t smem, cudaStream_t s, bool pre)
+{
+    if (pre) k2_sweep<K, true><<<grid, 256, smem, s>>>(a);
+    else k2_sweep<K><<<grid, 256, smem, s>>>(a);
     return 0;
 }
 
@@ -698,6 +725,7 @@ extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double
     const pic2d_config &c = *cfg;
     if (!(c.L1 > 0.0) || !(c.L2 > 0.0) || c.M1 < 1 || c.M2 < 1 || (long long)c.M1 * c.M2 > kMax2DNodes ||
         c.degree < 2 || c.degree > 5 || c.np < 1 || !(c.dt > 0.0) || !(c.tol > 0.0) || c.max_iter < 1 ||
+        (c.warm != 0 && c.warm != 1) ||
         !std::isfinite(c.weight) || !std::isfinite(c.hbar) || (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE))
         return fail2d(nullptr, PIC_ERR_INVALID, "bad 2D configuration");
     pic2d_handle *h = new (std::nothrow) pic2d_handle();
@@ -780,10 +808,10 @@ extern "C" int pic2d_init(const pic2d_config *cfg, const double *x, const double
     const size_t smem = 2 * N * sizeof(double);
     cudaError_t e = cudaSuccess;
     switch (c.degree) {
-    case 2: e = cudaFuncSetAttribute(k2_sweep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    case 3: e = cudaFuncSetAttribute(k2_sweep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    case 4: e = cudaFuncSetAttribute(k2_sweep<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    default: e = cudaFuncSetAttribute(k2_sweep<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    case 2: e = smem_optin<2>(smem); break;
+    case 3: e = smem_optin<3>(smem); break;
+    case 4: e = smem_optin<4>(smem); break;
+    default: e = smem_optin<5>(smem); break;
     }
     if (e != cudaSuccess) return bail(fail2d(h, PIC_ERR_CUDA, "shared-memory opt-in: %s", cudaGetErrorString(e)));
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(fail2d(h, PIC_ERR_CUDA, "init sync"));
@@ -832,16 +860,36 @@ extern "C" int pic2d_substep1(pic2d_handle *h, int32_t *iters)
     unsigned long long hb[3];
     int hs = 0;
     int it = 0;
+    const bool warm = c.warm != 0;
+    if (warm) {
+        // the predicted start: delta^(0) and its current, then e^(0) = e^n - M1^{-1} j^(0)
+        // and e_bar = (e^n + e^(0)) / 2 for the first sweep
+        CK2(cudaMemsetAsync(h->jx, 0, N * sizeof(double), s));
+        CK2(cudaMemsetAsync(h->jy, 0, N * sizeof(double), s));
+        switch (c.degree) {
+        case 2: launch_sweep2d<2>(a, grid, smem, s, true); break;
+        case 3: launch_sweep2d<3>(a, grid, smem, s, true); break;
+        case 4: launch_sweep2d<4>(a, grid, smem, s, true); break;
+        default: launch_sweep2d<5>(a, grid, smem, s, true); break;
+        }
+        CK2(cudaGetLastError());
+        int rc;
+        if ((rc = solve_axis_pair(h, h->g1x, h->g0y, h->jx))) return rc;
+        k2_update<<<(h->N + 255) / 256, 256, 0, s>>>(h->N, h->ex, h->sol, h->exk, h->ebx, h->bits + 2);
+        if ((rc = solve_axis_pair(h, h->g0x, h->g1y, h->jy))) return rc;
+        k2_update<<<(h->N + 255) / 256, 256, 0, s>>>(h->N, h->ey, h->sol, h->eyk, h->eby, h->bits + 2);
+        CK2(cudaGetLastError());
+    }
     for (;;) {
         CK2(cudaMemsetAsync(h->jx, 0, N * sizeof(double), s));
         CK2(cudaMemsetAsync(h->jy, 0, N * sizeof(double), s));
         CK2(cudaMemsetAsync(h->bits, 0, 3 * sizeof(unsigned long long), s));
-        a.first = it == 0;
+        a.first = !warm && it == 0;          // the predicted start stored A(x^n) already
         switch (c.degree) {
-        case 2: launch_sweep2d<2>(a, grid, smem, s); break;
-        case 3: launch_sweep2d<3>(a, grid, smem, s); break;
-        case 4: launch_sweep2d<4>(a, grid, smem, s); break;
-        default: launch_sweep2d<5>(a, grid, smem, s); break;
+        case 2: launch_sweep2d<2>(a, grid, smem, s, false); break;
+        case 3: launch_sweep2d<3>(a, grid, smem, s, false); break;
+        case 4: launch_sweep2d<4>(a, grid, smem, s, false); break;
+        default: launch_sweep2d<5>(a, grid, smem, s, false); break;
         }
         CK2(cudaGetLastError());
         int rc;

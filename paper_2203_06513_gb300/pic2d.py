@@ -16,7 +16,7 @@ class pic2d_config(ctypes.Structure):
     _fields_ = [("L1", ctypes.c_double), ("L2", ctypes.c_double), ("M1", ctypes.c_int32), ("M2", ctypes.c_int32),
                 ("degree", ctypes.c_int32), ("np", ctypes.c_int64), ("weight", ctypes.c_double),
                 ("dt", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
-                ("hbar", ctypes.c_double)]
+                ("hbar", ctypes.c_double), ("warm", ctypes.c_int32)]
 
 
 _ready = False
@@ -52,10 +52,11 @@ class Config2D:
     tol: float = 1e-13
     max_iter: int = 100
     hbar: float = 0.0
+    warm: int = 0
 
     def c(self) -> pic2d_config:
         return pic2d_config(self.L1, self.L2, self.M1, self.M2, self.degree, self.np, self.weight, self.dt,
-                            self.tol, self.max_iter, self.hbar)
+                            self.tol, self.max_iter, self.hbar, self.warm)
 
 
 def _f64(a) -> np.ndarray:

@@ -160,3 +160,49 @@ def test_2d_spin_required_when_hbar_set():
     with pytest.raises(pic.PicError):
         g.substep1()
     g.close()
+
+
+@pytest.mark.parametrize("k,M1,M2,spin", [(2, 6, 5, False), (3, 7, 6, False), (3, 7, 6, True)])
+def test_2d_predicted_start_same_fixed_point(k, M1, M2, spin):
+    """warm = 1 starts the fixed point at the explicit predictor with its consistent
+    field: the same fixed point (the oracle's result, started from x^n, at 1e-10)
+    in no more sweeps than the start at x^n."""
+    cfg, orc, x, p, ex, ey, a = _case(80 + k, M1, M2, k, 60)
+    s, bz = _spins(81 + k, 60, M1 * M2)
+    if spin:
+        cfg.hbar = orc.hbar = 0.1
+    cfg.warm = 1
+    g = P2.Pic2D(cfg, x, p, ex, ey, a)
+    if spin:
+        g.set_spin(s, bz)
+    sx, sp, sex, sey = x, p, ex, ey
+    for step in range(2):
+        sx, sp, sex, sey, it = orc.substep1(sx, sp, sex, sey, a, s=s if spin else None, bz=bz if spin else None)
+        it_gpu = g.substep1()
+        print(f"step {step}: sweeps oracle (from x^n) {it}, GPU predicted start {it_gpu}")
+        assert it_gpu <= it
+        st = g.state()
+        assert _close(st["x"][:, 0], sx[:, 0], cfg.L1, 1e-10)
+        assert _close(st["x"][:, 1], sx[:, 1], cfg.L2, 1e-10)
+        assert np.max(np.abs(st["p"] - sp)) <= 1e-10 * np.max(np.abs(sp))
+        assert np.max(np.abs(st["ex"] - sex)) <= 1e-10 * np.max(np.abs(sex))
+        assert np.max(np.abs(st["ey"] - sey)) <= 1e-10 * np.max(np.abs(sey))
+    g.close()
+
+
+def test_2d_predicted_start_energy_and_gauss():
+    cfg, orc, x, p, ex, ey, a = _case(88, 12, 10, 3, 4000, L1=6.0, L2=5.0, vth=0.3)
+    cfg.warm = 1
+    g = P2.Pic2D(cfg, x, p, ex, ey, a)
+    H0 = g.energy()["total"]
+    st0 = g.state()
+    sweeps = [g.substep1() for _ in range(5)]
+    H1 = g.energy()["total"]
+    st1 = g.state()
+    g.close()
+    print("sweeps with the predicted start:", sweeps)
+    assert abs(H1 - H0) < 1e-12 * abs(H0)
+    gr = orc.g
+    lhs = gr.Gx.T @ (gr.M1x @ (st1["ex"] - st0["ex"])) + gr.Gy.T @ (gr.M1y @ (st1["ey"] - st0["ey"]))
+    rhs = -(gr.charge(st1["x"], cfg.weight) - gr.charge(st0["x"], cfg.weight))
+    assert np.max(np.abs(lhs - rhs)) < 1e-11 * np.max(np.abs(gr.charge(st0["x"], cfg.weight)))
