@@ -4,10 +4,11 @@ TEST INFRASTRUCTURE ONLY (same rules as oracle.py: only tests/, the smoke check
 and the benchmark's CPU-baseline leg may use it).
 
 The network is the one the library trains and runs: 6 inputs -> three hidden
-layers of width 64 with GELU -> 2 outputs, parameters packed in one vector in
-the order W1 (64x6, row-major [out][in]), b1, W2 (64x64), b2, W3, b3, W4 (2x64),
-b4 (8898 numbers).  GELU is the tanh form
-    gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
+layers of width 64 with ReLU, relu(z) = max(z, 0) -> 2 outputs, parameters packed
+in one vector in the order W1 (64x6, row-major [out][in]), b1, W2 (64x64), b2, W3,
+b3, W4 (2x64), b4 (8898 numbers).  The network is not from the paper: it only
+proposes the start of the subsystem-I fixed point, whose result does not depend on
+it.  Its derivative at z = 0 is taken as 0.
 The training loss is the mean over the batch of the squared error summed over
 the two outputs.  Gradients are by the chain rule, written out layer by layer;
 tests pin them against central finite differences.
@@ -20,7 +21,6 @@ import numpy as np
 
 SIZES = [(64, 6), (64, 64), (64, 64), (2, 64)]
 N_PARAMS = sum(o * i + o for o, i in SIZES)
-_C = math.sqrt(2.0 / math.pi)
 
 
 def unpack(theta: np.ndarray):
@@ -35,15 +35,12 @@ def unpack(theta: np.ndarray):
     return out
 
 
-def gelu(z):
-    return 0.5 * z * (1.0 + np.tanh(_C * (z + 0.044715 * z ** 3)))
+def relu(z):
+    return np.maximum(z, 0.0)
 
 
-def gelu_grad(z):
-    u = _C * (z + 0.044715 * z ** 3)
-    t = np.tanh(u)
-    du = _C * (1.0 + 3 * 0.044715 * z ** 2)
-    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * du
+def relu_grad(z):
+    return (z > 0.0).astype(np.float64)
 
 
 def forward(theta, X):
@@ -54,7 +51,7 @@ def forward(theta, X):
     for li, (W, b) in enumerate(layers):
         z = h @ W.T + b
         zs.append(z)
-        h = gelu(z) if li < len(layers) - 1 else z
+        h = relu(z) if li < len(layers) - 1 else z
         hs.append(h)
     return h, (zs, hs)
 
@@ -74,7 +71,7 @@ def grad(theta, X, T):
     for li in range(len(layers) - 1, -1, -1):
         W, _ = layers[li]
         if li < len(layers) - 1:
-            d = d * gelu_grad(zs[li])           # through the activation
+            d = d * relu_grad(zs[li])           # through the activation
         grads[li] = (d.T @ hs[li], d.sum(axis=0))
         d = d @ W                               # to the previous layer's output
     return np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])

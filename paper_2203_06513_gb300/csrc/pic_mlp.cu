@@ -6,8 +6,8 @@
 // the converged state or the conservation properties.
 //
 // Network: 6 inputs (cell-relative x, p, E_x(x^n), A_y(x^n), A_z(x^n), dt), each
-// normalised by (v - shift) * scale; three hidden layers of width 64 with GELU
-// (tanh form); 2 outputs, scaled by out_scale, read as
+// normalised by (v - shift) * scale; three hidden layers of width 64 with ReLU;
+// 2 outputs, scaled by out_scale, read as
 //   y0 = (x^{n+1} - x^n - dt p/gamma(p, A(x^n))) / dt^2   (residual of the explicit predictor)
 //   y1 = (p^{n+1} - p^n - dt E_x(x^n)) / dt^2.
 // Parameters: one float vector W1 (64x6, row-major [out][in]), b1, W2 (64x64),
@@ -15,7 +15,7 @@
 //
 // Inference runs on the 5th-generation tensor cores (tcgen05.mma, bf16 operands
 // in shared memory, fp32 accumulators in tensor memory), 128 markers per tile;
-// the GELU runs in packed bf16 on each thread's accumulator row.  Training
+// the ReLU runs in packed bf16 on each thread's accumulator row.  Training
 // (forward + backward + Adam) runs in fp32 on the CUDA cores.
 #include <cuda_bf16.h>
 
@@ -37,18 +37,10 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
 static_assert(kOffB4 + kOut == kNParams, "parameter packing");
 constexpr int kNorm = 2 * kIn + kOut;     // shift[6], scale[6], out_scale[2]
 
-__device__ __forceinline__ float gelu_exact(float z)
-{
-    return 0.5f * z * (1.f + tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z)));
-}
+__device__ __forceinline__ float relu(float z) { return fmaxf(z, 0.f); }
 
-__device__ __forceinline__ float gelu_grad(float z)
-{
-    const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
-    const float t = tanhf(u);
-    const float du = 0.7978845608028654f * (1.f + 3.f * 0.044715f * z * z);
-    return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * du;
-}
+// derivative of the ReLU, taken as 0 at z = 0
+__device__ __forceinline__ float relu_grad(float z) { return z > 0.f ? 1.f : 0.f; }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -58,30 +50,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return u;
 }
 
-// GELU (tanh form) of two pre-activations, evaluated in packed bf16 arithmetic on
-// their bf16 roundings and returned packed: the result is a bf16 activation of
-// the next layer either way, and one tanh.approx.bf16x2 serves both values.
-struct GeluConsts {
-    __nv_bfloat162 c0, c1;          // sqrt(2/pi), sqrt(2/pi) 0.044715
-    __device__ __forceinline__ GeluConsts()
-        : c0(__float2bfloat162_rn(0.7978845608028654f)), c1(__float2bfloat162_rn(0.7978845608028654f * 0.044715f))
-    {
-    }
-};
-
-// Twice the tanh-form GELU of a pair, z (1 + tanh u): the factor 1/2 is folded
-// into the next layer's weights (staged halved, exact in bf16), which saves one
-// packed multiply a pair.
-__device__ __forceinline__ uint32_t gelu2_bf16x2(float z0, float z1, const GeluConsts &k)
+// ReLU of two pre-activations, rounded to bf16 and packed: one packed max a pair.
+__device__ __forceinline__ uint32_t relu_bf16x2(float z0, float z1)
 {
-    const __nv_bfloat162 z = __floats2bfloat162_rn(z0, z1);
-    const __nv_bfloat162 u = __hmul2(z, __hfma2(__hmul2(z, z), k.c1, k.c0));   // c0 z + c1 z^3
-    uint32_t ui, ti;
-    memcpy(&ui, &u, 4);
-    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(ti) : "r"(ui));
-    __nv_bfloat162 th;
-    memcpy(&th, &ti, 4);
-    const __nv_bfloat162 out = __hfma2(z, th, z);                              // z (1 + tanh u)
+    const __nv_bfloat162 out = __hmax2(__floats2bfloat162_rn(z0, z1), __float2bfloat162_rn(0.f));
     uint32_t o;
     memcpy(&o, &out, 4);
     return o;
@@ -96,7 +68,7 @@ __device__ __forceinline__ uint32_t gelu2_bf16x2(float z0, float z1, const GeluC
 // issues the layer's tcgen05.mma instructions (M = 128, N = 64, K = 16 each) and
 // commits them to the chain's mbarrier, every thread of the chain waits (bounded),
 // loads its row of the fp32 accumulator from the chain's 64 tensor-memory columns
-// and applies the GELU.  While one chain waits for the tensor
+// and applies the ReLU.  While one chain waits for the tensor
 // cores, the other seven run their epilogues.  Weights are staged once per block,
 // in the same layout, and shared by the chains.
 // ---------------------------------------------------------------------------
@@ -228,15 +200,14 @@ __device__ void stage_umma(MlpUmma &S, const float *params, const float *norm)
         const int r = i >> 4, k = i & 15;
         put_bf16(S.ONES, kmaj_off(r, k, 16), k == 0 ? 1.f : 0.f);
     }
-    // the layers after a GELU take its doubled output: their weights are halved
     for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
         const int n = i >> 6, k = i & 63;
-        put_bf16(S.W2, kmaj_off(n, k, 64), 0.5f * params[kOffW2 + n * kHid + k]);
-        put_bf16(S.W3, kmaj_off(n, k, 64), 0.5f * params[kOffW3 + n * kHid + k]);
+        put_bf16(S.W2, kmaj_off(n, k, 64), params[kOffW2 + n * kHid + k]);
+        put_bf16(S.W3, kmaj_off(n, k, 64), params[kOffW3 + n * kHid + k]);
     }
     for (int i = threadIdx.x; i < kOutN * 64; i += blockDim.x) {
         const int n = i >> 6, k = i & 63;
-        put_bf16(S.W4, kmaj_off(n, k, 64), n < kOut ? 0.5f * params[kOffW4 + n * kHid + k] : 0.f);
+        put_bf16(S.W4, kmaj_off(n, k, 64), n < kOut ? params[kOffW4 + n * kHid + k] : 0.f);
     }
     if (threadIdx.x < kOut) S.b4[threadIdx.x] = params[kOffB4 + threadIdx.x];
     if (threadIdx.x < kNorm) S.norm[threadIdx.x] = norm[threadIdx.x];
@@ -328,14 +299,13 @@ __device__ __forceinline__ bool umma_layer(MlpUmma &S, int g, int r, const __nv_
     return ok;
 }
 
-// Doubled GELU of this thread's accumulator row (the chain's 64 columns, bias
-// included) into its row of the next layer's operand.  Warp w reads tensor-memory lanes
+// ReLU of this thread's accumulator row (the chain's 64 columns, bias included)
+// into its row of the next layer's operand.  Warp w reads tensor-memory lanes
 // 32 (w % 4) .. + 31.
 __device__ __forceinline__ void umma_epilogue(MlpUmma &S, int g, int r)
 {
     const uint32_t taddr = S.tmem + ((uint32_t)(r & ~31) << 16) + 64u * g;
     char *row = reinterpret_cast<char *>(S.C[g].A);
-    const GeluConsts k;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float v[32];
@@ -344,10 +314,10 @@ __device__ __forceinline__ void umma_epilogue(MlpUmma &S, int g, int r)
         for (int c = 0; c < 4; ++c) {      // 8 columns = one 16-byte chunk of the row
             uint4 o;
             const int k0 = 32 * h + 8 * c;
-            o.x = gelu2_bf16x2(v[8 * c + 0], v[8 * c + 1], k);
-            o.y = gelu2_bf16x2(v[8 * c + 2], v[8 * c + 3], k);
-            o.z = gelu2_bf16x2(v[8 * c + 4], v[8 * c + 5], k);
-            o.w = gelu2_bf16x2(v[8 * c + 6], v[8 * c + 7], k);
+            o.x = relu_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+            o.y = relu_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+            o.z = relu_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+            o.w = relu_bf16x2(v[8 * c + 6], v[8 * c + 7]);
             *reinterpret_cast<uint4 *>(row + kmaj_off(r, k0, 64)) = o;
         }
     }
@@ -492,7 +462,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_warm_mlp(WarmArgs A)
 
 // ---------------------------------------------------------------------------
 // Training: loss = mean over the batch of sum_o (y_o - T_o / out_scale_o)^2 on
-// the normalised outputs; gradients by the chain rule in fp32 (exact tanh).
+// the normalised outputs; gradients by the chain rule in fp32.
 // One block takes 32 samples; weight gradients are summed in shared memory and
 // added to the global gradient once per block.
 // ---------------------------------------------------------------------------
@@ -514,7 +484,7 @@ __device__ __forceinline__ void dense_fwd(const float *W, const float *b, const 
         float acc = b[n];
         for (int k = 0; k < nin; ++k) acc += W[n * nin + k] * hin[s * nin + k];
         z[s][n] = acc;
-        h[s][n] = gelu_exact(acc);
+        h[s][n] = relu(acc);
     }
 }
 
@@ -562,12 +532,12 @@ __global__ void __launch_bounds__(256) k_mlp_train(const float *params, const fl
         for (int s = 0; s < ns; ++s) acc += S.y[s][threadIdx.x];
         S.G[kOffB4 + threadIdx.x] += acc;
     }
-    // d3 = (dY W4) * gelu'(z3)   (into d1)
+    // d3 = (dY W4) * relu'(z3)   (into d1)
     for (int i = threadIdx.x; i < ns * kHid; i += blockDim.x) {
         const int s = i / kHid, k = i % kHid;
         float acc = 0.f;
         for (int o = 0; o < kOut; ++o) acc += S.y[s][o] * S.Wt[kOffW4 + o * kHid + k];
-        S.d1[s][k] = acc * gelu_grad(S.z3[s][k]);
+        S.d1[s][k] = acc * relu_grad(S.z3[s][k]);
     }
     __syncthreads();
     // hidden layers 3, 2, 1 (d in, gradient of W/b, d out)
@@ -597,7 +567,7 @@ __global__ void __launch_bounds__(256) k_mlp_train(const float *params, const fl
                 const int s = i / kHid, k = i % kHid;
                 float acc = 0.f;
                 for (int n = 0; n < kHid; ++n) acc += din[s][n] * S.Wt[offW[L] + n * kHid + k];
-                dout[s][k] = acc * gelu_grad(zprev[L][s][k]);
+                dout[s][k] = acc * relu_grad(zprev[L][s][k]);
             }
         }
         __syncthreads();

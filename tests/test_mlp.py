@@ -24,15 +24,15 @@ def test_reference_gradient_matches_finite_differences():
         assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(fd)), (i, fd, g[i])
 
 
-def test_reference_packing_and_gelu():
+def test_reference_packing_and_relu():
     assert R.N_PARAMS == 8898
-    z = np.linspace(-4, 4, 101)
-    # gelu(0) = 0, gelu(z) -> z for large z, -> 0 for very negative z
-    assert R.gelu(np.array([0.0]))[0] == 0.0
-    assert abs(R.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
-    assert abs(R.gelu(np.array([-10.0]))[0]) < 1e-12
+    z = np.array([-4.0, -1e-3, 0.0, 1e-3, 2.5])
+    np.testing.assert_array_equal(R.relu(z), [0.0, 0.0, 0.0, 1e-3, 2.5])
+    np.testing.assert_array_equal(R.relu_grad(z), [0.0, 0.0, 0.0, 1.0, 1.0])
+    # away from the kink the derivative is the difference quotient
+    zz = np.linspace(-4, 4, 100) + 0.0101
     h = 1e-6
-    np.testing.assert_allclose(R.gelu_grad(z), (R.gelu(z + h) - R.gelu(z - h)) / (2 * h), atol=1e-8)
+    np.testing.assert_allclose(R.relu_grad(zz), (R.relu(zz + h) - R.relu(zz - h)) / (2 * h), atol=1e-8)
 
 
 def _norm():
