@@ -1,7 +1,8 @@
 """Train the warm-start network on iterates the method itself generates.
 
-Runs small plain workloads (M = 128, cubic splines, 2e4 markers, dt = 0.05) with
-pump amplitudes 0.05..0.3 and thermal speeds 0.05..0.15 through libpic, and
+Runs small plain workloads (L = 4 pi, by default M = 128 cells and 2e5 markers,
+cubic splines, dt = 0.05) with pump amplitudes 0.05..0.3 and thermal speeds
+0.05..0.15 through libpic, and
 records, for every marker and step, the features at x^n (cell-relative x, p,
 E_x, A_y, A_z, dt) and the converged subsystem-I update, as the residuals of the
 explicit predictor scaled by 1/dt^2:
@@ -10,7 +11,7 @@ explicit predictor scaled by 1/dt^2:
 Training uses the library's own fp32 forward/backward kernels and Adam
 (pic_mlp_train_step).  Output: an .npz with params (8898 float32) and norm (14).
 
-    python -m paper_2203_06513_gb300.train_warm [out.npz]
+    python -m paper_2203_06513_gb300.train_warm [out.npz] [--nx 128] [--np 200000]
 """
 from __future__ import annotations
 
@@ -28,13 +29,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_OUT = os.path.join(HERE, "data", "warm_mlp.npz")
 
 
-def collect(torch, pumps=(0.05, 0.1, 0.2, 0.3), vths=(0.05, 0.1, 0.15), steps=12, np_run=20000,
-            seeds=(0, 1)):
+def collect(torch, pumps=(0.05, 0.1, 0.2, 0.3), vths=(0.05, 0.1, 0.15), steps=12, np_run=200000,
+            seeds=(0, 1), nx=128):
     X, Y = [], []
     for pump in pumps:
         for vth in vths:
             for seed in seeds:
-                w = I.Workload("train", nx=128, degree=3, np=np_run, dt=0.05, vth=vth, pump=pump,
+                w = I.Workload("train", nx=nx, degree=3, np=np_run, dt=0.05, vth=vth, pump=pump,
                                seed=100 + seed)
                 x, p = I.particles(w)
                 ay, az, ey, ez = I.fields(w)
@@ -109,11 +110,16 @@ def fit(torch, X, Y, norm, epochs=30, batch=4096, lr=2e-3, seed=0, log=print):
 
 
 def main(argv=None):
+    import argparse
     import torch
-    argv = sys.argv[1:] if argv is None else argv
-    out = argv[0] if argv else DEFAULT_OUT
+    ap = argparse.ArgumentParser()
+    ap.add_argument("out", nargs="?", default=DEFAULT_OUT)
+    ap.add_argument("--nx", type=int, default=128, help="cells of the training runs")
+    ap.add_argument("--np", type=int, default=200000, help="markers of each training run")
+    args = ap.parse_args(sys.argv[1:] if argv is None else argv)
+    out = args.out
     t = time.time()
-    X, Y = collect(torch)
+    X, Y = collect(torch, nx=args.nx, np_run=args.np)
     print(f"collected {X.shape[0]} samples in {time.time() - t:.1f} s", flush=True)
     norm = normalisation(X, Y)
     m, vloss, base = fit(torch, X, Y, norm)
