@@ -301,8 +301,8 @@ const char *pic_last_error(const pic_handle *h);
  * V0; the deposit uses degree-1).  Work is ordered on `stream` (cudaStream_t
  * as void*); every call reads a status word back and synchronises that stream,
  * so it blocks the host until out is complete.  The first call on a device
- * (with that device current) sets up the scratch address and kernel attributes;
- * make that first call before any stream capture.  All calls share the one
+ * (with that device current) sets up the scratch address and kernel attributes.
+ * All calls share the one
  * scratch array, which keeps the last call's contents: calls whose kernels
  * overlap on the GPU (other streams or threads) race and give wrong results.
  * Errors: PIC_ERR_INVALID, PIC_ERR_NUMERIC (a position or displacement that is
