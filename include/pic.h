@@ -22,8 +22,10 @@
  *    arrays have M entries, index j = coefficient of the j-th basis function.
  *  - Arrays passed with mem = PIC_MEM_DEVICE are device pointers on the
  *    handle's device; with PIC_MEM_HOST they are host pointers (pageable or
- *    pinned).  The caller owns every array it passes; the handle never keeps
- *    a caller pointer after a call returns.
+ *    page-locked; pic_init's load kernel reads page-locked marker arrays over
+ *    the host link itself, pageable ones are copied to the device first).  The
+ *    caller owns every array it passes; the handle never keeps a caller
+ *    pointer after a call returns.
  *  - The handle owns its device state and scratch (allocated in pic_init,
  *    freed in pic_destroy).  They come from a stream-ordered memory pool that
  *    the library keeps per device: what pic_destroy returns stays reserved in

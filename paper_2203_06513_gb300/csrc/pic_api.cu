@@ -222,6 +222,20 @@ static void stage_doubles(pic_handle *h, int b, double **x, double **p)
     if (p) *p = reinterpret_cast<double *>(base + a256((size_t)h->np * sizeof(double)));
 }
 
+// The device address of a page-locked host array (cudaMallocHost, cudaHostAlloc,
+// cudaHostRegister), through which kernels read and write it over the host link at
+// the copy engines' rate; null for pageable memory, which is staged by copies.
+static const void *pinned_device_ptr(const void *hp)
+{
+    if (!hp) return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, hp) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // degree of the time extrapolation that starts each subsystem's fixed point
 constexpr int kStartOrder1 = 0;
 constexpr int kStartOrder2 = 3;
@@ -506,13 +520,19 @@ extern "C" int pic_init_split(const pic_config *cfg, const pic_arrays *in, int32
 
     // inputs
     {
-        double *dx_in = nullptr, *dp_in = nullptr;
+        const double *dx_in = in->x, *dp_in = in->p;
         const bool host = mem == PIC_MEM_HOST;
         if (host) {
+            // page-locked host arrays are read by the load kernel itself; others are
             // staged in the second marker copy, which the first sort overwrites
-            stage_doubles(h, 1, &dx_in, &dp_in);
-            cudaMemcpyAsync(dx_in, in->x, np * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-            cudaMemcpyAsync(dp_in, in->p, np * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            const double *px = static_cast<const double *>(pinned_device_ptr(in->x));
+            const double *pp = static_cast<const double *>(pinned_device_ptr(in->p));
+            double *sx = nullptr, *sp = nullptr;
+            stage_doubles(h, 1, &sx, &sp);
+            if (px) dx_in = px;
+            else { cudaMemcpyAsync(sx, in->x, np * sizeof(double), cudaMemcpyHostToDevice, h->stream); dx_in = sx; }
+            if (pp) dp_in = pp;
+            else { cudaMemcpyAsync(sp, in->p, np * sizeof(double), cudaMemcpyHostToDevice, h->stream); dp_in = sp; }
         }
         const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
         cudaMemcpyAsync(h->ay, in->ay, M * sizeof(double), kind, h->stream);
@@ -524,8 +544,7 @@ extern "C" int pic_init_split(const pic_config *cfg, const pic_arrays *in, int32
         PartPtrs P0 = h->P[0];
         P0.delta = h->delta;
         P0.pnew = h->pnew;
-        launch_load(h->fp32, h->np, h->M, dx, host ? dx_in : in->x, host ? dp_in : in->p, P0,
-                    particle_grid(h), 256, h->stream);
+        launch_load(h->fp32, h->np, h->M, dx, dx_in, dp_in, P0, particle_grid(h), 256, h->stream);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess)
             return bail(fail(h, PIC_ERR_CUDA, "input copies / load: %s", cudaGetErrorString(e)));
@@ -1122,9 +1141,11 @@ extern "C" int pic_get_state(pic_handle *h, const pic_arrays *o, int32_t mem)
     if (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE) return fail(h, PIC_ERR_INVALID, "bad mem");
     const size_t np = (size_t)h->np, M = (size_t)h->M;
     const bool host = mem == PIC_MEM_HOST;
-    int rc = PIC_OK;
     if (o->x || o->p) {
         double *dx_out = o->x, *dp_out = o->p;
+        // the store writes each marker to its input position (a permutation after the
+        // sorts): scattered there in device memory, then copied to the host in bulk
+        // (writing host arrays directly from the kernel, scattered, ran 4x slower)
         if (host) stage_doubles(h, 1 - h->cur, o->x ? &dx_out : nullptr, o->p ? &dp_out : nullptr);
         launch_store(h->fp32, h->np, h->dx, cur_parts(h), dx_out, dp_out, particle_grid(h), 256, h->stream);
         cudaError_t e = cudaGetLastError();
