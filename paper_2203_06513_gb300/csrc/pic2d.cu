@@ -262,7 +262,8 @@ __device__ __forceinline__ bool deposit_path(const Args2D &A, double *s_j, int N
 
 // mean of dA/dx1 along x1 from u0 to u0 + du at fixed x2 (cell coordinate uo):
 // sum (G_x a)_i (mean of N^{K-1}(x1 - i1)) N^K(x2 - i2); and the same along x2.
-// The across factor is contracted once per knot piece.
+// The across factor is contracted once per knot piece; the along factor is the
+// exact piece mean of the midpoint form (no quadrature nodes).
 template <int K>
 __device__ __forceinline__ double dA_mean(const Args2D &A, int axis, double u0, double du, double uo)
 {
@@ -288,15 +289,15 @@ __device__ __forceinline__ double dA_mean(const Args2D &A, int axis, double u0, 
             for (int ro = 0; ro <= K; ++ro) acc = fma(q[io[ro]], vo[ro], acc);
             col[r] = acc;
         }
+        // the exact mean of the degree-(K-1) pieces over this piece (midpoint form,
+        // S_{K-1} times the mean), times its parameter length and (K-1)! / S_{K-1}
+        double m[K];
+        piece_means_scaled<K - 1, double>(fma(sm, du, u0) - c, 2.0 * hs * du, m);
+        double v = 0.0;
 #pragma unroll
-        for (int g = 0; g < K; ++g) {
-            double bm[K];
-            bspline_scaled<K - 1, double>(fma(fma(hs, A.glx[g], sm), du, u0) - c, bm);
-            double v = 0.0;
-#pragma unroll
-            for (int r = 0; r < K; ++r) v = fma(bm[r], col[r], v);
-            s = fma(hs * A.glw[g], v, s);
-        }
+        for (int r = 0; r < K; ++r) v = fma(m[r], col[r], v);
+        constexpr double kPM = (double)Fact<K - 1>::v / (double)MeanScale<K - 1>::S;
+        s = fma(2.0 * hs * kPM, v, s);
     });
     return s * (1.0 / ((double)Fact<K - 1>::v * (double)Fact<K>::v));
 }
