@@ -262,13 +262,16 @@ def e2e_run(pic, torch, w, arrays, precision, warm, steps, stream, mlp=None):
     g = pic.Pic(cfg, hx, hp, ay, az, ey, ez, stream=stream.cuda_stream)
     if mlp is not None:
         mlp.attach(g)
+    ta = time.perf_counter()          # pic_init returns with its work complete
     g.step(steps)
+    tb = time.perf_counter()          # pic_step returns with its work complete
     g.get_state(**out)
     t1 = time.perf_counter()
     g.close()
     h2d = 2 * 8 * w.np + 4 * 8 * w.nx
     d2h = 2 * 8 * w.np + 5 * 8 * w.nx
-    return {"s": t1 - t0, "h2d": h2d, "d2h": d2h}
+    return {"s": t1 - t0, "h2d": h2d, "d2h": d2h,
+            "phases_ms": {"init": 1e3 * (ta - t0), "steps": 1e3 * (tb - ta), "get_state": 1e3 * (t1 - tb)}}
 
 
 def twod_run(steps: int, np_: int | None = None, oracle_np: int = 100):
@@ -613,7 +616,8 @@ def main():
             "e2e": None if e2e is None else {
                 "value": R.whole_job_rate(w.np, ws, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": e2e["h2d"] / args.steps,
-                "d2h_bytes_per_step": e2e["d2h"] / args.steps},
+                "d2h_bytes_per_step": e2e["d2h"] / args.steps,
+                "phases_ms": e2e["phases_ms"]},
             "kernels": [_compact_kernel(k) for k in kernels],
             "kernel_ms": {"steps": tr["steps"], "sweep1": tr["sweep1_ms"], "sweep2": tr["sweep2_ms"],
                           "solve": tr["solve_ms"], "warm_start": tr["warm_ms"],
