@@ -1141,11 +1141,21 @@ extern "C" int pic_get_state(pic_handle *h, const pic_arrays *o, int32_t mem)
     if (mem != PIC_MEM_HOST && mem != PIC_MEM_DEVICE) return fail(h, PIC_ERR_INVALID, "bad mem");
     const size_t np = (size_t)h->np, M = (size_t)h->M;
     const bool host = mem == PIC_MEM_HOST;
-    if (o->x || o->p) {
+    // page-locked host arrays: written in caller order over the host link by one
+    // kernel, through the inverse of the markers' permutation (in the other marker copy)
+    double *px = (host && o->x) ? static_cast<double *>(const_cast<void *>(pinned_device_ptr(o->x))) : nullptr;
+    double *pp = (host && o->p) ? static_cast<double *>(const_cast<void *>(pinned_device_ptr(o->p))) : nullptr;
+    if ((o->x || o->p) && (!o->x || px) && (!o->p || pp)) {
+        int32_t *inv = reinterpret_cast<int32_t *>(h->Pblk[1 - h->cur]);
+        launch_store_ordered(h->fp32, h->np, h->dx, cur_parts(h), inv, px, pp, particle_grid(h), 256, h->stream);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return fail(h, PIC_ERR_CUDA, "get_state: %s", cudaGetErrorString(e));
+        h->launches += 2;
+    } else if (o->x || o->p) {
         double *dx_out = o->x, *dp_out = o->p;
         // the store writes each marker to its input position (a permutation after the
         // sorts): scattered there in device memory, then copied to the host in bulk
-        // (writing host arrays directly from the kernel, scattered, ran 4x slower)
         if (host) stage_doubles(h, 1 - h->cur, o->x ? &dx_out : nullptr, o->p ? &dp_out : nullptr);
         launch_store(h->fp32, h->np, h->dx, cur_parts(h), dx_out, dp_out, particle_grid(h), 256, h->stream);
         cudaError_t e = cudaGetLastError();

@@ -127,6 +127,10 @@ int launch_load(int fp32, long long np, int M, double dx, const double *x, const
                 PartPtrs P, int grid, int block, cudaStream_t s);
 int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, double *p,
                  int grid, int block, cudaStream_t s);
+// the same values in caller order through an inverse permutation (inv: np int32 of
+// scratch); consecutive writes, so x and p may be device addresses of page-locked host memory
+int launch_store_ordered(int fp32, long long np, double dx, PartPtrs P, int32_t *inv, double *x, double *p,
+                         int grid, int block, cudaStream_t s);
 int sweep_blocks_per_sm(int K, int fp32, int acc, int which, int block, size_t smem);
 // whether the sweep kernels are built for (degree, form, accumulator)
 bool sweep_variant_ok(int K, int fp32, int acc);

@@ -1364,6 +1364,41 @@ int launch_store(int fp32, long long np, double dx, PartPtrs P, double *x, doubl
     return 0;
 }
 
+// inv[id[a]] = a: where the marker of each caller index is stored
+__global__ void __launch_bounds__(256) k_inverse_id(long long np, const int32_t *__restrict__ id,
+                                                    int32_t *__restrict__ inv)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < np; a += stride)
+        inv[id[a]] = (int32_t)a;
+}
+
+// x[i], p[i] in caller order, each read from where marker i is stored: the writes are
+// consecutive, so the destination may be page-locked host memory written over the host
+// link (the same values as k_store)
+template <typename R>
+__global__ void __launch_bounds__(256) k_store_ordered(long long np, double dx, PartPtrs P,
+                                                       const int32_t *__restrict__ inv, double *x, double *p)
+{
+    const R *tp = static_cast<const R *>(P.t);
+    const R *pp = static_cast<const R *>(P.p);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
+        const long long a = inv[i];
+        if (x) x[i] = ((double)P.cell[a] + (double)tp[a]) * dx;
+        if (p) p[i] = (double)pp[a];
+    }
+}
+
+int launch_store_ordered(int fp32, long long np, double dx, PartPtrs P, int32_t *inv, double *x, double *p,
+                         int grid, int block, cudaStream_t s)
+{
+    k_inverse_id<<<grid, block, 0, s>>>(np, P.id, inv);
+    if (fp32) k_store_ordered<float><<<grid, block, 0, s>>>(np, dx, P, inv, x, p);
+    else k_store_ordered<double><<<grid, block, 0, s>>>(np, dx, P, inv, x, p);
+    return 0;
+}
+
 // ---------------------------------------------------------------------------
 // Counting sort of the markers by key = cell * nbins + velocity bin, the bin being
 // the expected displacement tau p in units of 1/per cell (nbins = 16 per, clamped),
