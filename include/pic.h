@@ -23,7 +23,8 @@
  *  - Arrays passed with mem = PIC_MEM_DEVICE are device pointers on the
  *    handle's device; with PIC_MEM_HOST they are host pointers (pageable or
  *    page-locked; pic_init's load kernel reads page-locked marker arrays over
- *    the host link itself, pageable ones are copied to the device first).  The
+ *    the host link itself and pic_get_state writes them the same way, while
+ *    pageable ones are copied through device buffers).  The
  *    caller owns every array it passes; the handle never keeps a caller
  *    pointer after a call returns.
  *  - The handle owns its device state and scratch (allocated in pic_init,
