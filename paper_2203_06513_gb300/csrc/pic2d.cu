@@ -345,17 +345,22 @@ __device__ __forceinline__ double zee_mean(const Args2D &A, int axis, double u0,
                 colq[r < K - 1 ? r : 0] = ep * ap + eb * ab;
             }
         }
+        // exact means of the degree-(K-1) and degree-(K-2) pieces over this piece
+        // (midpoint form, S_D times the mean; degree 0 is 1 inside one cell), each
+        // times D! / S_D to match the unnormalised values the weights expect
+        const double tm = fma(sm, du, u0) - c, hh = 2.0 * hs * du;
+        double m1[K], m2[K - 1];
+        piece_means_scaled<K - 1, double>(tm, hh, m1);
+        if constexpr (K >= 3) piece_means_scaled<(K >= 3 ? K - 2 : 1), double>(tm, hh, m2);
+        else m2[0] = 1.0;
+        constexpr double c1 = (double)Fact<K - 1>::v / (double)MeanScale<K - 1>::S;
+        constexpr double c2 = (double)Fact<K - 2>::v / (double)MeanScale<K - 2>::S;
+        double v1 = 0.0, v2 = 0.0;
 #pragma unroll
-        for (int g = 0; g < K; ++g) {
-            double b1[K], b2[K - 1];
-            bsp_pair<K - 1>(fma(fma(hs, A.glx[g], sm), du, u0) - c, b1, b2);
-            double v = 0.0;
+        for (int r = 0; r < K; ++r) v1 = fma(m1[r], colm[r], v1);
 #pragma unroll
-            for (int r = 0; r < K; ++r) v = fma(b1[r], colm[r], v);
-#pragma unroll
-            for (int r = 0; r < K - 1; ++r) v = fma(b2[r], colq[r], v);
-            s = fma(hs * A.glw[g], v, s);
-        }
+        for (int r = 0; r < K - 1; ++r) v2 = fma(m2[r], colq[r], v2);
+        s = fma(2.0 * hs, c1 * v1 + c2 * v2, s);
     });
     return s;
 }
